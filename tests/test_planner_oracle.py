@@ -1,0 +1,93 @@
+"""Pins of the planner oracle (Sec. 3): hand-derived costs, hand-counted
+trees, exhaustive enumeration of every TTM-tree against the recurrence, and
+the Remark that always reusing a mode is not optimal."""
+import json
+import os
+import random
+
+import pytest
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "planner_costs.json")
+
+
+def test_hand_derived_costs(orc):
+    data = json.load(open(GOLD))
+    for case in data["cases"]:
+        L, K = case["L"], case["K"]
+        assert orc.chain_cost(L, K) == case["chain_natural"]
+        assert orc.balanced_cost(L, K) == case["balanced"]
+        assert orc.tree_dp(L, K) == case["optimal"]
+        cnt, mn, mx = orc.tree_bruteforce(L, K)
+        assert mn == case["optimal"]
+        assert mx >= case["chain_natural"]
+
+
+def test_hand_counted_tree_numbers(orc):
+    data = json.load(open(GOLD))["tree_counts"]
+    for n_str, count in data.items():
+        if n_str.startswith("_"):
+            continue
+        N = int(n_str)
+        cnt, _, _ = orc.tree_bruteforce([3] * N, [2] * N)
+        assert cnt == count
+
+
+def test_bruteforce_equals_dp_random_small(orc):
+    rnd = random.Random(7)
+    for trial in range(150):
+        N = rnd.choice([2, 3, 4])
+        L = [rnd.choice([2, 3, 5, 8, 20, 50]) for _ in range(N)]
+        K = [rnd.randint(1, l) for l in L]
+        cnt, mn, mx = orc.tree_bruteforce(L, K)
+        assert mn == orc.tree_dp(L, K), (L, K)
+        # the chain and balanced trees are TTM-trees, so they cost at least the optimum
+        assert orc.chain_cost(L, K) >= mn
+        assert orc.balanced_cost(L, K) >= mn
+        assert orc.chain_cost(L, K, orc.k_order(L, K)) >= mn
+        assert orc.chain_cost(L, K, orc.h_order(L, K)) >= mn
+        if N == 4:
+            assert cnt == 4092
+
+
+@pytest.mark.slow
+def test_bruteforce_equals_dp_five_modes(orc):
+    # N = 5 has tens of millions of trees; two instances keep the run short.
+    for L, K in [((8, 12, 6, 10, 9), (3, 5, 2, 7, 4)), ((20, 50, 20, 100, 400), (10, 25, 16, 20, 40))]:
+        cnt, mn, _ = orc.tree_bruteforce(L, K)
+        assert cnt == 40241424
+        assert mn == orc.tree_dp(L, K)
+
+
+def test_always_reuse_is_not_optimal(orc):
+    # Remark after the recurrence (Sec. 3.3): the optimal tree may decline a
+    # reusable mode.  This 5-mode instance shows it; the DP without that
+    # restriction agrees with exhaustive enumeration.
+    L, K = (8, 400, 8, 64, 400), (5, 378, 8, 3, 302)
+    opt = orc.tree_dp(L, K)
+    greedy = orc.tree_dp(L, K, greedy=True)
+    assert greedy > opt
+    assert opt == 270174029056
+    assert greedy == 270194130176
+
+
+def test_balanced_and_chain_counts_match_section_3_2(orc):
+    # chain trees perform N(N-1) TTMs; with all K_n = L_n every TTM costs
+    # L*|T|, which exposes the TTM count directly.
+    for N in (2, 3, 4, 5):
+        L = [3] * N
+        cost = orc.chain_cost(L, L)
+        assert cost == N * (N - 1) * 3 * 3 ** N
+    # balanced tree for N = 4 has 8 internal nodes (Fig. "Example TTM-trees" (c))
+    assert orc.balanced_cost([3] * 4, [3] * 4) == 8 * 3 * 3 ** 4
+
+
+def test_tree_validator(orc):
+    # the N = 3 optimal tree for L=(2,3,4), K=(1,2,3), written out by hand
+    #  0 root; 1: x2 (mode 1); 2: x3 under 1 -> leaf F1; 3: x1 under 1 -> leaf F3
+    #  4: x1 under root; 5: x3 under 4 -> leaf F2
+    labels = [-1, 1, 2, 0, 0, 2, -2, -4, -3]
+    parents = [-1, 0, 1, 1, 0, 4, 2, 3, 5]
+    assert orc.tree_cost((2, 3, 4), (1, 2, 3), labels, parents) == 172
+    bad = list(parents)
+    bad[7] = 2  # leaf F3 under a path that lacks mode 1
+    assert orc.tree_cost((2, 3, 4), (1, 2, 3), labels, bad) is None

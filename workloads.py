@@ -1,0 +1,145 @@
+"""Seeded synthetic inputs shared by the tests, the oracle legs and bench.py.
+
+This module only draws random numbers and assembles planted Tucker tensors
+(Sec. 2.2 model T = G x_1 F_1 ... x_N F_N + E); it holds none of the HOOI /
+TTM-tree arithmetic of either side.  The planted product uses torch.tensordot
+(a library contraction) so that neither the oracle nor the CUDA path is
+involved in making its own inputs.
+
+Workload recipes (synthetic stand-ins; the paper fills its tensors with
+random data, Sec. 6 "Tensors"):
+  small_hooi   3-way FP64 64^3, core 8^3 N(0,1), F_n = Q of QR(64x8 Gaussian),
+               ||E|| = 1e-3 ||X||, ranks (8,8,8), seed 1.
+  big_fp32     4-way FP32 200^4, core 20^4 whose mode spectra are scaled by
+               1/k, QR factors, ||E|| = 1e-2 ||X||, ranks 20, seed 2.
+  precision5   5-way 64^5, core 16^5 with geometric 0.8 mode scaling,
+               1e-2 relative noise, ranks 16, seed 3 (stored BF16).
+  uneven6      64x56x48x40x32x24, core 16x14x12x10x8x6 N(0,1), Student-t
+               (nu = 3) noise at 1e-2 relative, seed 5 (stored BF16).
+"""
+from __future__ import annotations
+
+import math
+from typing import Sequence
+
+import torch
+
+
+def _gen(seed: int, device) -> torch.Generator:
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def orthonormal_factor(L: int, K: int, gen: torch.Generator, device, dtype=torch.float64):
+    """Q factor of the QR of an L x K Gaussian matrix (orthonormal columns)."""
+    A = torch.randn(L, K, generator=gen, device=device, dtype=torch.float64)
+    Q, R = torch.linalg.qr(A)
+    # make the factorisation unique: positive diagonal of R
+    s = torch.sign(torch.diagonal(R))
+    s[s == 0] = 1
+    return (Q * s).to(dtype)
+
+
+def spectrum_scale(K: int, kind, device):
+    if kind is None:
+        return None
+    if kind == "inv_k":
+        return 1.0 / torch.arange(1, K + 1, device=device, dtype=torch.float64)
+    if isinstance(kind, tuple) and kind[0] == "geom":
+        return kind[1] ** torch.arange(0, K, device=device, dtype=torch.float64)
+    raise ValueError(kind)
+
+
+def _mode_product(X: torch.Tensor, A: torch.Tensor, n: int) -> torch.Tensor:
+    """X x_n A for A of size J x X.shape[n] via tensordot (library contraction)."""
+    Y = torch.tensordot(A, X, dims=([1], [n]))  # J x (other modes)
+    return torch.movedim(Y, 0, n).contiguous()
+
+
+def planted_tucker(L: Sequence[int], K: Sequence[int], rho: float, seed: int,
+                   spectrum=None, noise: str = "gauss", dtype=torch.float32,
+                   device="cpu", build_dtype=None):
+    """Planted Tucker tensor T = G x_1 F_1 ... x_N F_N + E with ||E|| = rho * ||X||.
+
+    spectrum: None (core i.i.d. N(0,1)), "inv_k" (core mode k scaled by 1/k on
+    every mode) or ("geom", r) (scaled by r^(k-1)).  noise: "gauss" or
+    "student_t3".  Returns dict(T, G, F, X_norm).
+    """
+    device = torch.device(device)
+    g = _gen(seed, device)
+    N = len(L)
+    bdt = build_dtype or (torch.float64 if math.prod(L) <= 50_000_000 else torch.float32)
+    G = torch.randn(*K, generator=g, device=device, dtype=torch.float64)
+    for n in range(N):
+        d = spectrum_scale(K[n], spectrum, device)
+        if d is not None:
+            shape = [1] * N
+            shape[n] = K[n]
+            G = G * d.view(shape)
+    Fs = [orthonormal_factor(L[n], K[n], g, device) for n in range(N)]
+    X = G.to(bdt)
+    # apply the factors from the smallest growth to the largest to keep
+    # intermediates small
+    order = sorted(range(N), key=lambda n: L[n] / K[n])
+    for n in order:
+        X = _mode_product(X, Fs[n].to(bdt), n)
+    xnorm = float(torch.linalg.vector_norm(X.double() if X.numel() < 2**27 else X).item())
+    numel = X.numel()
+    if rho > 0:
+        sigma = rho * xnorm / math.sqrt(numel)
+        # draw the noise in chunks to bound the memory of big tensors
+        flat = X.view(-1)
+        chunk = 1 << 26
+        for s in range(0, numel, chunk):
+            e = min(numel, s + chunk)
+            if noise == "gauss":
+                z = torch.randn(e - s, generator=g, device=device, dtype=bdt)
+            elif noise == "student_t3":
+                # t_3 = Z / sqrt(chi2_3 / 3); unit variance needs a factor 1/sqrt(3)
+                z = torch.randn(e - s, generator=g, device=device, dtype=bdt)
+                chi = torch.zeros(e - s, device=device, dtype=bdt)
+                for _ in range(3):
+                    w = torch.randn(e - s, generator=g, device=device, dtype=bdt)
+                    chi += w * w
+                z = z / torch.sqrt(chi / 3.0) / math.sqrt(3.0)
+            else:
+                raise ValueError(noise)
+            flat[s:e] += sigma * z
+    T = X.to(dtype).contiguous()
+    return {"T": T, "G": G, "F": Fs, "X_norm": xnorm}
+
+
+def random_tensor(shape: Sequence[int], seed: int, dtype=torch.float32, device="cpu"):
+    g = _gen(seed, torch.device(device))
+    return torch.randn(*shape, generator=g, device=device, dtype=torch.float64).to(dtype)
+
+
+def random_factor(L: int, K: int, seed: int, dtype=torch.float32, device="cpu",
+                  orthonormal: bool = True):
+    g = _gen(seed, torch.device(device))
+    if orthonormal:
+        return orthonormal_factor(L, K, g, device).to(dtype)
+    return torch.randn(L, K, generator=g, device=device, dtype=torch.float64).to(dtype)
+
+
+# The named workloads used by bench.py and the parity tests.
+WORKLOADS = {
+    "small_hooi": dict(L=(64, 64, 64), K=(8, 8, 8), rho=1e-3, seed=1, spectrum=None,
+                       noise="gauss", dtype=torch.float64, sweeps=5),
+    "big_fp32": dict(L=(200, 200, 200, 200), K=(20, 20, 20, 20), rho=1e-2, seed=2,
+                     spectrum="inv_k", noise="gauss", dtype=torch.float32, sweeps=10),
+    "precision5": dict(L=(64,) * 5, K=(16,) * 5, rho=1e-2, seed=3, spectrum=("geom", 0.8),
+                       noise="gauss", dtype=torch.float32, sweeps=10),
+    "uneven6": dict(L=(64, 56, 48, 40, 32, 24), K=(16, 14, 12, 10, 8, 6), rho=1e-2, seed=5,
+                    spectrum=None, noise="student_t3", dtype=torch.float32, sweeps=8),
+}
+
+
+def make_workload(name: str, device="cpu", **override):
+    w = dict(WORKLOADS[name])
+    w.update(override)
+    out = planted_tucker(w["L"], w["K"], w["rho"], w["seed"], spectrum=w["spectrum"],
+                         noise=w["noise"], dtype=w["dtype"], device=device)
+    out["spec"] = w
+    return out
