@@ -1,0 +1,177 @@
+/*
+ * tucker.h -- C ABI of the GB300 (sm_103a) dense Tucker / HOOI library.
+ *
+ * The library computes, on one GPU, the STHOSVD initial decomposition and the
+ * HOOI procedure of Chakaravarthy et al., "On Optimizing Distributed Tucker
+ * Decomposition for Dense Tensors" (arXiv 1707.05594), whose TTM component is
+ * executed along the optimal TTM-tree of the paper's Sec. 3.3.
+ *
+ * Conventions shared by every call
+ *   - A tensor of size L_0 x ... x L_{N-1} is dense, row-major (C order, mode
+ *     N-1 fastest), contiguous, in device memory.  Modes are numbered from 0
+ *     (the paper counts them 1..N).
+ *   - Factor F_n is an L_n x K_n row-major matrix with orthonormal columns
+ *     (Sec. 2.2); the core G is K_0 x ... x K_{N-1} row-major.
+ *   - Element types: the plan's storage type fixes the type of T; factors and
+ *     core are double for TUCKER_F64 and float otherwise.
+ *   - Pointer arrays (F_in, F_out, ...) are HOST arrays of N DEVICE pointers.
+ *   - Every call that takes a stream is asynchronous on it.  The caller owns
+ *     all device buffers and the stream; the library owns plans.
+ *   - The workspace `ws` is caller-provided device memory of at least
+ *     tucker_plan_cost()'s ws_bytes, 256-byte aligned; one workspace must not
+ *     be used by two calls that may overlap on the GPU.
+ *   - Return value: TUCKER_OK (0) or a negative TUCKER_ERR_* code; the text of
+ *     the last error of the calling thread is returned by tucker_last_error().
+ *     No C++ exception crosses this boundary.  Arguments are validated on the
+ *     host before anything is launched.
+ */
+#ifndef TUCKER_GB300_H
+#define TUCKER_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TUCKER_OK 0
+#define TUCKER_ERR_INVALID_ARG (-1)
+#define TUCKER_ERR_UNSUPPORTED (-2)
+#define TUCKER_ERR_WORKSPACE (-3)
+#define TUCKER_ERR_CUDA (-4)
+#define TUCKER_ERR_TIMEOUT (-5)
+#define TUCKER_ERR_NONFINITE (-6)
+
+#define TUCKER_MAX_MODES 8
+
+/* Storage type of the input tensor T. */
+typedef enum {
+  TUCKER_F32 = 0,  /* float32; factors/core float32                        */
+  TUCKER_F64 = 1,  /* float64; factors/core float64                        */
+  TUCKER_BF16 = 2  /* bfloat16 (raw uint16 bits); factors/core float32     */
+} tucker_dtype_t;
+
+/* Which TTM-tree the plan executes (Sec. 3.2 / 3.3). */
+typedef enum {
+  TUCKER_TREE_OPTIMAL = 0,  /* DP of Sec. 3.3 (min cost)                  */
+  TUCKER_TREE_CHAIN = 1,    /* N independent chains, natural mode order  */
+  TUCKER_TREE_CHAIN_K = 2,  /* chains, modes by increasing K_n           */
+  TUCKER_TREE_CHAIN_H = 3,  /* chains, modes by increasing K_n / L_n     */
+  TUCKER_TREE_BALANCED = 4  /* Kaya-Ucar balanced tree                   */
+} tucker_tree_t;
+
+/* Node cost the optimal-tree DP minimises. */
+typedef enum {
+  TUCKER_COST_MACS = 0,  /* the paper's computational load K_n*|In(u)|   */
+  TUCKER_COST_ELEMS = 1  /* elements moved |In(u)| + |Out(u)|            */
+} tucker_cost_t;
+
+typedef struct {
+  int32_t dtype;      /* tucker_dtype_t, storage type of T               */
+  int32_t tree;       /* tucker_tree_t                                   */
+  int32_t cost_model; /* tucker_cost_t (only for TUCKER_TREE_OPTIMAL)    */
+  int32_t reserved;   /* must be 0                                       */
+} tucker_plan_opts_t;
+
+typedef struct tucker_plan_s* tucker_plan_t;
+
+/* One node of a plan's TTM-tree, in depth-first pre-order (root first).
+ * label: mode n (0-based) for an internal node (Out = In x_n F_n^T), -1 for
+ * the root, -(n+2) for the leaf that yields the new factor F~_n.
+ * parent: index of the parent node, -1 for the root.
+ * in_elems / out_elems: |In(u)|, |Out(u)|; macs: K_n*|In(u)| (0 for root and
+ * leaves); ws_offset: byte offset of Out(u) inside the workspace (internal
+ * nodes only, else 0). */
+typedef struct {
+  int32_t label;
+  int32_t parent;
+  uint64_t in_elems;
+  uint64_t out_elems;
+  uint64_t macs;
+  uint64_t ws_offset;
+} tucker_node_t;
+
+/* Builds a plan for tensor lengths L[0..N-1] and core lengths K[0..N-1]
+ * (Sec. 5: the planner needs only this metadata; the plan is reused by every
+ * sweep).  Host only, no device work.  Validation: 2 <= N <= 8,
+ * 1 <= K_n <= L_n, K_n <= prod_{j != n} K_j (else Z_(n) has rank < K_n),
+ * prod L_n < 2^40.  opts may be NULL (F32, optimal tree, MAC cost). */
+int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opts_t* opts,
+                tucker_plan_t* out);
+
+/* Per-sweep figures of the plan.  tree_macs: cost of the TTM-tree in the
+ * paper's unit (Sec. 3.1); tree_elems: elements read + written by its nodes;
+ * core_macs: the new-core TTM chain; ws_bytes: workspace every call of this
+ * plan needs.  Any output pointer may be NULL. */
+int tucker_plan_cost(tucker_plan_t plan, uint64_t* tree_macs, uint64_t* tree_elems,
+                     uint64_t* core_macs, size_t* ws_bytes);
+
+/* Copies at most `capacity` nodes of the plan's tree (see tucker_node_t) and
+ * sets *n_nodes to the total count.  nodes may be NULL to query the count. */
+int tucker_plan_nodes(tucker_plan_t plan, tucker_node_t* nodes, int capacity, int* n_nodes);
+
+void tucker_plan_destroy(tucker_plan_t plan);
+
+/* STHOSVD initial decomposition (Sec. 2.2 cites it; natural mode order):
+ * for n = 0..N-1, F_n <- leading K_n eigenvectors of Y_(n) Y_(n)^T and
+ * Y <- Y x_n F_n^T, starting from Y = T; G <- Y.  F: N device pointers. */
+int tucker_sthosvd(tucker_plan_t plan, const void* T, void* const* F, void* G, void* ws,
+                   size_t ws_bytes, void* stream);
+
+/* One HOOI invocation (Fig. 2) along the plan's TTM-tree: for every mode n,
+ * Z_n = T x_{j != n} F_in[j]^T (input factors for every chain), then
+ * F_out[n] <- leading K_n left singular vectors of Z_(n), computed as the
+ * leading eigenvectors of the Gram Z_(n) Z_(n)^T (Sec. 5).  Eigenvectors are
+ * ordered by decreasing eigenvalue, and each column's entry of largest
+ * magnitude is positive.  F_out may not alias F_in. */
+int tucker_hooi_sweep(tucker_plan_t plan, const void* T, const void* const* F_in,
+                      void* const* F_out, void* ws, size_t ws_bytes, void* stream);
+
+/* New core (Fig. 2): G = T x_0 F_0^T ... x_{N-1} F_{N-1}^T, with the chain's
+ * mode order chosen to minimise multiply-adds. */
+int tucker_core(tucker_plan_t plan, const void* T, const void* const* F, void* G, void* ws,
+                size_t ws_bytes, void* stream);
+
+/* ||T||_F^2 accumulated in double, written to the device double *out. */
+int tucker_norm2(tucker_plan_t plan, const void* T, double* out, void* stream);
+
+/* Error metric of Sec. 2.2 ("normalized root mean square"), using
+ * ||T - G x F||^2 = ||T||^2 - ||G||^2 for orthonormal factors:
+ * out[0] = fit = 1 - sqrt(max(0, normT2 - ||G||^2)) / sqrt(normT2),
+ * out[1] = ||G||^2.  normT2 and out are device pointers (out: 2 doubles). */
+int tucker_fit(tucker_plan_t plan, const void* G, const double* normT2, double* out,
+               void* stream);
+
+/* Single mode-n TTM (Sec. 2.1) Y = X x_n F^T for an X of lengths dims[0..N-1]
+ * of type x_dtype; F is dims[n] x K row-major (double for TUCKER_F64, else
+ * float); Y has dims with dims[n] replaced by K and type double for
+ * TUCKER_F64, else float.  Exposed for testing the TTM kernels. */
+int tucker_ttm(int N, const int64_t* dims, const void* X, int x_dtype, int n, const void* F,
+               int64_t K, void* Y, void* stream);
+
+/* Gram W = Z_(n) Z_(n)^T (Sec. 5) of a tensor Z of lengths dims[0..N-1] and
+ * type z_dtype; W is a dims[n] x dims[n] device double matrix (overwritten). */
+int tucker_gram(int N, const int64_t* dims, const void* Z, int z_dtype, int n, double* W,
+                void* stream);
+
+/* Leading-K eigenvectors of `batch` symmetric matrices (Sec. 5's EVD step).
+ * W[b]: L[b] x L[b] device doubles (read only); F[b]: L[b] x K[b] row-major
+ * output of type f_dtype (TUCKER_F64: double, else float), columns ordered by
+ * decreasing eigenvalue, sign as in tucker_hooi_sweep.  ws: device scratch of
+ * at least tucker_eig_ws_bytes(batch, L, K) bytes.  Requires L[b] <= 224. */
+int tucker_eig_topk(int batch, const int64_t* L, const int64_t* K, const double* const* W,
+                    void* const* F, int f_dtype, void* ws, size_t ws_bytes, void* stream);
+size_t tucker_eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* tucker_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int tucker_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUCKER_GB300_H */

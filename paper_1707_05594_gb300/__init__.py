@@ -1,0 +1,288 @@
+"""Python binding of the GB300 dense Tucker / HOOI library (include/tucker.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libtucker_gb300.so.  There is no CPU fallback; if the library is
+not built the import of any entry point raises.
+
+Tensors are torch tensors on the current CUDA device, contiguous; factor
+matrices are (L_n, K_n) row-major with the factor dtype (float64 for FP64
+tensors, float32 otherwise); bf16 tensors are passed as torch.bfloat16.
+Every call is asynchronous on torch's current stream (or `stream=`).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtucker_gb300.so")
+
+TUCKER_F32, TUCKER_F64, TUCKER_BF16 = 0, 1, 2
+TREE_OPTIMAL, TREE_CHAIN, TREE_CHAIN_K, TREE_CHAIN_H, TREE_BALANCED = 0, 1, 2, 3, 4
+COST_MACS, COST_ELEMS = 0, 1
+ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "WORKSPACE", -4: "CUDA", -5: "TIMEOUT",
+          -6: "NONFINITE"}
+
+_lib = None
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_vpp = ctypes.POINTER(ctypes.c_void_p)
+
+
+class TuckerError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("tree", ctypes.c_int32),
+                ("cost_model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Node(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_int32), ("parent", ctypes.c_int32),
+                ("in_elems", ctypes.c_uint64), ("out_elems", ctypes.c_uint64),
+                ("macs", ctypes.c_uint64), ("ws_offset", ctypes.c_uint64)]
+
+
+def lib():
+    """Load libtucker_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1707_05594_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    L.tucker_plan.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.POINTER(PlanOpts),
+                              ctypes.POINTER(ctypes.c_void_p)]
+    L.tucker_plan_cost.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p,
+                                   ctypes.POINTER(ctypes.c_size_t)]
+    L.tucker_plan_nodes.argtypes = [ctypes.c_void_p, ctypes.POINTER(Node), ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int)]
+    L.tucker_plan_destroy.argtypes = [ctypes.c_void_p]
+    L.tucker_plan_destroy.restype = None
+    L.tucker_sthosvd.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _vpp, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    L.tucker_hooi_sweep.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _vpp, _vpp,
+                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    L.tucker_core.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _vpp, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    L.tucker_norm2.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.tucker_fit.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p]
+    L.tucker_ttm.argtypes = [ctypes.c_int, _i64p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    L.tucker_gram.argtypes = [ctypes.c_int, _i64p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_void_p, ctypes.c_void_p]
+    L.tucker_eig_topk.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    L.tucker_eig_ws_bytes.argtypes = [ctypes.c_int, _i64p, _i64p]
+    L.tucker_eig_ws_bytes.restype = ctypes.c_size_t
+    L.tucker_last_error.restype = ctypes.c_char_p
+    L.tucker_version.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        msg = lib().tucker_last_error().decode(errors="replace")
+        raise TuckerError(rc, where, msg)
+
+
+def _i64(a: Sequence[int]):
+    return (ctypes.c_int64 * len(a))(*[int(x) for x in a])
+
+
+def _ptrs(ts):
+    return (ctypes.c_void_p * len(ts))(*[ctypes.c_void_p(t.data_ptr()) for t in ts])
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return TUCKER_F32
+    if t.dtype == torch.float64:
+        return TUCKER_F64
+    if t.dtype == torch.bfloat16:
+        return TUCKER_BF16
+    raise TypeError(f"unsupported tensor dtype {t.dtype}")
+
+
+def factor_torch_dtype(code: int):
+    import torch
+    return torch.float64 if code == TUCKER_F64 else torch.float32
+
+
+def _req(t, name):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+
+
+@dataclass
+class Plan:
+    """Owns a tucker_plan_t (library-owned TTM-tree + workspace layout)."""
+    handle: ctypes.c_void_p
+    L: tuple
+    K: tuple
+    dtype: int
+    tree: int
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.tucker_plan_destroy(self.handle)
+            self.handle = None
+
+    @property
+    def N(self):
+        return len(self.L)
+
+    @property
+    def factor_dtype(self):
+        return factor_torch_dtype(self.dtype)
+
+
+def tucker_plan(L: Sequence[int], K: Sequence[int], dtype: int = TUCKER_F32,
+                tree: int = TREE_OPTIMAL, cost_model: int = COST_MACS) -> Plan:
+    h = ctypes.c_void_p()
+    opts = PlanOpts(dtype, tree, cost_model, 0)
+    _check(lib().tucker_plan(len(L), _i64(L), _i64(K), ctypes.byref(opts), ctypes.byref(h)),
+           "tucker_plan")
+    return Plan(h, tuple(int(x) for x in L), tuple(int(x) for x in K), dtype, tree)
+
+
+def tucker_plan_cost(plan: Plan):
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    w = ctypes.c_size_t()
+    _check(lib().tucker_plan_cost(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                  ctypes.byref(w)), "tucker_plan_cost")
+    return {"tree_macs": a.value, "tree_elems": b.value, "core_macs": c.value,
+            "ws_bytes": w.value}
+
+
+def tucker_plan_nodes(plan: Plan) -> List[dict]:
+    n = ctypes.c_int()
+    _check(lib().tucker_plan_nodes(plan.handle, None, 0, ctypes.byref(n)), "tucker_plan_nodes")
+    arr = (Node * n.value)()
+    _check(lib().tucker_plan_nodes(plan.handle, arr, n.value, ctypes.byref(n)),
+           "tucker_plan_nodes")
+    return [{"label": x.label, "parent": x.parent, "in_elems": x.in_elems,
+             "out_elems": x.out_elems, "macs": x.macs, "ws_offset": x.ws_offset} for x in arr]
+
+
+def workspace(plan: Plan, device=None):
+    """Allocates a workspace of the plan's size (a torch uint8 buffer)."""
+    import torch
+    nb = tucker_plan_cost(plan)["ws_bytes"]
+    return torch.empty(max(nb, 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def tucker_sthosvd(plan: Plan, T, F: Sequence, G, ws, stream=None):
+    _req(T, "T")
+    _check(lib().tucker_sthosvd(plan.handle, ctypes.c_void_p(T.data_ptr()), _ptrs(F),
+                                ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                ws.numel(), _stream(stream)), "tucker_sthosvd")
+
+
+def tucker_hooi_sweep(plan: Plan, T, F_in: Sequence, F_out: Sequence, ws, stream=None):
+    _req(T, "T")
+    _check(lib().tucker_hooi_sweep(plan.handle, ctypes.c_void_p(T.data_ptr()), _ptrs(F_in),
+                                   _ptrs(F_out), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                   _stream(stream)), "tucker_hooi_sweep")
+
+
+def tucker_core(plan: Plan, T, F: Sequence, G, ws, stream=None):
+    _check(lib().tucker_core(plan.handle, ctypes.c_void_p(T.data_ptr()), _ptrs(F),
+                             ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                             ws.numel(), _stream(stream)), "tucker_core")
+
+
+def tucker_norm2(plan: Plan, T, out, stream=None):
+    _check(lib().tucker_norm2(plan.handle, ctypes.c_void_p(T.data_ptr()),
+                              ctypes.c_void_p(out.data_ptr()), _stream(stream)), "tucker_norm2")
+
+
+def tucker_fit(plan: Plan, G, normT2, out, stream=None):
+    _check(lib().tucker_fit(plan.handle, ctypes.c_void_p(G.data_ptr()),
+                            ctypes.c_void_p(normT2.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                            _stream(stream)), "tucker_fit")
+
+
+def tucker_ttm(X, n: int, F, Y, stream=None):
+    _req(X, "X")
+    _check(lib().tucker_ttm(X.dim(), _i64(X.shape), ctypes.c_void_p(X.data_ptr()),
+                            _dtype_code(X), n, ctypes.c_void_p(F.data_ptr()), F.shape[1],
+                            ctypes.c_void_p(Y.data_ptr()), _stream(stream)), "tucker_ttm")
+
+
+def tucker_gram(Z, n: int, W, stream=None):
+    _req(Z, "Z")
+    _check(lib().tucker_gram(Z.dim(), _i64(Z.shape), ctypes.c_void_p(Z.data_ptr()),
+                             _dtype_code(Z), n, ctypes.c_void_p(W.data_ptr()), _stream(stream)),
+           "tucker_gram")
+
+
+def tucker_eig_ws_bytes(Ls: Sequence[int], Ks: Sequence[int]) -> int:
+    return int(lib().tucker_eig_ws_bytes(len(Ls), _i64(Ls), _i64(Ks)))
+
+
+def tucker_eig_topk(Ws: Sequence, Fs: Sequence, ws, stream=None):
+    Ls = [W.shape[0] for W in Ws]
+    Ks = [F.shape[1] for F in Fs]
+    _check(lib().tucker_eig_topk(len(Ws), _i64(Ls), _i64(Ks), _ptrs(Ws), _ptrs(Fs),
+                                 _dtype_code(Fs[0]), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                 _stream(stream)), "tucker_eig_topk")
+
+
+def tucker_last_error() -> str:
+    return lib().tucker_last_error().decode(errors="replace")
+
+
+def tucker_version() -> int:
+    return lib().tucker_version()
+
+
+# ---------------------------------------------------------------- helpers ---
+class Decomposition:
+    """Convenience driver over the C ABI: holds T, the plan, workspace, factors,
+    core and the cached ||T||^2 on one device.  Every step calls the library."""
+
+    def __init__(self, T, K: Sequence[int], tree: int = TREE_OPTIMAL,
+                 cost_model: int = COST_MACS):
+        import torch
+        self.T = T
+        self.code = _dtype_code(T)
+        self.plan = tucker_plan(T.shape, K, self.code, tree, cost_model)
+        self.ws = workspace(self.plan, T.device)
+        fdt = self.plan.factor_dtype
+        L = T.shape
+        self.F = [torch.empty(L[n], K[n], dtype=fdt, device=T.device) for n in range(len(L))]
+        self.F_next = [torch.empty_like(f) for f in self.F]
+        self.G = torch.empty(*K, dtype=fdt, device=T.device)
+        self.normT2 = torch.empty(1, dtype=torch.float64, device=T.device)
+        self.fit_out = torch.empty(2, dtype=torch.float64, device=T.device)
+        tucker_norm2(self.plan, T, self.normT2)
+
+    def sthosvd(self):
+        tucker_sthosvd(self.plan, self.T, self.F, self.G, self.ws)
+        tucker_fit(self.plan, self.G, self.normT2, self.fit_out)
+
+    def sweep(self, with_core: bool = True):
+        tucker_hooi_sweep(self.plan, self.T, self.F, self.F_next, self.ws)
+        self.F, self.F_next = self.F_next, self.F
+        if with_core:
+            tucker_core(self.plan, self.T, self.F, self.G, self.ws)
+            tucker_fit(self.plan, self.G, self.normT2, self.fit_out)
+
+    def fit(self) -> float:
+        return float(self.fit_out[0].item())

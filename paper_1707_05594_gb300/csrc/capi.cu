@@ -1,0 +1,225 @@
+// capi.cu -- the executor behind the C ABI: walks a plan's TTM-tree in
+// depth-first order on a stream (Sec. 3.1 top-down execution, every node's
+// output reused by all its children), forms the Gram of each leaf's input
+// (Sec. 5), solves the N eigenproblems in one batched launch, and runs the
+// new-core chain, STHOSVD, norms and fit.
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+namespace tk {
+namespace {
+
+int factor_dtype(int dtype) { return dtype == TUCKER_F64 ? TUCKER_F64 : TUCKER_F32; }
+
+// [R][L][C] view of a tensor with lengths `dims` along mode n
+void view3(const int64_t* dims, int N, int n, int64_t* R, int64_t* L, int64_t* C) {
+  *R = prod(dims, 0, n);
+  *L = dims[n];
+  *C = prod(dims, n + 1, N);
+}
+
+int check_ws(const Plan& p, void* ws, size_t ws_bytes, const char* who) {
+  if (!ws) return fail(TUCKER_ERR_WORKSPACE, std::string(who) + ": workspace is NULL");
+  if (ws_bytes < p.ws_total)
+    return fail(TUCKER_ERR_WORKSPACE, std::string(who) + ": workspace smaller than ws_bytes");
+  if ((uintptr_t)ws % kAlign != 0)
+    return fail(TUCKER_ERR_WORKSPACE, std::string(who) + ": workspace not 256-byte aligned");
+  return TUCKER_OK;
+}
+
+int check_ptrs(const void* const* F, int N, const char* who) {
+  if (!F) return fail(TUCKER_ERR_INVALID_ARG, std::string(who) + ": factor array is NULL");
+  for (int n = 0; n < N; ++n)
+    if (!F[n]) return fail(TUCKER_ERR_INVALID_ARG, std::string(who) + ": a factor pointer is NULL");
+  return TUCKER_OK;
+}
+
+}  // namespace
+}  // namespace tk
+
+using namespace tk;
+
+extern "C" {
+
+int tucker_ttm(int N, const int64_t* dims, const void* X, int x_dtype, int n, const void* F,
+               int64_t K, void* Y, void* stream) {
+  if (N < 1 || N > kMaxModes || !dims || n < 0 || n >= N || K < 1 || !X || !F || !Y)
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_ttm: invalid argument");
+  for (int i = 0; i < N; ++i)
+    if (dims[i] < 1) return fail(TUCKER_ERR_INVALID_ARG, "tucker_ttm: lengths must be >= 1");
+  int64_t R, L, C;
+  view3(dims, N, n, &R, &L, &C);
+  return launch_ttm(x_dtype, X, R, L, C, F, K, Y, static_cast<cudaStream_t>(stream));
+}
+
+int tucker_gram(int N, const int64_t* dims, const void* Z, int z_dtype, int n, double* W,
+                void* stream) {
+  if (N < 1 || N > kMaxModes || !dims || n < 0 || n >= N || !Z || !W)
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_gram: invalid argument");
+  for (int i = 0; i < N; ++i)
+    if (dims[i] < 1) return fail(TUCKER_ERR_INVALID_ARG, "tucker_gram: lengths must be >= 1");
+  int64_t R, L, C;
+  view3(dims, N, n, &R, &L, &C);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TK_CUDA_TRY(cudaMemsetAsync(W, 0, (size_t)L * (size_t)L * sizeof(double), s));
+  return launch_gram(z_dtype, Z, R, L, C, W, s);
+}
+
+int tucker_eig_topk(int batch, const int64_t* L, const int64_t* K, const double* const* W,
+                    void* const* F, int f_dtype, void* ws, size_t ws_bytes, void* stream) {
+  if (batch < 1 || !L || !K || !W || !F)
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_eig_topk: invalid argument");
+  std::vector<EigProblem> probs((size_t)batch);
+  for (int b = 0; b < batch; ++b) {
+    if (!W[b] || !F[b]) return fail(TUCKER_ERR_INVALID_ARG, "tucker_eig_topk: NULL matrix");
+    probs[(size_t)b] = EigProblem{W[b], F[b], (int)L[b], (int)K[b]};
+  }
+  return launch_eig_topk(probs.data(), batch, f_dtype, ws, ws_bytes,
+                         static_cast<cudaStream_t>(stream));
+}
+
+int tucker_hooi_sweep(tucker_plan_t plan, const void* T, const void* const* F_in,
+                      void* const* F_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!plan || !T) return fail(TUCKER_ERR_INVALID_ARG, "tucker_hooi_sweep: NULL plan or T");
+  const Plan& p = plan->p;
+  int rc = check_ptrs(F_in, p.N, "tucker_hooi_sweep");
+  if (rc) return rc;
+  rc = check_ptrs(const_cast<const void* const*>(F_out), p.N, "tucker_hooi_sweep");
+  if (rc) return rc;
+  for (int n = 0; n < p.N; ++n)
+    for (int j = 0; j < p.N; ++j)
+      if (F_out[n] == F_in[j])
+        return fail(TUCKER_ERR_INVALID_ARG, "tucker_hooi_sweep: F_out aliases F_in");
+  rc = check_ws(p, ws, ws_bytes, "tucker_hooi_sweep");
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* wsb = static_cast<char*>(ws);
+  const int fdt = factor_dtype(p.dtype);
+  for (size_t i = 1; i < p.nodes.size(); ++i) {
+    const PlanNode& nd = p.nodes[i];
+    const PlanNode& par = p.nodes[(size_t)nd.parent];
+    const bool from_root = nd.parent == 0;
+    const void* in = from_root ? T : (const void*)(wsb + p.off_scratch + par.ws_off);
+    const int in_dt = from_root ? p.dtype : fdt;
+    if (nd.label >= 0) {
+      int64_t R, L, C;
+      view3(par.out_dims, p.N, nd.label, &R, &L, &C);
+      rc = launch_ttm(in_dt, in, R, L, C, F_in[nd.label], p.K[nd.label],
+                      wsb + p.off_scratch + nd.ws_off, s);
+      if (rc) return rc;
+    } else {
+      const int n = -nd.label - 2;
+      int64_t R, L, C;
+      view3(par.out_dims, p.N, n, &R, &L, &C);
+      double* W = reinterpret_cast<double*>(wsb + p.off_gram[n]);
+      TK_CUDA_TRY(cudaMemsetAsync(W, 0, (size_t)L * (size_t)L * sizeof(double), s));
+      rc = launch_gram(in_dt, in, R, L, C, W, s);
+      if (rc) return rc;
+    }
+  }
+  EigProblem probs[kMaxModes];
+  for (int n = 0; n < p.N; ++n)
+    probs[n] = EigProblem{reinterpret_cast<const double*>(wsb + p.off_gram[n]), F_out[n],
+                          (int)p.L[n], (int)p.K[n]};
+  return launch_eig_topk(probs, p.N, fdt, wsb + p.off_eig, p.bytes_eig, s);
+}
+
+int tucker_core(tucker_plan_t plan, const void* T, const void* const* F, void* G, void* ws,
+                size_t ws_bytes, void* stream) {
+  if (!plan || !T || !G) return fail(TUCKER_ERR_INVALID_ARG, "tucker_core: NULL argument");
+  const Plan& p = plan->p;
+  int rc = check_ptrs(F, p.N, "tucker_core");
+  if (rc) return rc;
+  rc = check_ws(p, ws, ws_bytes, "tucker_core");
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* wsb = static_cast<char*>(ws) + p.off_scratch;
+  const int fdt = factor_dtype(p.dtype);
+  // ping-pong buffers sized for the largest intermediate of the chain
+  size_t mx = 0;
+  unsigned P = 0;
+  for (int i = 0; i < p.N; ++i) {
+    P |= 1u << p.core_order[(size_t)i];
+    mx = std::max(mx, (size_t)tensor_size(p, P));
+  }
+  void* buf[2] = {wsb, wsb + align_up(mx * p.inter_bytes())};
+  int64_t dims[kMaxModes];
+  std::memcpy(dims, p.L, sizeof(int64_t) * (size_t)p.N);
+  const void* cur = T;
+  int cur_dt = p.dtype;
+  for (int i = 0; i < p.N; ++i) {
+    const int m = p.core_order[(size_t)i];
+    void* out = (i == p.N - 1) ? G : buf[i & 1];
+    int64_t R, L, C;
+    view3(dims, p.N, m, &R, &L, &C);
+    rc = launch_ttm(cur_dt, cur, R, L, C, F[m], p.K[m], out, s);
+    if (rc) return rc;
+    dims[m] = p.K[m];
+    cur = out;
+    cur_dt = fdt;
+  }
+  return TUCKER_OK;
+}
+
+int tucker_sthosvd(tucker_plan_t plan, const void* T, void* const* F, void* G, void* ws,
+                   size_t ws_bytes, void* stream) {
+  if (!plan || !T || !G) return fail(TUCKER_ERR_INVALID_ARG, "tucker_sthosvd: NULL argument");
+  const Plan& p = plan->p;
+  int rc = check_ptrs(const_cast<const void* const*>(F), p.N, "tucker_sthosvd");
+  if (rc) return rc;
+  rc = check_ws(p, ws, ws_bytes, "tucker_sthosvd");
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* wsb = static_cast<char*>(ws);
+  const int fdt = factor_dtype(p.dtype);
+  size_t mx = 0;
+  unsigned P = 0;
+  for (int n = 0; n < p.N; ++n) {
+    P |= 1u << n;
+    mx = std::max(mx, (size_t)tensor_size(p, P));
+  }
+  void* buf[2] = {wsb + p.off_scratch, wsb + p.off_scratch + align_up(mx * p.inter_bytes())};
+  int64_t dims[kMaxModes];
+  std::memcpy(dims, p.L, sizeof(int64_t) * (size_t)p.N);
+  const void* cur = T;
+  int cur_dt = p.dtype;
+  for (int n = 0; n < p.N; ++n) {
+    int64_t R, L, C;
+    view3(dims, p.N, n, &R, &L, &C);
+    double* W = reinterpret_cast<double*>(wsb + p.off_gram[n]);
+    TK_CUDA_TRY(cudaMemsetAsync(W, 0, (size_t)L * (size_t)L * sizeof(double), s));
+    rc = launch_gram(cur_dt, cur, R, L, C, W, s);
+    if (rc) return rc;
+    EigProblem pr{W, F[n], (int)L, (int)p.K[n]};
+    rc = launch_eig_topk(&pr, 1, fdt, wsb + p.off_eig, p.bytes_eig, s);
+    if (rc) return rc;
+    void* out = (n == p.N - 1) ? G : buf[n & 1];
+    rc = launch_ttm(cur_dt, cur, R, L, C, F[n], p.K[n], out, s);
+    if (rc) return rc;
+    dims[n] = p.K[n];
+    cur = out;
+    cur_dt = fdt;
+  }
+  return TUCKER_OK;
+}
+
+int tucker_norm2(tucker_plan_t plan, const void* T, double* out, void* stream) {
+  if (!plan || !T || !out) return fail(TUCKER_ERR_INVALID_ARG, "tucker_norm2: NULL argument");
+  const Plan& p = plan->p;
+  return launch_norm2(p.dtype, T, (int64_t)tensor_size(p, 0), out,
+                      static_cast<cudaStream_t>(stream));
+}
+
+int tucker_fit(tucker_plan_t plan, const void* G, const double* normT2, double* out,
+               void* stream) {
+  if (!plan || !G || !normT2 || !out)
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_fit: NULL argument");
+  const Plan& p = plan->p;
+  const unsigned full = (1u << p.N) - 1u;
+  return launch_fit(factor_dtype(p.dtype), G, (int64_t)tensor_size(p, full), normT2, out,
+                    static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,144 @@
+// common.cuh -- small device/host helpers shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "internal.h"
+
+#define TK_CUDA_TRY(expr)                                                                \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return ::tk::fail(TUCKER_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// Launch check: a failed launch returns TUCKER_ERR_CUDA with the kernel name.
+#define TK_LAUNCH_CHECK(name)                                                            \
+  do {                                                                                   \
+    cudaError_t _e = cudaGetLastError();                                                 \
+    if (_e != cudaSuccess)                                                               \
+      return ::tk::fail(TUCKER_ERR_CUDA, std::string("launch ") + (name) + ": " +          \
+                                             cudaGetErrorString(_e));                    \
+  } while (0)
+
+namespace tk {
+
+// Accumulator / factor type per storage type: double for FP64 tensors, float
+// otherwise (BF16 and FP32 tensors accumulate in FP32).
+template <typename T>
+struct AccOf {
+  using type = float;
+};
+template <>
+struct AccOf<double> {
+  using type = double;
+};
+
+// bfloat16 storage as raw 16-bit patterns (no dependence on cuda_bf16 types in
+// the ABI); widening is exact: the bf16 bits are the high half of a float.
+struct bf16_t {
+  uint16_t bits;
+};
+
+__device__ __forceinline__ float bf16_to_float(uint16_t b) {
+  return __uint_as_float(((uint32_t)b) << 16);
+}
+
+template <typename T>
+__device__ __forceinline__ typename AccOf<T>::type load_one(const T* p) {
+  return __ldg(p);
+}
+template <>
+__device__ __forceinline__ float load_one<bf16_t>(const bf16_t* p) {
+  return bf16_to_float(__ldg(reinterpret_cast<const unsigned short*>(p)));
+}
+
+// Load VEC consecutive elements (the pointer is VEC*sizeof(T) aligned).
+template <typename T, int VEC>
+struct VecLoad {
+  static __device__ __forceinline__ void run(const T* p, typename AccOf<T>::type* out) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) out[v] = load_one<T>(p + v);
+  }
+};
+template <>
+struct VecLoad<float, 4> {
+  static __device__ __forceinline__ void run(const float* p, float* out) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    out[0] = q.x; out[1] = q.y; out[2] = q.z; out[3] = q.w;
+  }
+};
+template <>
+struct VecLoad<double, 2> {
+  static __device__ __forceinline__ void run(const double* p, double* out) {
+    const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+    out[0] = q.x; out[1] = q.y;
+  }
+};
+template <>
+struct VecLoad<bf16_t, 4> {
+  static __device__ __forceinline__ void run(const bf16_t* p, float* out) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+    out[0] = __uint_as_float(q.x << 16);
+    out[1] = __uint_as_float(q.x & 0xFFFF0000u);
+    out[2] = __uint_as_float(q.y << 16);
+    out[3] = __uint_as_float(q.y & 0xFFFF0000u);
+  }
+};
+
+template <typename T, int VEC>
+struct VecStore {
+  template <typename A>
+  static __device__ __forceinline__ void run(T* p, const A* v) {
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) p[i] = (T)v[i];
+  }
+};
+template <>
+struct VecStore<float, 4> {
+  static __device__ __forceinline__ void run(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct VecStore<double, 2> {
+  static __device__ __forceinline__ void run(double* p, const double* v) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+inline int64_t prod(const int64_t* d, int a, int b) {
+  int64_t p = 1;
+  for (int i = a; i < b; ++i) p *= d[i];
+  return p;
+}
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// ---- launchers implemented in the .cu files --------------------------------
+// Y = X x_n F^T on a tensor viewed as [R][L][C] (R = modes before n, C = modes
+// after n).  x_dtype: TUCKER_F32 / F64 / BF16; F and Y in the factor type.
+int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, const void* F,
+               int64_t K, void* Y, cudaStream_t s);
+// W += Z_(n) Z_(n)^T for Z viewed as [R][L][C] (W must be zeroed first).
+int launch_gram(int z_dtype, const void* Z, int64_t R, int64_t L, int64_t C, double* W,
+                cudaStream_t s);
+// out[0] += sum x^2 (out must be zeroed first)
+int launch_norm2(int dtype, const void* X, int64_t n, double* out, cudaStream_t s);
+// fit from G (factor type) and normT2
+int launch_fit(int g_dtype, const void* G, int64_t n, const double* normT2, double* out,
+               cudaStream_t s);
+
+struct EigProblem {
+  const double* W;  // L x L
+  void* F;          // L x K output
+  int L, K;
+};
+int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, size_t ws_bytes,
+                    cudaStream_t s);
+
+}  // namespace tk

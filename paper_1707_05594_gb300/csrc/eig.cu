@@ -1,0 +1,700 @@
+// eig.cu -- leading-K eigenvectors of symmetric L x L Gram matrices (the EVD
+// step of Sec. 5, which the paper runs with LAPACK's dsyevx: Householder
+// tridiagonalisation, bisection for the wanted eigenvalues, inverse iteration
+// for their eigenvectors, back-transformation).
+//
+// GB300 has little FP64 throughput, so the O(L^3) part runs in FP32 and the
+// answer is then refined in FP64:
+//   stage 1 (one CTA per matrix, FP32, all in shared memory):
+//     Householder tridiagonalisation T = Q^T W Q; multisection bisection on
+//     Sturm counts for the K largest eigenvalues (one warp per eigenvalue, 32
+//     points per step); inverse iteration with partial pivoting for each
+//     eigenvector, re-orthogonalised inside clusters of close eigenvalues;
+//     back-transformation by the stored reflectors  -> V0 (L x K), theta.
+//   refinement (FP64): one or more subspace-iteration steps Y = W V,
+//     Q = orth(Y diag(1/theta)) (classical Gram-Schmidt, twice), then
+//     Rayleigh-Ritz: H = Q^T (W Q), Jacobi on the K x K matrix H, F = Q U.
+//   The result's eigenvectors are sorted by decreasing eigenvalue and each
+//   column's entry of largest magnitude (lowest row on ties) is made positive.
+//
+// One step multiplies the FP32 error of V0 by lambda_{K+1}/lambda_K; the FP64
+// orthogonalisation and Rayleigh-Ritz keep F orthonormal to FP64 accuracy, so
+// the orthonormal-factor identity used for the fit holds.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace tk {
+namespace {
+
+constexpr int kEigThreads = 512;
+constexpr int kEigWarps = kEigThreads / 32;
+constexpr int kMaxEigL = 200;
+constexpr int kMaxEigK = 64;
+constexpr int kMaxBatch = TUCKER_MAX_MODES;
+
+struct EigDesc {
+  const double* W;
+  void* F;
+  float* V0;     // [K][L]
+  float* theta;  // [K]
+  double* Q;     // [K][L]
+  double* Y;     // [K][L]
+  int L, K;
+};
+struct EigBatch {
+  EigDesc d[kMaxBatch];
+  int batch;
+  int inv_warps;  // warps doing inverse iteration in stage 1
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread receives the result.  `red` holds >= 16 floats.
+__device__ float block_sum(float v, float* red) {
+  __syncthreads();  // red may still be read by a previous call
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < kEigWarps; ++i) s += red[i];
+  return s;
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x.
+__device__ int sturm_count(const float* d, const float* e2, int n, float x, float pivmin) {
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int c = q < 0.f;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - e2[i - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
+  }
+  return c;
+}
+
+__device__ __forceinline__ float start_value(int i, int t) {
+  unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)((t + 1) * 40503u);
+  h ^= h >> 13;
+  h *= 0x5bd1e995u;
+  h ^= h >> 15;
+  return 1.0f + 0.5f * ((float)(h & 0xFFFFu) / 65536.0f - 0.5f);
+}
+
+// ---------------------------------------------------------------------------
+// Stage 1: FP32 tridiagonalisation, bisection, inverse iteration, back-transform.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch B) {
+  const EigDesc P = B.d[blockIdx.x];
+  const int n = P.L, K = P.K, LD = n | 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  extern __shared__ __align__(16) float sm[];
+  float* A = sm;            // n x LD
+  float* Zs = A + n * LD;   // K x n
+  float* dv = Zs + K * n;   // n
+  float* ev = dv + n;       // n
+  float* e2 = ev + n;       // n
+  float* tau = e2 + n;      // n
+  float* vv = tau + n;      // n
+  float* pp = vv + n;       // n
+  float* lam = pp + n;      // K
+  float* sj = lam + K;      // K
+  float* red = sj + K;      // 48
+  int* cstart = reinterpret_cast<int*>(red + 48);  // K + 1
+  float* work = reinterpret_cast<float*>(cstart + K + 1);  // inv_warps * 6n
+
+  for (int i = tid; i < n * n; i += kEigThreads) {
+    const int r = i / n, c = i - (i / n) * n;
+    A[r * LD + c] = (float)P.W[i];
+  }
+  __syncthreads();
+
+  // ---- Householder tridiagonalisation (lower), reflectors kept in A ----
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    float part = 0.f;
+    for (int i = 1 + tid; i < m; i += kEigThreads) {
+      const float x = A[(k + 1 + i) * LD + k];
+      part += x * x;
+    }
+    const float xn2 = block_sum(part, red);
+    if (tid == 0) {
+      const float alpha = A[(k + 1) * LD + k];
+      dv[k] = A[k * LD + k];
+      if (xn2 == 0.f) {
+        tau[k] = 0.f;
+        ev[k] = alpha;
+        red[32] = 0.f;
+      } else {
+        const float beta = -copysignf(sqrtf(alpha * alpha + xn2), alpha);
+        tau[k] = (beta - alpha) / beta;
+        red[32] = 1.0f / (alpha - beta);
+        ev[k] = beta;
+      }
+    }
+    __syncthreads();
+    const float tk = tau[k];
+    if (tk == 0.f) continue;  // uniform over the block
+    const float scale = red[32];
+    for (int i = tid; i < m; i += kEigThreads) {
+      float v = 1.f;
+      if (i > 0) {
+        v = A[(k + 1 + i) * LD + k] * scale;
+        A[(k + 1 + i) * LD + k] = v;
+      }
+      vv[i] = v;
+    }
+    __syncthreads();
+    // p = tau * A22 v with tpr threads per row
+    int tpr = 1;
+    while (tpr < 32 && m * tpr * 2 <= kEigThreads) tpr *= 2;
+    {
+      const int row = tid / tpr, sub = tid - (tid / tpr) * tpr;
+      float s = 0.f;
+      if (row < m) {
+        const float* arow = A + (k + 1 + row) * LD + (k + 1);
+        for (int j = sub; j < m; j += tpr) s += arow[j] * vv[j];
+      }
+      for (int o = tpr >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (row < m && sub == 0) pp[row] = tk * s;
+    }
+    __syncthreads();
+    float part2 = 0.f;
+    for (int i = tid; i < m; i += kEigThreads) part2 += pp[i] * vv[i];
+    const float pv = block_sum(part2, red);
+    const float Kc = 0.5f * tk * pv;
+    for (int i = tid; i < m; i += kEigThreads) pp[i] -= Kc * vv[i];
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += kEigThreads) {
+      const int i = idx / m, j = idx - (idx / m) * m;
+      A[(k + 1 + i) * LD + (k + 1 + j)] -= vv[i] * pp[j] + pp[i] * vv[j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      dv[n - 2] = A[(n - 2) * LD + (n - 2)];
+      ev[n - 2] = A[(n - 1) * LD + (n - 2)];
+    }
+    dv[n - 1] = A[(n - 1) * LD + (n - 1)];
+    // Gershgorin interval, scale of T, pivot floor
+    float lo = 3.0e38f, hi = -3.0e38f;
+    for (int i = 0; i < n; ++i) {
+      const float r = (i > 0 ? fabsf(ev[i - 1]) : 0.f) + (i + 1 < n ? fabsf(ev[i]) : 0.f);
+      lo = fminf(lo, dv[i] - r);
+      hi = fmaxf(hi, dv[i] + r);
+    }
+    const float tnorm = fmaxf(fabsf(lo), fabsf(hi));
+    const float pivmin = fmaxf(tnorm * 1e-30f, 1e-36f);
+    red[33] = lo - 1e-6f * tnorm - pivmin;
+    red[34] = hi + 1e-6f * tnorm + pivmin;
+    red[35] = tnorm;
+    red[36] = pivmin;
+  }
+  __syncthreads();
+  for (int i = tid; i + 1 < n; i += kEigThreads) e2[i] = ev[i] * ev[i];
+  __syncthreads();
+  const float glo = red[33], ghi = red[34], tnorm = red[35], pivmin = red[36];
+
+  // ---- multisection bisection: eigenvalue t (descending) = index n-1-t ----
+  for (int t = warp; t < K; t += kEigWarps) {
+    const int j = n - 1 - t;
+    float lo = glo, hi = ghi;
+    for (int it = 0; it < 12; ++it) {
+      const float x = lo + (hi - lo) * ((float)(lane + 1) / 33.0f);
+      const int c = sturm_count(dv, e2, n, x, pivmin);
+      const unsigned mask = __ballot_sync(0xffffffffu, c > j);
+      const int first = mask ? (__ffs(mask) - 1) : 32;
+      const float xl = __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0);
+      const float xh = __shfl_sync(0xffffffffu, x, first < 32 ? first : 31);
+      const float nlo = first > 0 ? xl : lo;
+      const float nhi = first < 32 ? xh : hi;
+      lo = nlo;
+      hi = nhi;
+      if (hi - lo <= 2.4e-7f * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
+    }
+    if (lane == 0) lam[t] = 0.5f * (lo + hi);
+  }
+  __syncthreads();
+
+  // ---- clusters of close eigenvalues ----
+  if (tid == 0) {
+    int nc = 0;
+    for (int t = 0; t < K; ++t)
+      if (t == 0 || lam[t - 1] - lam[t] > 1e-3f * tnorm) cstart[nc++] = t;
+    cstart[nc] = K;
+    red[40] = __int_as_float(nc);
+  }
+  __syncthreads();
+  const int nclust = __float_as_int(red[40]);
+
+  // ---- inverse iteration, one warp per cluster ----
+  if (warp < B.inv_warps) {
+    float* dd = work + warp * 6 * n;
+    float* du = dd + n;
+    float* du2 = du + n;
+    float* dl = du2 + n;
+    float* pv = dl + n;
+    float* x = pv + n;
+    const float eps_piv = fmaxf(1.2e-7f * tnorm, 1e-30f);
+    for (int c = warp; c < nclust; c += B.inv_warps) {
+      for (int t = cstart[c]; t < cstart[c + 1]; ++t) {
+        const float lmb = lam[t];
+        if (lane == 0) {
+          // LU with partial pivoting of T - lmb I (rows i, i+1 may swap)
+          for (int i = 0; i < n; ++i) {
+            dd[i] = dv[i] - lmb;
+            du[i] = (i + 1 < n) ? ev[i] : 0.f;
+            dl[i] = (i + 1 < n) ? ev[i] : 0.f;
+            du2[i] = 0.f;
+            pv[i] = 0.f;
+          }
+          for (int i = 0; i + 1 < n; ++i) {
+            if (fabsf(dd[i]) >= fabsf(dl[i])) {
+              if (dd[i] == 0.f) dd[i] = eps_piv;
+              const float f = dl[i] / dd[i];
+              dl[i] = f;
+              dd[i + 1] -= f * du[i];
+            } else {
+              const float f = dd[i] / dl[i];
+              dd[i] = dl[i];
+              dl[i] = f;
+              const float tmp = du[i];
+              du[i] = dd[i + 1];
+              dd[i + 1] = tmp - f * dd[i + 1];
+              if (i + 2 < n) {
+                du2[i] = du[i + 1];
+                du[i + 1] = -f * du[i + 1];
+              }
+              pv[i] = 1.f;
+            }
+          }
+          for (int i = 0; i < n; ++i)
+            if (fabsf(dd[i]) < eps_piv * 1e-3f) dd[i] = copysignf(eps_piv * 1e-3f, dd[i] == 0.f ? 1.f : dd[i]);
+        }
+        for (int i = lane; i < n; i += 32) x[i] = start_value(i, t);
+        __syncwarp();
+        for (int iter = 0; iter < 3; ++iter) {
+          if (lane == 0) {
+            for (int i = 0; i + 1 < n; ++i) {
+              if (pv[i] == 0.f) {
+                x[i + 1] -= dl[i] * x[i];
+              } else {
+                const float tmp = x[i];
+                x[i] = x[i + 1];
+                x[i + 1] = tmp - dl[i] * x[i];
+              }
+            }
+            x[n - 1] /= dd[n - 1];
+            if (n >= 2) x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / dd[n - 2];
+            for (int i = n - 3; i >= 0; --i)
+              x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / dd[i];
+          }
+          __syncwarp();
+          // normalise (scale by the max first to stay in range), then
+          // orthogonalise against earlier members of the cluster
+          for (int pass = 0; pass < 2; ++pass) {
+            float mx = 0.f;
+            for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(x[i]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (!(mx > 0.f) || !isfinite(mx)) {
+              for (int i = lane; i < n; i += 32) x[i] = start_value(i, t + 7 * iter + 1);
+              mx = 2.f;
+            }
+            const float inv = 1.f / mx;
+            float ss = 0.f;
+            for (int i = lane; i < n; i += 32) {
+              const float y = x[i] * inv;
+              x[i] = y;
+              ss += y * y;
+            }
+            ss = warp_sum(ss);
+            const float rn = rsqrtf(ss);
+            for (int i = lane; i < n; i += 32) x[i] *= rn;
+            __syncwarp();
+            if (pass == 1) break;
+            for (int q = cstart[c]; q < t; ++q) {
+              const float* zq = Zs + q * n;
+              float dt = 0.f;
+              for (int i = lane; i < n; i += 32) dt += zq[i] * x[i];
+              dt = warp_sum(dt);
+              for (int i = lane; i < n; i += 32) x[i] -= dt * zq[i];
+              __syncwarp();
+            }
+          }
+        }
+        for (int i = lane; i < n; i += 32) Zs[t * n + i] = x[i];
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- back-transformation V0 = H_0 ... H_{n-3} Z ----
+  for (int k = n - 3; k >= 0; --k) {
+    const float tk = tau[k];
+    if (tk == 0.f) continue;
+    const int m = n - k - 1;
+    for (int j = warp; j < K; j += kEigWarps) {
+      const float* zj = Zs + j * n + (k + 1);
+      float s = 0.f;
+      for (int i = lane; i < m; i += 32) s += (i == 0 ? 1.f : A[(k + 1 + i) * LD + k]) * zj[i];
+      s = warp_sum(s);
+      if (lane == 0) sj[j] = tk * s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < K * m; idx += kEigThreads) {
+      const int j = idx / m, i = idx - (idx / m) * m;
+      const float v = (i == 0) ? 1.f : A[(k + 1 + i) * LD + k];
+      Zs[j * n + k + 1 + i] -= sj[j] * v;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < K * n; i += kEigThreads) P.V0[i] = Zs[i];
+  for (int t = tid; t < K; t += kEigThreads) P.theta[t] = lam[t];
+}
+
+// ---------------------------------------------------------------------------
+// Out[c][r] = sum_j W[r][j] * In[c][j] in FP64 (In: [K][L], float or double).
+// One warp per row r; lanes split j.
+// ---------------------------------------------------------------------------
+template <typename TIn>
+__global__ void __launch_bounds__(256) eig_wmul_kernel(const EigBatch B, int use_v0) {
+  const EigDesc P = B.d[blockIdx.y];
+  const int n = P.L, K = P.K;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= n) return;
+  const double* wr = P.W + (int64_t)r * n;
+  double* out = P.Y;
+  const TIn* in = use_v0 ? reinterpret_cast<const TIn*>(P.V0) : reinterpret_cast<const TIn*>(P.Q);
+  for (int c0 = 0; c0 < K; c0 += 32) {
+    const int cn = min(32, K - c0);
+    double acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const double w = wr[j];
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < cn) acc[c] = fma(w, (double)in[(int64_t)(c0 + c) * n + j], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      if (c < cn) {
+        const double s = warp_sum(acc[c]);
+        if (lane == 0) out[(int64_t)(c0 + c) * n + r] = s;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Q = orth(Y diag(1/theta)) by classical Gram-Schmidt applied twice, in FP64,
+// column by column in eigenvalue order.  Writes Q.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B) {
+  const EigDesc P = B.d[blockIdx.x];
+  const int n = P.L, K = P.K;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ double dots[kMaxEigK];
+  __shared__ double red[8];
+  double* Q = P.Q;
+  // scaled columns; fall back to V0 when theta is negligible
+  float tmax = 0.f;
+  for (int t = 0; t < K; ++t) tmax = fmaxf(tmax, fabsf(P.theta[t]));
+  for (int i = tid; i < K * n; i += 256) {
+    const int t = i / n;
+    const float th = P.theta[t];
+    Q[i] = (fabsf(th) > 1e-20f * tmax && th != 0.f) ? P.Y[i] / (double)th : (double)P.V0[i];
+  }
+  __syncthreads();
+  for (int j = 0; j < K; ++j) {
+    double* qj = Q + (int64_t)j * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      // dots with the previous columns (warp per column)
+      for (int i = warp; i < j; i += 8) {
+        const double* qi = Q + (int64_t)i * n;
+        double s = 0.0;
+        for (int r = lane; r < n; r += 32) s += qi[r] * qj[r];
+        s = warp_sum(s);
+        if (lane == 0) dots[i] = s;
+      }
+      __syncthreads();
+      for (int r = tid; r < n; r += 256) {
+        double v = qj[r];
+        for (int i = 0; i < j; ++i) v -= dots[i] * Q[(int64_t)i * n + r];
+        qj[r] = v;
+      }
+      __syncthreads();
+    }
+    double s = 0.0;
+    for (int r = tid; r < n; r += 256) s += qj[r] * qj[r];
+    s = warp_sum(s);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < 8; ++w) tot += red[w];
+    const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+    for (int r = tid; r < n; r += 256) qj[r] *= inv;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz: H = Q^T Y (Y = W Q), Jacobi on H (one warp, FP64), F = Q U,
+// sort by decreasing eigenvalue, fix signs, write F (L x K row-major).
+// ---------------------------------------------------------------------------
+template <typename TOut>
+__global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B) {
+  const EigDesc P = B.d[blockIdx.x];
+  const int n = P.L, K = P.K;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  extern __shared__ __align__(16) double dsm[];
+  double* H = dsm;          // K x K
+  double* U = H + K * K;    // K x K
+  double* Fs = U + K * K;   // n x K
+  __shared__ int order[kMaxEigK];
+  __shared__ int flip[kMaxEigK];
+  for (int idx = warp; idx < K * K; idx += 8) {
+    const int a = idx / K, b = idx - (idx / K) * K;
+    const double* qa = P.Q + (int64_t)a * n;
+    const double* yb = P.Y + (int64_t)b * n;
+    double s = 0.0;
+    for (int r = lane; r < n; r += 32) s += qa[r] * yb[r];
+    s = warp_sum(s);
+    if (lane == 0) H[idx] = s;
+  }
+  for (int idx = tid; idx < K * K; idx += 256) U[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int idx = tid; idx < K * K; idx += 256) {
+    const int a = idx / K, b = idx - (idx / K) * K;
+    if (a < b) {
+      const double v = 0.5 * (H[a * K + b] + H[b * K + a]);
+      H[a * K + b] = v;
+      H[b * K + a] = v;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      int rotated = 0;
+      for (int p = 0; p < K - 1; ++p) {
+        for (int q = p + 1; q < K; ++q) {
+          const double apq = H[p * K + q];
+          const double app = H[p * K + p], aqq = H[q * K + q];
+          if (apq == 0.0) continue;
+          if (fabs(apq) <= 1e-17 * sqrt(fabs(app) * fabs(aqq))) {
+            __syncwarp();
+            if (lane == 0) H[p * K + q] = H[q * K + p] = 0.0;
+            __syncwarp();
+            continue;
+          }
+          rotated = 1;
+          const double th = (aqq - app) / (2.0 * apq);
+          const double t = (th >= 0.0) ? 1.0 / (th + sqrt(1.0 + th * th))
+                                       : -1.0 / (-th + sqrt(1.0 + th * th));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+          __syncwarp();
+          for (int k = lane; k < K; k += 32) {
+            const double hkp = H[k * K + p], hkq = H[k * K + q];
+            H[k * K + p] = c * hkp - s * hkq;
+            H[k * K + q] = s * hkp + c * hkq;
+          }
+          __syncwarp();
+          for (int k = lane; k < K; k += 32) {
+            const double hpk = H[p * K + k], hqk = H[q * K + k];
+            H[p * K + k] = c * hpk - s * hqk;
+            H[q * K + k] = s * hpk + c * hqk;
+            const double ukp = U[k * K + p], ukq = U[k * K + q];
+            U[k * K + p] = c * ukp - s * ukq;
+            U[k * K + q] = s * ukp + c * ukq;
+          }
+          __syncwarp();
+          if (lane == 0) H[p * K + q] = H[q * K + p] = 0.0;
+          __syncwarp();
+        }
+      }
+      if (!rotated) break;
+    }
+    if (lane == 0) {
+      for (int i = 0; i < K; ++i) order[i] = i;
+      for (int i = 0; i < K; ++i) {
+        int best = i;
+        for (int j = i + 1; j < K; ++j)
+          if (H[order[j] * K + order[j]] > H[order[best] * K + order[best]]) best = j;
+        const int tmp = order[i];
+        order[i] = order[best];
+        order[best] = tmp;
+      }
+    }
+  }
+  __syncthreads();
+  // F = Q U(:, order)
+  for (int idx = tid; idx < n * K; idx += 256) {
+    const int r = idx / K, c = idx - (idx / K) * K;
+    const int oc = order[c];
+    double s = 0.0;
+    for (int a = 0; a < K; ++a) s += P.Q[(int64_t)a * n + r] * U[a * K + oc];
+    Fs[idx] = s;
+  }
+  __syncthreads();
+  for (int c = warp; c < K; c += 8) {
+    double best = -1.0;
+    int bi = n;
+    for (int r = lane; r < n; r += 32) {
+      const double v = fabs(Fs[r * K + c]);
+      if (v > best) {
+        best = v;
+        bi = r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (lane == 0) flip[c] = (bi < n && Fs[bi * K + c] < 0.0) ? 1 : 0;
+  }
+  __syncthreads();
+  TOut* F = static_cast<TOut*>(P.F);
+  for (int idx = tid; idx < n * K; idx += 256) {
+    const int c = idx - (idx / K) * K;
+    const double v = flip[c] ? -Fs[idx] : Fs[idx];
+    F[idx] = (TOut)v;
+  }
+}
+
+size_t stage1_smem(int L, int K, int inv_warps) {
+  const size_t LD = (size_t)(L | 1);
+  size_t floats = (size_t)L * LD + (size_t)K * L + 6 * (size_t)L + 2 * (size_t)K + 48;
+  size_t bytes = floats * 4 + (size_t)(K + 1) * 4;
+  bytes = (bytes + 15) / 16 * 16;
+  return bytes + (size_t)inv_warps * 6 * L * 4;
+}
+
+int max_smem_optin() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (v <= 0) v = 48 * 1024;
+  }
+  return v;
+}
+
+}  // namespace
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
+int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, size_t ws_bytes,
+                    cudaStream_t s) {
+  if (batch <= 0) return TUCKER_OK;
+  int64_t Ls[kMaxBatch], Ks[kMaxBatch];
+  for (int b0 = 0; b0 < batch; b0 += kMaxBatch) {
+    const int nb = std::min(kMaxBatch, batch - b0);
+    for (int b = 0; b < nb; ++b) {
+      Ls[b] = probs[b0 + b].L;
+      Ks[b] = probs[b0 + b].K;
+      if (Ls[b] < 1 || Ls[b] > kMaxEigL || Ks[b] < 1 || Ks[b] > Ls[b] || Ks[b] > kMaxEigK)
+        return fail(TUCKER_ERR_UNSUPPORTED,
+                    "eig: need 1 <= K <= min(L, 64) and L <= 200 for every matrix");
+    }
+    const size_t need = eig_ws_bytes(nb, Ls, Ks);
+    if (!ws || ws_bytes < need) return fail(TUCKER_ERR_WORKSPACE, "eig: workspace too small");
+    EigBatch EB{};
+    EB.batch = nb;
+    char* p = static_cast<char*>(ws);
+    int maxL = 1, maxK = 1;
+    for (int b = 0; b < nb; ++b) {
+      const EigProblem& pr = probs[b0 + b];
+      EigDesc& d = EB.d[b];
+      const size_t l = (size_t)pr.L, k = (size_t)pr.K;
+      d.W = pr.W;
+      d.F = pr.F;
+      d.L = pr.L;
+      d.K = pr.K;
+      d.V0 = reinterpret_cast<float*>(p);
+      p += align_up(l * k * 4);
+      d.theta = reinterpret_cast<float*>(p);
+      p += align_up(k * 4);
+      d.Q = reinterpret_cast<double*>(p);
+      p += align_up(l * k * 8);
+      d.Y = reinterpret_cast<double*>(p);
+      p += align_up(l * k * 8);
+      maxL = std::max(maxL, pr.L);
+      maxK = std::max(maxK, pr.K);
+    }
+    const int smax = max_smem_optin();
+    const size_t base = stage1_smem(maxL, maxK, 0);
+    const size_t per_warp = (size_t)6 * maxL * 4;
+    if (base + per_warp > (size_t)smax)
+      return fail(TUCKER_ERR_UNSUPPORTED, "eig: matrix too large for shared memory");
+    EB.inv_warps = (int)std::min<size_t>({(size_t)kEigWarps, (size_t)maxK,
+                                          ((size_t)smax - base) / per_warp});
+    const size_t sm1 = stage1_smem(maxL, maxK, EB.inv_warps);
+    TK_CUDA_TRY(cudaFuncSetAttribute(eig_stage1_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    eig_stage1_kernel<<<nb, kEigThreads, sm1, s>>>(EB);
+    TK_LAUNCH_CHECK("eig_stage1");
+    const dim3 gmul((unsigned)((maxL + 7) / 8), (unsigned)nb);
+    // one subspace-iteration step: Y = W V0, Q = orth(Y / theta)
+    eig_wmul_kernel<float><<<gmul, 256, 0, s>>>(EB, 1);
+    TK_LAUNCH_CHECK("eig_wmul");
+    eig_orth_kernel<<<nb, 256, 0, s>>>(EB);
+    TK_LAUNCH_CHECK("eig_orth");
+    if (f_dtype == TUCKER_F64) {
+      // a second step for FP64 factors
+      eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0);
+      TK_LAUNCH_CHECK("eig_wmul");
+      eig_orth_kernel<<<nb, 256, 0, s>>>(EB);
+      TK_LAUNCH_CHECK("eig_orth");
+    }
+    // Rayleigh-Ritz on span(Q): Y = W Q, then the K x K problem
+    eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0);
+    TK_LAUNCH_CHECK("eig_wmul");
+    const size_t sm3 = ((size_t)2 * maxK * maxK + (size_t)maxL * maxK) * 8;
+    if (sm3 > (size_t)smax) return fail(TUCKER_ERR_UNSUPPORTED, "eig: K too large");
+    if (f_dtype == TUCKER_F64) {
+      TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+      eig_finalize_kernel<double><<<nb, 256, sm3, s>>>(EB);
+    } else {
+      TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+      eig_finalize_kernel<float><<<nb, 256, sm3, s>>>(EB);
+    }
+    TK_LAUNCH_CHECK("eig_finalize");
+  }
+  return TUCKER_OK;
+}
+
+}  // namespace tk

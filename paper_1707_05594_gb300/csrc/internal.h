@@ -1,0 +1,65 @@
+// internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tucker.h"
+
+namespace tk {
+
+constexpr int kMaxModes = TUCKER_MAX_MODES;
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+// One node of the TTM-tree (Sec. 3.1).  `P` is the set of modes multiplied on
+// the path from the root down to and including this node, so Out(u) = T[P].
+struct PlanNode {
+  int label = -1;   // mode for internal nodes, -1 root, -(n+2) leaf of F~_n
+  int parent = -1;
+  unsigned P = 0;
+  int64_t out_dims[kMaxModes] = {};
+  uint64_t in_elems = 0, out_elems = 0, macs = 0;
+  size_t ws_off = 0;  // byte offset of Out(u) in the workspace (internal nodes)
+};
+
+struct Plan {
+  int N = 0;
+  int64_t L[kMaxModes] = {}, K[kMaxModes] = {};
+  int dtype = TUCKER_F32;
+  int tree = TUCKER_TREE_OPTIMAL;
+  int cost_model = TUCKER_COST_MACS;
+  std::vector<PlanNode> nodes;  // depth-first pre-order, nodes[0] is the root
+  uint64_t tree_macs = 0, tree_elems = 0;
+  std::vector<int> core_order;  // mode order of the new-core chain
+  uint64_t core_macs = 0;
+
+  // workspace layout (byte offsets)
+  size_t off_scratch = 0, bytes_scratch = 0;  // tree intermediates / chains
+  size_t off_gram[kMaxModes] = {};            // FP64 L_n x L_n
+  size_t off_eig = 0, bytes_eig = 0;          // eigensolver scratch
+  size_t off_misc = 0;                        // small device scalars
+  size_t ws_total = 0;
+
+  size_t elem_bytes() const { return dtype == TUCKER_F64 ? 8 : (dtype == TUCKER_BF16 ? 2 : 4); }
+  // intermediates are computed in the factor type: double for F64, else float
+  size_t inter_bytes() const { return dtype == TUCKER_F64 ? 8 : 4; }
+};
+
+// thread-local error text
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+uint64_t tensor_size(const Plan& p, unsigned P);
+
+// sizes of the eigensolver scratch for a batch of matrices
+size_t eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
+
+}  // namespace tk
+
+struct tucker_plan_s {
+  tk::Plan p;
+};

@@ -1,0 +1,212 @@
+// ttm_simt.cu -- mode-n tensor-times-matrix, Out = In x_n F^T (Sec. 2.1), on
+// the CUDA cores, without unfolding the tensor (the blocked, transposition-free
+// TTM of Sec. 5).
+//
+// The input is viewed as [R][L][C]: R = product of the lengths before mode n,
+// L = L_n, C = product of the lengths after it; the output is [R][K][C] with
+//   Out[r, k, c] = sum_l F[l, k] * In[r, l, c].
+// Two kernels:
+//   ttm_cols  C > 1: each thread owns VEC consecutive (r, c) positions and
+//             all KB outputs of its k-block; it streams In[r, :, c..c+VEC)
+//             (coalesced along c) and reads F from shared memory (broadcast).
+//   ttm_rows  C == 1 (last mode): the fibres are contiguous rows; a block
+//             stages 128 rows x 32 columns in shared memory with coalesced
+//             loads and each thread reduces its own row.
+// Accumulation is FP32 for FP32/BF16 inputs and FP64 for FP64 inputs.
+#include "common.cuh"
+
+namespace tk {
+namespace {
+
+constexpr int kColsThreads = 256;
+constexpr int kColsLChunk = 64;
+
+template <typename TIn, typename TOut, int KB, int VEC>
+__global__ void __launch_bounds__(kColsThreads)
+    ttm_cols_kernel(const TIn* __restrict__ X, const typename AccOf<TIn>::type* __restrict__ F,
+                    TOut* __restrict__ Y, int64_t R, int L, int64_t C, int K) {
+  using A = typename AccOf<TIn>::type;
+  __shared__ __align__(16) A Fs[kColsLChunk][KB];
+  const int kb0 = blockIdx.y * KB;
+  const int64_t total = R * C;
+  const int64_t m0 = ((int64_t)blockIdx.x * kColsThreads + threadIdx.x) * VEC;
+  const bool active = m0 < total;
+  int64_t r = 0, c = 0;
+  if (active) {
+    r = m0 / C;
+    c = m0 - r * C;
+  }
+  const TIn* xp = X + (r * L) * C + c;
+  A acc[KB][VEC];
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[k][v] = A(0);
+
+  for (int l0 = 0; l0 < L; l0 += kColsLChunk) {
+    const int lc = min(kColsLChunk, L - l0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kColsLChunk * KB; i += kColsThreads) {
+      const int l = i / KB, k = i - (i / KB) * KB;
+      Fs[l][k] = (l < lc && kb0 + k < K) ? F[(int64_t)(l0 + l) * K + kb0 + k] : A(0);
+    }
+    __syncthreads();
+    if (active) {
+      const TIn* p = xp + (int64_t)l0 * C;
+      int l = 0;
+      for (; l + 4 <= lc; l += 4) {
+        A x0[VEC], x1[VEC], x2[VEC], x3[VEC];
+        VecLoad<TIn, VEC>::run(p, x0);
+        VecLoad<TIn, VEC>::run(p + C, x1);
+        VecLoad<TIn, VEC>::run(p + 2 * C, x2);
+        VecLoad<TIn, VEC>::run(p + 3 * C, x3);
+        p += 4 * C;
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const A f0 = Fs[l][k], f1 = Fs[l + 1][k], f2 = Fs[l + 2][k], f3 = Fs[l + 3][k];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            acc[k][v] = fma(f0, x0[v], acc[k][v]);
+            acc[k][v] = fma(f1, x1[v], acc[k][v]);
+            acc[k][v] = fma(f2, x2[v], acc[k][v]);
+            acc[k][v] = fma(f3, x3[v], acc[k][v]);
+          }
+        }
+      }
+      for (; l < lc; ++l) {
+        A x0[VEC];
+        VecLoad<TIn, VEC>::run(p, x0);
+        p += C;
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const A f0 = Fs[l][k];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) acc[k][v] = fma(f0, x0[v], acc[k][v]);
+        }
+      }
+    }
+  }
+  if (!active) return;
+  TOut* yp = Y + (r * K + kb0) * C + c;
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    if (kb0 + k < K) {
+      TOut o[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) o[v] = (TOut)acc[k][v];
+      VecStore<TOut, VEC>::run(yp + (int64_t)k * C, o);
+    }
+  }
+}
+
+constexpr int kRowsThreads = 128;
+constexpr int kRowsLChunk = 32;
+
+template <typename TIn, typename TOut, int KB>
+__global__ void __launch_bounds__(kRowsThreads)
+    ttm_rows_kernel(const TIn* __restrict__ X, const typename AccOf<TIn>::type* __restrict__ F,
+                    TOut* __restrict__ Y, int64_t R, int L, int K) {
+  using A = typename AccOf<TIn>::type;
+  __shared__ A Xs[kRowsThreads][kRowsLChunk + 1];
+  __shared__ __align__(16) A Fs[kRowsLChunk][KB];
+  const int kb0 = blockIdx.y * KB;
+  const int64_t r0 = (int64_t)blockIdx.x * kRowsThreads;
+  A acc[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) acc[k] = A(0);
+  for (int l0 = 0; l0 < L; l0 += kRowsLChunk) {
+    const int lc = min(kRowsLChunk, L - l0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRowsThreads * kRowsLChunk; i += kRowsThreads) {
+      const int rr = i / kRowsLChunk, ll = i - rr * kRowsLChunk;
+      const int64_t r = r0 + rr;
+      Xs[rr][ll] = (r < R && ll < lc) ? load_one<TIn>(X + r * L + l0 + ll) : A(0);
+    }
+    for (int i = threadIdx.x; i < kRowsLChunk * KB; i += kRowsThreads) {
+      const int l = i / KB, k = i - (i / KB) * KB;
+      Fs[l][k] = (l < lc && kb0 + k < K) ? F[(int64_t)(l0 + l) * K + kb0 + k] : A(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int l = 0; l < kRowsLChunk; ++l) {
+      const A x = Xs[threadIdx.x][l];
+#pragma unroll
+      for (int k = 0; k < KB; ++k) acc[k] = fma(Fs[l][k], x, acc[k]);
+    }
+  }
+  const int64_t r = r0 + threadIdx.x;
+  if (r >= R) return;
+  TOut* yp = Y + r * K + kb0;
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+    if (kb0 + k < K) yp[k] = (TOut)acc[k];
+}
+
+int pick_kb(int64_t K) {
+  if (K <= 8) return 8;
+  if (K <= 16) return 16;
+  if (K <= 20) return 20;
+  if (K <= 24) return 24;
+  return 32;
+}
+
+template <typename TIn, typename TOut, int KB>
+int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccOf<TIn>::type* F,
+              int64_t K, TOut* Y, cudaStream_t s) {
+  const unsigned gy = (unsigned)((K + KB - 1) / KB);
+  if (C == 1) {
+    const int64_t gx = (R + kRowsThreads - 1) / kRowsThreads;
+    ttm_rows_kernel<TIn, TOut, KB><<<dim3((unsigned)gx, gy), kRowsThreads, 0, s>>>(X, F, Y, R,
+                                                                                   (int)L, (int)K);
+    TK_LAUNCH_CHECK("ttm_rows");
+    return TUCKER_OK;
+  }
+  constexpr int V = sizeof(TIn) == 8 ? 2 : 4;
+  const bool vec_ok = (C % V == 0) && ((uintptr_t)X % (V * sizeof(TIn)) == 0) &&
+                      ((uintptr_t)Y % (V * sizeof(TOut)) == 0);
+  const int64_t total = R * C;
+  if (vec_ok) {
+    const int64_t gx = (total / V + kColsThreads - 1) / kColsThreads;
+    ttm_cols_kernel<TIn, TOut, KB, V><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
+        X, F, Y, R, (int)L, C, (int)K);
+  } else {
+    const int64_t gx = (total + kColsThreads - 1) / kColsThreads;
+    ttm_cols_kernel<TIn, TOut, KB, 1><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
+        X, F, Y, R, (int)L, C, (int)K);
+  }
+  TK_LAUNCH_CHECK("ttm_cols");
+  return TUCKER_OK;
+}
+
+template <typename TIn, typename TOut>
+int launch_typed(const void* X, int64_t R, int64_t L, int64_t C, const void* F, int64_t K,
+                 void* Y, cudaStream_t s) {
+  using A = typename AccOf<TIn>::type;
+  const TIn* x = static_cast<const TIn*>(X);
+  const A* f = static_cast<const A*>(F);
+  TOut* y = static_cast<TOut*>(Y);
+  switch (pick_kb(K)) {
+    case 8: return launch_kb<TIn, TOut, 8>(x, R, L, C, f, K, y, s);
+    case 16: return launch_kb<TIn, TOut, 16>(x, R, L, C, f, K, y, s);
+    case 20: return launch_kb<TIn, TOut, 20>(x, R, L, C, f, K, y, s);
+    case 24: return launch_kb<TIn, TOut, 24>(x, R, L, C, f, K, y, s);
+    default: return launch_kb<TIn, TOut, 32>(x, R, L, C, f, K, y, s);
+  }
+}
+
+}  // namespace
+
+int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, const void* F,
+               int64_t K, void* Y, cudaStream_t s) {
+  if (R * C == 0 || K == 0) return TUCKER_OK;
+  if (R * C / kColsThreads >= (int64_t)INT32_MAX || L > INT32_MAX || K > INT32_MAX)
+    return fail(TUCKER_ERR_UNSUPPORTED, "ttm: tensor too large for the grid");
+  switch (x_dtype) {
+    case TUCKER_F32: return launch_typed<float, float>(X, R, L, C, F, K, Y, s);
+    case TUCKER_F64: return launch_typed<double, double>(X, R, L, C, F, K, Y, s);
+    case TUCKER_BF16: return launch_typed<bf16_t, float>(X, R, L, C, F, K, Y, s);
+    default: return fail(TUCKER_ERR_INVALID_ARG, "ttm: unknown dtype");
+  }
+}
+
+}  // namespace tk

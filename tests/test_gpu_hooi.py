@@ -1,0 +1,227 @@
+"""Parity of whole STHOSVD / HOOI sweeps / core / fit on the GPU with the FP64
+oracle (Fig. 2), on seeded planted-Tucker inputs.
+
+Bars (FP32 path): relative fit difference <= 1e-5 and largest principal angle
+between GPU and oracle factor subspaces <= 1e-4 rad.  The FP64 path is held to
+1e-9 / 1e-7.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tk():
+    from paper_1707_05594_gb300 import build
+    build.build()
+    import paper_1707_05594_gb300 as pkg
+    pkg.lib()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return pkg
+
+
+def sin_angle(A, B):
+    Qa, _ = np.linalg.qr(A)
+    Qb, _ = np.linalg.qr(B)
+    s = np.linalg.norm(Qb - Qa @ (Qa.T @ Qb), 2)
+    return math.asin(min(1.0, s))
+
+
+def align_signs(Fg, Fo):
+    """Flip GPU columns to match the oracle's orientation (dot product sign)."""
+    out = []
+    for A, B in zip(Fg, Fo):
+        s = np.sign(np.einsum("ij,ij->j", A, B))
+        s[s == 0] = 1
+        out.append(A * s)
+    return out
+
+
+def bars(dtype):
+    return (1e-9, 1e-7) if dtype == torch.float64 else (1e-5, 1e-4)
+
+
+CASES = [
+    # L, K, rho, seed, dtype, tree
+    ((24, 20, 18), (4, 3, 5), 0.5, 7, torch.float32, 0),
+    ((30, 30, 30), (6, 4, 5), 1.0, 8, torch.float32, 0),        # hard: fit moves across sweeps
+    ((16, 12, 10, 9), (3, 4, 2, 3), 0.3, 9, torch.float32, 0),
+    ((16, 12, 10, 9), (3, 4, 2, 3), 0.3, 9, torch.float32, 1),  # naive chains
+    ((16, 12, 10, 9), (3, 4, 2, 3), 0.3, 9, torch.float32, 4),  # balanced
+    ((10, 9, 8, 7, 6), (3, 3, 2, 2, 2), 0.2, 10, torch.float32, 0),
+    ((64, 64, 64), (8, 8, 8), 1e-3, 1, torch.float64, 0),        # the 64^3 FP64 workload
+    ((20, 17, 15), (5, 4, 6), 0.6, 12, torch.float64, 0),
+    ((33, 45), (7, 7), 0.4, 13, torch.float32, 0),               # N = 2
+    ((12, 10, 8), (12, 10, 8), 0.1, 14, torch.float32, 0),       # full rank
+]
+
+
+def run_gpu(tk, T, K, tree, sweeps):
+    d = tk.Decomposition(T.cuda(), K, tree=tree)
+    d.sthosvd()
+    out = [([f.double().cpu().numpy() for f in d.F], d.G.double().cpu().numpy(), d.fit())]
+    for _ in range(sweeps):
+        d.sweep()
+        out.append(([f.double().cpu().numpy() for f in d.F], d.G.double().cpu().numpy(), d.fit()))
+    torch.cuda.synchronize()
+    return out, d
+
+
+@pytest.mark.parametrize("L,K,rho,seed,dtype,tree", CASES)
+def test_sweeps_match_oracle(tk, orc, L, K, rho, seed, dtype, tree):
+    w = workloads.planted_tucker(L, K, rho, seed, dtype=dtype)
+    T = w["T"]
+    Tn = T.numpy()
+    sweeps = 3
+    gpu, _ = run_gpu(tk, T, K, tree, sweeps)
+    fit_bar, ang_bar = bars(dtype)
+    nT2 = orc.norm2(Tn)
+    F_o, G_o = orc.sthosvd(Tn, K)
+    ref = [(F_o, G_o)]
+    for _ in range(sweeps):
+        F_o, G_o = orc.hooi_sweep(Tn, F_o, K)
+        ref.append((F_o, G_o))
+    for s, ((Fg, Gg, fit_g), (Fo, Go)) in enumerate(zip(gpu, ref)):
+        fit_o = orc.fit(nT2, orc.norm2(Go))
+        assert abs(fit_g - fit_o) <= fit_bar * abs(fit_o), (s, fit_g, fit_o)
+        for n in range(len(L)):
+            if K[n] < L[n]:
+                assert sin_angle(Fg[n], Fo[n]) <= ang_bar, (s, n)
+            assert np.abs(Fg[n].T @ Fg[n] - np.eye(K[n])).max() <= (1e-12 if dtype == torch.float64 else 1e-6)
+
+
+def test_sweep_from_common_input_factors(tk, orc):
+    """One sweep from the same input factors on both sides: isolates the
+    sweep from STHOSVD, and checks core entries after sign alignment."""
+    L, K = (28, 22, 19, 9), (5, 4, 6, 3)
+    w = workloads.planted_tucker(L, K, 0.7, 21, dtype=torch.float32)
+    T = w["T"]
+    F0, _ = orc.sthosvd(T.numpy(), K)
+    F0 = [np.asarray(f, dtype=np.float32) for f in F0]
+    Fo, Go = orc.hooi_sweep(T.numpy(), [f.astype(np.float64) for f in F0], K)
+    plan = tk.tucker_plan(L, K)
+    ws = tk.workspace(plan)
+    Fin = [torch.tensor(f, device="cuda") for f in F0]
+    Fout = [torch.empty_like(f) for f in Fin]
+    G = torch.empty(*K, dtype=torch.float32, device="cuda")
+    tk.tucker_hooi_sweep(plan, T.cuda(), Fin, Fout, ws)
+    tk.tucker_core(plan, T.cuda(), Fout, G, ws)
+    torch.cuda.synchronize()
+    Fg = [f.double().cpu().numpy() for f in Fout]
+    for n in range(4):
+        assert sin_angle(Fg[n], Fo[n]) <= 1e-4
+    # the core in the oracle's basis: G' = T x F_o^T computed from GPU factors
+    # aligned to the oracle's signs must match the oracle core
+    Fa = align_signs(Fg, Fo)
+    Ga = orc.core(T.numpy(), Fa)
+    Gg = G.double().cpu().numpy()
+    Gref = orc.core(T.numpy(), Fg)
+    np.testing.assert_allclose(Gg, Gref, rtol=0, atol=1e-5 * np.abs(Gref).max())
+    np.testing.assert_allclose(Ga, Go, rtol=0, atol=1e-3 * np.abs(Go).max())
+
+
+def test_fit_monotone_on_gpu(tk, orc):
+    L, K = (30, 26, 22), (6, 5, 4)
+    w = workloads.planted_tucker(L, K, 0.9, 31, dtype=torch.float32)
+    gpu, _ = run_gpu(tk, w["T"], K, 0, 6)
+    fits = [g[2] for g in gpu]
+    assert all(b >= a - 1e-6 * a for a, b in zip(fits, fits[1:])), fits
+
+
+def test_zero_noise_recovers_planted_subspaces(tk):
+    L, K = (40, 36, 30), (5, 6, 4)
+    w = workloads.planted_tucker(L, K, 0.0, 41, dtype=torch.float32)
+    gpu, _ = run_gpu(tk, w["T"], K, 0, 1)
+    Fg, _, fit = gpu[-1]
+    for n in range(3):
+        assert sin_angle(Fg[n], w["F"][n].numpy()) <= 1e-5
+    assert fit >= 1 - 1e-3
+
+
+def test_norm_and_fit_kernels(tk, orc):
+    T = workloads.random_tensor((50, 41, 33), seed=3, dtype=torch.float32)
+    plan = tk.tucker_plan(T.shape, (5, 4, 3))
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    tk.tucker_norm2(plan, T.cuda(), out)
+    ref = orc.norm2(T.numpy())
+    G = workloads.random_tensor((5, 4, 3), seed=4, dtype=torch.float32).cuda()
+    fo = torch.empty(2, dtype=torch.float64, device="cuda")
+    tk.tucker_fit(plan, G, out, fo)
+    torch.cuda.synchronize()
+    assert abs(out.item() - ref) <= 1e-6 * ref
+    g2 = orc.norm2(G.cpu().numpy())
+    assert abs(fo[1].item() - g2) <= 1e-6 * g2
+    assert abs(fo[0].item() - orc.fit(ref, g2)) <= 1e-9
+
+
+def test_workspace_errors(tk):
+    plan = tk.tucker_plan((8, 8, 8), (2, 2, 2))
+    T = torch.zeros(8, 8, 8, device="cuda")
+    F = [torch.zeros(8, 2, device="cuda") for _ in range(3)]
+    Fo = [torch.zeros(8, 2, device="cuda") for _ in range(3)]
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tk.TuckerError) as e:
+        tk.tucker_hooi_sweep(plan, T, F, Fo, small)
+    assert e.value.code == -3
+    ws = tk.workspace(plan)
+    with pytest.raises(tk.TuckerError) as e:
+        tk.tucker_hooi_sweep(plan, T, F, F, ws)
+    assert e.value.code == -1
+
+
+def test_full_size_fp32_workload(tk, orc):
+    """The 200^4 FP32 workload at full size, with the bench's launch
+    configuration: sampled TTM outputs of both root TTMs against oracle dot
+    products, the core against the oracle's core from the GPU factors, the
+    fit, orthonormality and recovery of the planted subspaces."""
+    if torch.cuda.get_device_properties(0).total_memory < 40e9:
+        pytest.skip("needs a large GPU")
+    spec = workloads.WORKLOADS["big_fp32"]
+    w = workloads.make_workload("big_fp32", device="cuda")
+    T = w["T"]
+    L, K = spec["L"], spec["K"]
+    d = tk.Decomposition(T, K)
+    d.sthosvd()
+    d.sweep()
+    torch.cuda.synchronize()
+    Fg = [f.double().cpu().numpy() for f in d.F]
+    Gg = d.G.double().cpu().numpy()
+    fit_g = d.fit()
+    # orthonormal factors, planted subspaces recovered to the noise level
+    for n in range(4):
+        assert np.abs(Fg[n].T @ Fg[n] - np.eye(K[n])).max() <= 1e-6
+        assert sin_angle(Fg[n], w["F"][n].cpu().numpy()) <= 2e-3
+    # sampled root-TTM outputs (modes 0 and 2, as the planner's tree starts)
+    rng = np.random.default_rng(0)
+    for n in (0, 2):
+        out_shape = list(L)
+        out_shape[n] = K[n]
+        Y = torch.empty(out_shape, dtype=torch.float32, device="cuda")
+        Fn = d.F[n]
+        tk.tucker_ttm(T, n, Fn, Y)
+        torch.cuda.synchronize()
+        idx = [rng.integers(0, s, size=64) for s in out_shape]
+        Fd = Fn.double().cpu().numpy()
+        for i in range(64):
+            pos = [int(ix[i]) for ix in idx]
+            sl = list(pos)
+            sl[n] = slice(None)
+            fib = T[tuple(sl)].double().cpu().numpy()
+            k = pos[n]
+            ref = float(np.dot(Fd[:, k], fib))
+            bnd = float(np.dot(np.abs(Fd[:, k]), np.abs(fib))) * (L[n] + 2) * 2.0 ** -24
+            assert abs(Y[tuple(pos)].item() - ref) <= bnd + 1e-30
+        del Y
+    # the oracle's core from the GPU's factors, and the fit from it
+    Th = T.cpu().numpy()
+    G_ref = orc.core(Th, Fg)
+    np.testing.assert_allclose(Gg, G_ref, rtol=0, atol=1e-5 * np.abs(G_ref).max())
+    fit_ref = orc.fit(orc.norm2(Th), orc.norm2(G_ref))
+    assert abs(fit_g - fit_ref) <= 1e-5 * fit_ref

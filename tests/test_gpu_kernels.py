@@ -1,0 +1,178 @@
+"""Parity of the individual CUDA kernels (through the C ABI) with the FP64
+oracle: TTM (Sec. 2.1), Gram (Sec. 5), leading eigenvectors (Sec. 5 EVD).
+
+Tolerances are rounding-error bounds of the arithmetic, not fitted numbers:
+an FP32 dot product of length L accumulated with fused multiply-adds is within
+(L + 2) * 2^-24 * sum |a_i b_i| of the exact value (FP64: 2^-53).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+U32, U64 = 2.0 ** -24, 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def tk():
+    from paper_1707_05594_gb300 import build
+    build.build()
+    import paper_1707_05594_gb300 as pkg
+    pkg.lib()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return pkg
+
+
+def sin_angle(A, B):
+    Qa, _ = np.linalg.qr(A)
+    Qb, _ = np.linalg.qr(B)
+    s = np.linalg.norm(Qb - Qa @ (Qa.T @ Qb), 2)
+    return math.asin(min(1.0, s))
+
+
+TTM_CASES = [
+    # shape, mode, K -- ragged tails, C == 1, odd C, K > 32 (k-blocking), L > 64 (l-chunks)
+    ((37, 29, 11), 0, 5), ((37, 29, 11), 1, 7), ((37, 29, 11), 2, 3),
+    ((5, 200, 12), 1, 20), ((300, 65), 1, 16), ((3, 7, 5, 6), 2, 2),
+    ((257, 33), 0, 40), ((1, 130, 1), 1, 8), ((9, 8, 7, 6, 5), 3, 6),
+    ((200, 4, 50), 0, 24), ((13, 1, 17), 1, 1), ((64, 64, 64), 2, 8),
+]
+
+
+@pytest.mark.parametrize("shape,n,K", TTM_CASES)
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16"])
+def test_ttm_matches_oracle(tk, orc, shape, n, K, dtype):
+    tdt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[dtype]
+    X = workloads.random_tensor(shape, seed=sum(shape) + n, dtype=tdt)
+    fdt = torch.float64 if dtype == "f64" else torch.float32
+    F = workloads.random_factor(shape[n], K, seed=K, dtype=fdt, orthonormal=False)
+    out_shape = list(shape)
+    out_shape[n] = K
+    Y = torch.empty(out_shape, dtype=fdt, device="cuda")
+    tk.tucker_ttm(X.cuda(), n, F.cuda(), Y)
+    torch.cuda.synchronize()
+    Xd = X.double().numpy()
+    Fd = F.double().numpy()
+    ref = orc.ttm(Xd, n, Fd.T)
+    bound = orc.ttm(np.abs(Xd), n, np.abs(Fd).T)
+    u = U64 if dtype == "f64" else U32
+    err = np.abs(Y.double().cpu().numpy() - ref)
+    assert np.all(err <= (shape[n] + 2) * u * bound + 1e-300), err.max()
+
+
+@pytest.mark.parametrize("shape,n", [((37, 29, 11), 0), ((37, 29, 11), 1), ((37, 29, 11), 2),
+                                     ((130, 700), 0), ((700, 130), 1), ((3, 200, 41), 1),
+                                     ((20, 20, 20, 200), 3), ((5, 6, 7), 1)])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_gram_matches_oracle(tk, orc, shape, n, dtype):
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    Z = workloads.random_tensor(shape, seed=len(shape) * 7 + n, dtype=tdt)
+    L = shape[n]
+    W = torch.empty(L, L, dtype=torch.float64, device="cuda")
+    tk.tucker_gram(Z.cuda(), n, W)
+    torch.cuda.synchronize()
+    Zd = Z.double().numpy()
+    ref = orc.gram(Zd, n)
+    bound = orc.gram(np.abs(Zd), n)
+    # FP32 products summed in FP32 runs of 256 columns, runs summed in FP64
+    u = U64 * (Zd.size // L + 2) if dtype == "f64" else U32 * (256 + 2) + U64 * (Zd.size // L)
+    err = np.abs(W.cpu().numpy() - ref)
+    assert np.all(err <= u * bound + 1e-300), (err / (bound + 1e-300)).max()
+    Wc = W.cpu().numpy()
+    assert np.array_equal(Wc, Wc.T)
+
+
+def spectrum_matrix(L, evals, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((L, L)))
+    return (Q * evals) @ Q.T
+
+
+EIG_CASES = [
+    (16, 4, "rand"), (37, 5, "rand"), (64, 8, "rand"), (64, 16, "decay"), (96, 12, "decay"),
+    (200, 20, "decay"), (50, 10, "cluster"), (20, 20, "rand"), (1, 1, "rand"), (2, 1, "rand"),
+    (128, 64, "rand"), (33, 3, "lowrank"),
+]
+
+
+@pytest.mark.parametrize("L,K,kind", EIG_CASES)
+@pytest.mark.parametrize("fdt", [torch.float32, torch.float64])
+def test_eig_topk_matches_oracle(tk, orc, L, K, kind, fdt):
+    rng = np.random.default_rng(L * 100 + K)
+    if kind == "rand":
+        M = rng.standard_normal((L, L + 3))
+        W = M @ M.T
+    elif kind == "decay":
+        ev = np.concatenate([1.0 / np.arange(1, K + 1) ** 2, 1e-6 * rng.random(L - K)])
+        W = spectrum_matrix(L, ev, L)
+    elif kind == "cluster":
+        ev = np.concatenate([[3, 2, 2, 2, 2, 1, 1, 1, 0.5, 0.4], 0.01 * rng.random(L - 10)])
+        W = spectrum_matrix(L, ev, L)
+    else:  # rank 5 < L
+        M = rng.standard_normal((L, 5))
+        W = M @ M.T
+    W = 0.5 * (W + W.T)
+    evals, V, _ = orc.jacobi_eig(W)
+    Wg = torch.tensor(W, dtype=torch.float64, device="cuda")
+    F = torch.empty(L, K, dtype=fdt, device="cuda")
+    ws = torch.empty(tk.tucker_eig_ws_bytes([L], [K]), dtype=torch.uint8, device="cuda")
+    tk.tucker_eig_topk([Wg], [F], ws)
+    torch.cuda.synchronize()
+    Fc = F.double().cpu().numpy()
+    orth = 1e-12 if fdt == torch.float64 else 1e-6
+    assert np.abs(Fc.T @ Fc - np.eye(K)).max() <= orth
+    gap = evals[K - 1] - (evals[K] if K < L else -np.inf)
+    if gap > 1e-6 * evals[0]:
+        # subspace of the leading K eigenvectors (unique when the gap is open).
+        # Error model of the method: the FP32 stage leaves ~n*eps32*lambda_1/gap,
+        # each FP64 subspace-iteration step multiplies it by lambda_{K+1}/lambda_K
+        # (one step for FP32 factors, two for FP64), and the output rounding adds
+        # its own floor.
+        ratio = evals[K] / evals[K - 1] if K < L else 0.0
+        steps = 2 if fdt == torch.float64 else 1
+        stage1 = L * U32 * evals[0] / gap
+        floor = 1e-12 if fdt == torch.float64 else 4 * U32
+        assert sin_angle(Fc, V[:, :K]) <= stage1 * max(ratio, 0.0) ** steps + floor
+        # individual columns where the eigenvalue is simple: same vector incl. sign
+        for j in range(K):
+            lo = evals[j - 1] - evals[j] if j > 0 else np.inf
+            hi = evals[j] - evals[j + 1] if j + 1 < L else np.inf
+            if min(lo, hi) > 1e-3 * evals[0]:
+                assert np.abs(Fc[:, j] - V[:, j]).max() <= 1e-4, j
+    # Rayleigh quotients equal the leading eigenvalues
+    rq = np.einsum("ij,ij->j", Fc, W @ Fc)
+    u = 1e-12 if fdt == torch.float64 else 8 * U32
+    np.testing.assert_allclose(rq, evals[:K], rtol=0, atol=u * evals[0] + 1e-300)
+
+
+def test_eig_batch_of_uneven_sizes(tk, orc):
+    rng = np.random.default_rng(5)
+    sizes = [(16, 4), (96, 16), (37, 9), (64, 8), (50, 6)]
+    Ws, Fs, refs = [], [], []
+    for L, K in sizes:
+        M = rng.standard_normal((L, L))
+        W = M @ M.T
+        Ws.append(torch.tensor(W, device="cuda"))
+        Fs.append(torch.empty(L, K, dtype=torch.float32, device="cuda"))
+        refs.append(orc.jacobi_eig(W)[1][:, :K])
+    ws = torch.empty(tk.tucker_eig_ws_bytes([s[0] for s in sizes], [s[1] for s in sizes]),
+                     dtype=torch.uint8, device="cuda")
+    tk.tucker_eig_topk(Ws, Fs, ws)
+    torch.cuda.synchronize()
+    for F, R in zip(Fs, refs):
+        assert sin_angle(F.double().cpu().numpy(), R) <= 1e-4
+
+
+def test_eig_rejects_oversize(tk):
+    W = torch.zeros(256, 256, dtype=torch.float64, device="cuda")
+    F = torch.empty(256, 4, dtype=torch.float32, device="cuda")
+    ws = torch.empty(tk.tucker_eig_ws_bytes([256], [4]), dtype=torch.uint8, device="cuda")
+    with pytest.raises(tk.TuckerError) as e:
+        tk.tucker_eig_topk([W], [F], ws)
+    assert e.value.code == -2

@@ -1,0 +1,151 @@
+"""CPU-side checks of the library: it loads, exports every symbol declared in
+include/tucker.h, and its host planner (no device work) agrees with the
+planner oracle.  No kernel is launched here."""
+import os
+import random
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tk():
+    from paper_1707_05594_gb300 import build
+    build.build()
+    import paper_1707_05594_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "tucker.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(tucker_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(tk):
+    import ctypes
+    L = ctypes.CDLL(tk.LIB_PATH)
+    names = declared_symbols()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version_and_error_text(tk):
+    assert tk.tucker_version() >= 100
+    with pytest.raises(tk.TuckerError) as e:
+        tk.tucker_plan((4, 4), (5, 2))
+    assert "K_n" in str(e.value)
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("L,K,msg", [((4,), (2,), "N must"), ((4, 4), (0, 2), "K_n"),
+                                     ((6, 6, 6), (6, 1, 1), "product of the other"),
+                                     ((2 ** 14, 2 ** 14, 2 ** 13), (2, 2, 2), "2^40")])
+def test_plan_validation(tk, L, K, msg):
+    with pytest.raises(tk.TuckerError) as e:
+        tk.tucker_plan(L, K)
+    assert msg in str(e.value)
+
+
+def tree_of(tk, plan):
+    nodes = tk.tucker_plan_nodes(plan)
+    return [n["label"] for n in nodes], [n["parent"] for n in nodes], nodes
+
+
+def test_optimal_tree_matches_oracle_dp_and_bruteforce(tk, orc):
+    rnd = random.Random(3)
+    for trial in range(120):
+        N = rnd.choice([2, 3, 4, 5])
+        L = [rnd.choice([2, 3, 5, 8, 20, 50]) for _ in range(N)]
+        K = [rnd.randint(1, l) for l in L]
+        try:
+            plan = tk.tucker_plan(L, K)
+        except tk.TuckerError:
+            continue  # rank-deficient core (K_n > prod of the others)
+        labels, parents, nodes = tree_of(tk, plan)
+        cost = orc.tree_cost(L, K, labels, parents)
+        assert cost is not None, (L, K, labels, parents)
+        assert cost == tk.tucker_plan_cost(plan)["tree_macs"]
+        assert cost == orc.tree_dp(L, K), (L, K)
+        if N <= 4:
+            assert cost == orc.tree_bruteforce(L, K)[1]
+        # every internal node has at most 2 children (Lemma 3.1 trees are binary)
+        for i in range(len(labels)):
+            assert sum(1 for p in parents if p == i) <= 2
+
+
+@pytest.mark.parametrize("tree,fn", [(1, "chain"), (2, "chain_k"), (3, "chain_h"), (4, "balanced")])
+def test_prior_scheme_trees_match_oracle(tk, orc, tree, fn):
+    rnd = random.Random(11 + tree)
+    for trial in range(40):
+        N = rnd.choice([3, 4, 5, 6])
+        L = [rnd.choice([3, 5, 20, 50, 100]) for _ in range(N)]
+        K = [max(1, l // rnd.choice([1, 2, 5, 10])) for l in L]
+        try:
+            plan = tk.tucker_plan(L, K, tree=tree)
+        except tk.TuckerError:
+            continue
+        labels, parents, _ = tree_of(tk, plan)
+        cost = orc.tree_cost(L, K, labels, parents)
+        assert cost is not None
+        if fn == "chain":
+            ref = orc.chain_cost(L, K)
+        elif fn == "chain_k":
+            ref = orc.chain_cost(L, K, orc.k_order(L, K))
+        elif fn == "chain_h":
+            ref = orc.chain_cost(L, K, orc.h_order(L, K))
+        else:
+            ref = orc.balanced_cost(L, K)
+        assert cost == ref
+        assert cost >= orc.tree_dp(L, K)
+
+
+def test_workload_tree_costs(tk, orc):
+    # the benchmark shapes: the planner's optimum equals the oracle DP, and the
+    # chain/optimal load ratios are those of the enumeration
+    cases = [((200,) * 4, (20,) * 4), ((64,) * 5, (16,) * 5),
+             ((64, 56, 48, 40, 32, 24), (16, 14, 12, 10, 8, 6)), ((64,) * 3, (8,) * 3)]
+    for L, K in cases:
+        plan = tk.tucker_plan(L, K)
+        c = tk.tucker_plan_cost(plan)
+        assert c["tree_macs"] == orc.tree_dp(L, K)
+        labels, parents, _ = tree_of(tk, plan)
+        assert orc.tree_cost(L, K, labels, parents) == c["tree_macs"]
+
+
+def test_memory_plan_is_a_stack(tk):
+    """A node's output buffer must not overlap any buffer on its root path
+    (they are all live while the node runs)."""
+    for L, K in [((200,) * 4, (20,) * 4), ((64,) * 5, (16,) * 5), ((9, 8, 7, 6, 5), (3, 2, 4, 1, 2))]:
+        plan = tk.tucker_plan(L, K, dtype=tk.TUCKER_F32)
+        _, _, nodes = tree_of(tk, plan)
+        ws = tk.tucker_plan_cost(plan)["ws_bytes"]
+        for i, nd in enumerate(nodes):
+            if nd["label"] < 0:
+                continue
+            a0, a1 = nd["ws_offset"], nd["ws_offset"] + 4 * nd["out_elems"]
+            assert a1 <= ws
+            p = nd["parent"]
+            while p > 0:
+                q = nodes[p]
+                b0, b1 = q["ws_offset"], q["ws_offset"] + 4 * q["out_elems"]
+                assert a1 <= b0 or b1 <= a0, (i, p)
+                p = q["parent"]
+
+
+def test_elems_cost_model(tk, orc):
+    # the elements-moved objective never moves more elements than the MAC tree
+    for L, K in [((672, 672, 627, 16), (279, 279, 153, 14)),
+                 ((500, 500, 500, 11, 10), (81, 129, 127, 7, 6))]:
+        pm = tk.tucker_plan(L, K)
+        pe = tk.tucker_plan(L, K, cost_model=tk.COST_ELEMS)
+        cm, ce = tk.tucker_plan_cost(pm), tk.tucker_plan_cost(pe)
+        assert ce["tree_elems"] <= cm["tree_elems"]
+        assert cm["tree_macs"] <= ce["tree_macs"]
+        labels, parents, _ = tree_of(tk, pe)
+        assert orc.tree_cost(L, K, labels, parents) == ce["tree_macs"]
