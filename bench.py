@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""HOOI benchmark on GB300: sweeps/s of the planted 200^4 FP32 workload.
+
+One step = one HOOI sweep (all N new factors along the optimal TTM-tree, the
+new core and the fit: tucker_hooi_sweep + tucker_core + tucker_fit), inputs
+resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain C chain-tree HOOI of
+the oracle package) on the host cores, on a bounded sample of the same
+workload, and reports the same metric.  N > 1 (torchrun) runs independent
+replicas, one per GPU: the path has no exchange step to shard.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HOOI sweeps/s + first-TTM GB/s vs HBM peak; BF16 vs FP32 form at equal fit error"
+UNIT = "sweeps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="big_fp32")
+    ap.add_argument("--tree", default="optimal",
+                    choices=["optimal", "chain", "chain_k", "chain_h", "balanced"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+TREES = {"optimal": 0, "chain": 1, "chain_k": 2, "chain_h": 3, "balanced": 4}
+
+
+# ----------------------------------------------------------------- env -----
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# ------------------------------------------------------------- clocks ------
+class ClockSampler:
+    """Samples SM clock, power and clock-event reasons through NVML (read-only
+    queries) in a background thread during the timed region."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device_index=0):
+        self.samples = []
+        self.ok = False
+        self.max_mhz = None
+        try:
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nv.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            got = False
+            try:
+                import torch
+                uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+                if not uuid.startswith("GPU-"):
+                    uuid = "GPU-" + uuid
+                got = self.nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) == 0
+            except Exception:
+                got = False
+            if not got and self.nv.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(self.h)) != 0:
+                return
+            mx = ctypes.c_uint()
+            if self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+            self.ok = True
+        except OSError:
+            self.ok = False
+
+    def _one(self):
+        c, r, p = ctypes.c_uint(), ctypes.c_ulonglong(), ctypes.c_uint()
+        if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c)) != 0:
+            return
+        fn = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        fn(self.h, ctypes.byref(r))
+        self.nv.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(p))
+        self.samples.append((c.value, r.value, p.value / 1000.0))
+
+    def _run(self):
+        while not self._stop.is_set():
+            self._one()
+            time.sleep(0.002)
+
+    def start(self):
+        if not self.ok:
+            return
+        self._stop = threading.Event()
+        self._one()
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+
+    def stop(self):
+        if not self.ok:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvml unavailable"]}
+        self._stop.set()
+        self._t.join()
+        self._one()
+        mhz = [s[0] for s in self.samples]
+        reasons = set()
+        for _, r, _ in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(mhz),
+                "power_w_max": max(s[2] for s in self.samples)}
+
+
+# ------------------------------------------------------- CPU baseline -------
+def oracle_sample(T_host, K, factors):
+    """Bounded sample of the oracle's sweep on the 200^4 workload: the chain of
+    new factor 0 (T x_1 F_1^T x_2 F_2^T x_3 F_3^T on the full tensor), its Gram
+    and Jacobi EVD, and the last step of the new-core chain (x_0).  Every mode
+    of this workload has the same lengths, so each of the N chains costs the
+    same as chain 0 and the core chain is chain 0 plus x_0: one sweep takes
+    N*(chain + Gram + EVD) + chain + x_0."""
+    import numpy as np
+
+    import oracle
+    N = T_host.ndim
+    F = [np.ascontiguousarray(f, dtype=np.float64) for f in factors]
+    t0 = time.perf_counter()
+    Z = T_host
+    for j in range(1, N):
+        Z = oracle.ttm(Z, j, F[j].T)
+    t1 = time.perf_counter()
+    W = oracle.gram(Z, 0)
+    t2 = time.perf_counter()
+    oracle.jacobi_eig(W)
+    t3 = time.perf_counter()
+    oracle.ttm(Z, 0, F[0].T)
+    t4 = time.perf_counter()
+    chain, gram, evd, x0 = t1 - t0, t2 - t1, t3 - t2, t4 - t3
+    sweep_s = N * (chain + gram + evd) + chain + x0
+    return {"sample_s": t4 - t0, "sweep_s_est": sweep_s, "parts": {
+        "chain_ttms_s": chain, "gram_s": gram, "evd_s": evd, "core_x0_s": x0}}
+
+
+SAMPLE_TEXT = ("oracle (plain C, FP64 arithmetic on the FP32 tensor, OpenMP) on the full "
+               "200^4 tensor: chain of factor 0 (3 TTMs) + its Gram + Jacobi EVD + core step x_0, "
+               "timed once; sweep time = 4*(chain+Gram+EVD) + chain + x_0 (all modes equal)")
+
+
+# ------------------------------------------------------------ our arm ------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ttm_simt.cu",):
+        h.update(open(os.path.join(ROOT, "paper_1707_05594_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(key):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(key)
+    if not d or d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("bytes_per_launch")
+
+
+def run_ours(args, ws_size, rank):
+    import torch
+
+    import paper_1707_05594_gb300 as tk
+    import workloads
+    from paper_1707_05594_gb300 import build as tkbuild
+    tkbuild.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = workloads.WORKLOADS[args.workload]
+    L, K = spec["L"], spec["K"]
+    w = workloads.make_workload(args.workload, device=dev)
+    T = w["T"]
+    del w
+    torch.cuda.synchronize()
+    d = tk.Decomposition(T, K, tree=TREES[args.tree])
+    d.sthosvd()
+    torch.cuda.synchronize()
+    nodes = tk.tucker_plan_nodes(d.plan)
+    cost = tk.tucker_plan_cost(d.plan)
+    for _ in range(args.warmup):
+        d.sweep()
+    torch.cuda.synchronize()
+    # per-node event ring for the timed region
+    per_step = len(nodes) + 1 + d.plan.N
+    cap = per_step * args.steps + 8
+    tk.tucker_profile_enable(d.plan, cap)
+    sampler = ClockSampler(torch.cuda.current_device())
+    s = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws_size)
+    torch.cuda.synchronize()
+    launches0 = tk.tucker_launch_count()
+    sampler.start()
+    ev0.record(s)
+    for _ in range(args.steps):
+        d.sweep()
+    ev1.record(s)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = tk.tucker_launch_count() - launches0
+    barrier(ws_size)
+    ms = ev0.elapsed_time(ev1)
+    recs = tk.tucker_profile_read(d.plan, cap)
+    tk.tucker_profile_enable(d.plan, 0)
+    ms_max = max_over_ranks(ms, ws_size)
+    fit = d.fit()
+
+    # roofline of the dominant kernel: the root TTMs (they read all of T)
+    esz = T.element_size()
+    root_nodes = {i: nd for i, nd in enumerate(nodes) if nd["parent"] == 0 and nd["label"] >= 0}
+    byts, tms, durs = 0.0, 0.0, []
+    node_ms = {}
+    for node, label, t in recs:
+        node_ms.setdefault(node, []).append(t)
+        if node in root_nodes:
+            nd = root_nodes[node]
+            byts += nd["in_elems"] * esz + nd["out_elems"] * 4
+            tms += t
+            durs.append(t)
+    pk = peaks()
+    achieved = byts / (tms / 1e3) / 1e9 if tms > 0 else None
+    n_root = len(root_nodes)
+    first = min(root_nodes)
+    bytes_per_launch = (root_nodes[first]["in_elems"] * esz + root_nodes[first]["out_elems"] * 4)
+    traffic = traffic_from_profiles(f"ttm_root_{args.workload}")
+    total_node_ms = {str(k): round(sum(v) / len(v), 5) for k, v in sorted(node_ms.items())}
+
+    # end to end through the public API with host buffers
+    e2e_steps = max(1, args.e2e_steps)
+    T_host = torch.empty(T.shape, dtype=T.dtype, pin_memory=True)
+    T_host.copy_(T)
+    F_host = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in d.F]
+    G_host = torch.empty(d.G.shape, dtype=d.G.dtype, pin_memory=True)
+    fit_host = torch.empty(2, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    barrier(ws_size)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(e2e_steps):
+        T.copy_(T_host, non_blocking=True)
+        d.sweep()
+        for fh, fd in zip(F_host, d.F):
+            fh.copy_(fd, non_blocking=True)
+        G_host.copy_(d.G, non_blocking=True)
+        fit_host.copy_(d.fit_out, non_blocking=True)
+    e1.record(s)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, ws_size)
+    h2d = T.numel() * esz
+    d2h = sum(f.numel() * f.element_size() for f in d.F) + d.G.numel() * d.G.element_size() + 16
+
+    out = {
+        "metric": METRIC, "value": round(args.steps * ws_size / (ms_max / 1e3), 3), "unit": UNIT,
+        "n_gpus": ws_size, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: planted Tucker {'x'.join(map(str, L))} "
+                               f"{str(T.dtype).replace('torch.', '')}, ranks {'x'.join(map(str, K))}, "
+                               f"rho={spec['rho']}, seed {spec['seed']}",
+                   "tree": args.tree, "tree_macs": cost["tree_macs"],
+                   "core_macs": cost["core_macs"], "step": "hooi_sweep + core + fit",
+                   "l2": "inputs exceed L2 (tensor 6.4 GB >> 129 MB), no flush",
+                   "parallelism": "replicas" if ws_size > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "root TTM (ttm_cols, reads all of T)",
+                     "achieved": round(achieved, 1) if achieved else None,
+                     "peak": pk["hbm_gbs"], "peak_src": pk["src"], "unit": "GB/s",
+                     "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "launches_timed": len(durs), "avg_launch_ms": round(tms / max(1, len(durs)), 4)},
+        "first_ttm": {"gbs": round(achieved, 1) if achieved else None,
+                      "frac_of_hbm": round(achieved / pk["hbm_gbs"], 4) if achieved else None},
+        "node_avg_ms": total_node_ms,
+        "fit": fit,
+        "e2e": {"value": round(ws_size * 1e3 / e2e_ms, 3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and ws_size == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        Th = T_host.numpy()
+        Fh = [f.double().numpy() for f in F_host]
+        r = oracle_sample(Th, K, Fh)
+        out["cpu_baseline"] = {"value": round(1.0 / r["sweep_s_est"], 6), "unit": UNIT,
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": SAMPLE_TEXT, "sample_s": round(r["sample_s"], 2),
+                               "parts_s": {k: round(v, 3) for k, v in r["parts"].items()}}
+    return out
+
+
+# ------------------------------------------------------ reference arm ------
+def run_reference(args, ws_size, rank):
+    """The FP64 CPU oracle on the host cores, on the same workload and metric.
+    Each step is the bounded sample described in SAMPLE_TEXT."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads
+    oracle.build()
+    spec = workloads.WORKLOADS[args.workload]
+    if args.workload != "big_fp32":
+        return {"impl": "reference", "unavailable": "reference sample defined for big_fp32 only"}
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    w = workloads.make_workload(args.workload, device=dev)
+    Th = w["T"].cpu().numpy()
+    Fs = [f.cpu().numpy() for f in w["F"]]
+    del w
+    if dev == "cuda":
+        torch.cuda.empty_cache()
+    K = spec["K"]
+    for _ in range(args.warmup):
+        oracle_sample(Th, K, Fs)
+    t0 = time.perf_counter()
+    ests = []
+    for _ in range(args.steps):
+        ests.append(oracle_sample(Th, K, Fs)["sweep_s_est"])
+    wall = time.perf_counter() - t0
+    sweep_s = statistics.mean(ests)
+    v = round(1.0 / sweep_s, 6)
+    return {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws_size, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(sweep_s * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"{args.workload}: planted Tucker "
+                               f"{'x'.join(map(str, spec['L']))} float32 values, "
+                               f"ranks {'x'.join(map(str, K))}", "tree": "chain (oracle)",
+                   "step": "bounded sample, extrapolated to one sweep"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": SAMPLE_TEXT},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(wall, 2),
+    }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # rank 0 alone times the oracle; other ranks exit without work
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        out = run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), rank)
+        print(json.dumps(out), flush=True)
+        return 0
+    ws_size, rank, local = dist_setup()
+    out = run_ours(args, ws_size, rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws_size > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

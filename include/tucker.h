@@ -164,6 +164,28 @@ int tucker_eig_topk(int batch, const int64_t* L, const int64_t* K, const double*
                     void* const* F, int f_dtype, void* ws, size_t ws_bytes, void* stream);
 size_t tucker_eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
 
+/* Per-node CUDA-event timing of a plan's calls (tracing).  While enabled,
+ * tucker_hooi_sweep records a start/end event pair on its stream around each
+ * tree node's launches (node = index in tucker_plan_nodes order, label = its
+ * mode, or -(n+2) for the Gram of leaf n) and around the batched eigensolver
+ * (node = -1), and tucker_core around each chain step (node = -2, label =
+ * mode).  Recording stops when `capacity` pairs are used.  capacity = 0
+ * disables profiling and frees the events. */
+typedef struct {
+  int32_t node;
+  int32_t label;
+  float ms;
+} tucker_prof_rec_t;
+int tucker_profile_enable(tucker_plan_t plan, int capacity);
+/* Waits for the recorded events, copies at most `capacity` records (in
+ * recording order), sets *n_recs to the number recorded, and empties the
+ * ring.  recs may be NULL. */
+int tucker_profile_read(tucker_plan_t plan, tucker_prof_rec_t* recs, int capacity, int* n_recs);
+
+/* Number of kernels this library has launched in this process (all threads,
+ * all plans); a monotone counter for accounting. */
+uint64_t tucker_launch_count(void);
+
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* tucker_last_error(void);
 

@@ -48,6 +48,10 @@ class Node(ctypes.Structure):
                 ("macs", ctypes.c_uint64), ("ws_offset", ctypes.c_uint64)]
 
 
+class ProfRec(ctypes.Structure):
+    _fields_ = [("node", ctypes.c_int32), ("label", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
 def lib():
     """Load libtucker_gb300.so (raises if it has not been built)."""
     global _lib
@@ -81,6 +85,10 @@ def lib():
                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
     L.tucker_eig_ws_bytes.argtypes = [ctypes.c_int, _i64p, _i64p]
     L.tucker_eig_ws_bytes.restype = ctypes.c_size_t
+    L.tucker_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.tucker_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(ProfRec), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]
+    L.tucker_launch_count.restype = ctypes.c_uint64
     L.tucker_last_error.restype = ctypes.c_char_p
     L.tucker_version.restype = ctypes.c_int
     _lib = L
@@ -242,6 +250,24 @@ def tucker_eig_topk(Ws: Sequence, Fs: Sequence, ws, stream=None):
     _check(lib().tucker_eig_topk(len(Ws), _i64(Ls), _i64(Ks), _ptrs(Ws), _ptrs(Fs),
                                  _dtype_code(Fs[0]), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                  _stream(stream)), "tucker_eig_topk")
+
+
+def tucker_profile_enable(plan: Plan, capacity: int) -> None:
+    _check(lib().tucker_profile_enable(plan.handle, int(capacity)), "tucker_profile_enable")
+
+
+def tucker_profile_read(plan: Plan, capacity: int) -> List[tuple]:
+    """[(node, label, ms), ...] in recording order (at most `capacity`);
+    waits for the events and empties the ring."""
+    arr = (ProfRec * max(1, capacity))()
+    n = ctypes.c_int()
+    _check(lib().tucker_profile_read(plan.handle, arr, capacity, ctypes.byref(n)),
+           "tucker_profile_read")
+    return [(arr[i].node, arr[i].label, arr[i].ms) for i in range(min(n.value, capacity))]
+
+
+def tucker_launch_count() -> int:
+    return int(lib().tucker_launch_count())
 
 
 def tucker_last_error() -> str:

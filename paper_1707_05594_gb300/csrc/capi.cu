@@ -3,6 +3,7 @@
 // output reused by all its children), forms the Gram of each leaf's input
 // (Sec. 5), solves the N eigenproblems in one batched launch, and runs the
 // new-core chain, STHOSVD, norms and fit.
+#include <atomic>
 #include <cstring>
 #include <string>
 
@@ -36,7 +37,40 @@ int check_ptrs(const void* const* F, int N, const char* who) {
   return TUCKER_OK;
 }
 
+// Per-node event timing: record a start event before a node's launches and
+// an end event after them, while the ring has room.
+struct ProfScope {
+  Plan& p;
+  cudaStream_t s;
+  int slot = -1;
+  ProfScope(Plan& pp, cudaStream_t ss, int node, int label) : p(pp), s(ss) {
+    if (p.prof_cap > 0 && p.prof_n < p.prof_cap) {
+      slot = p.prof_n++;
+      p.prof_node[(size_t)slot] = node;
+      p.prof_label[(size_t)slot] = label;
+      cudaEventRecord(static_cast<cudaEvent_t>(p.prof_events[2 * (size_t)slot]), s);
+    }
+  }
+  ~ProfScope() {
+    if (slot >= 0) cudaEventRecord(static_cast<cudaEvent_t>(p.prof_events[2 * (size_t)slot + 1]), s);
+  }
+};
+
+std::atomic<uint64_t> g_launches{0};
+
 }  // namespace
+
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void destroy_profile(Plan& p) {
+  for (void* e : p.prof_events)
+    if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
+  p.prof_events.clear();
+  p.prof_node.clear();
+  p.prof_label.clear();
+  p.prof_cap = p.prof_n = 0;
+}
+
 }  // namespace tk
 
 using namespace tk;
@@ -103,6 +137,7 @@ int tucker_hooi_sweep(tucker_plan_t plan, const void* T, const void* const* F_in
     const bool from_root = nd.parent == 0;
     const void* in = from_root ? T : (const void*)(wsb + p.off_scratch + par.ws_off);
     const int in_dt = from_root ? p.dtype : fdt;
+    ProfScope prof(plan->p, s, (int)i, nd.label);
     if (nd.label >= 0) {
       int64_t R, L, C;
       view3(par.out_dims, p.N, nd.label, &R, &L, &C);
@@ -123,8 +158,55 @@ int tucker_hooi_sweep(tucker_plan_t plan, const void* T, const void* const* F_in
   for (int n = 0; n < p.N; ++n)
     probs[n] = EigProblem{reinterpret_cast<const double*>(wsb + p.off_gram[n]), F_out[n],
                           (int)p.L[n], (int)p.K[n]};
+  ProfScope prof(plan->p, s, -1, -1);
   return launch_eig_topk(probs, p.N, fdt, wsb + p.off_eig, p.bytes_eig, s);
 }
+
+int tucker_profile_enable(tucker_plan_t plan, int capacity) {
+  if (!plan || capacity < 0) return fail(TUCKER_ERR_INVALID_ARG, "tucker_profile_enable");
+  Plan& p = plan->p;
+  destroy_profile(p);
+  if (capacity == 0) return TUCKER_OK;
+  p.prof_events.assign(2 * (size_t)capacity, nullptr);
+  p.prof_node.assign((size_t)capacity, 0);
+  p.prof_label.assign((size_t)capacity, 0);
+  for (auto& e : p.prof_events) {
+    cudaEvent_t ev;
+    const cudaError_t err = cudaEventCreate(&ev);
+    if (err != cudaSuccess) {
+      destroy_profile(p);
+      return fail(TUCKER_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(err));
+    }
+    e = ev;
+  }
+  p.prof_cap = capacity;
+  p.prof_n = 0;
+  return TUCKER_OK;
+}
+
+int tucker_profile_read(tucker_plan_t plan, tucker_prof_rec_t* recs, int capacity, int* n_recs) {
+  if (!plan || !n_recs) return fail(TUCKER_ERR_INVALID_ARG, "tucker_profile_read");
+  Plan& p = plan->p;
+  int n = 0;
+  for (int i = 0; i < p.prof_n; ++i) {
+    cudaEvent_t a = static_cast<cudaEvent_t>(p.prof_events[2 * (size_t)i]);
+    cudaEvent_t b = static_cast<cudaEvent_t>(p.prof_events[2 * (size_t)i + 1]);
+    TK_CUDA_TRY(cudaEventSynchronize(b));
+    float ms = 0.f;
+    TK_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+    if (recs && n < capacity) {
+      recs[n].node = p.prof_node[(size_t)i];
+      recs[n].label = p.prof_label[(size_t)i];
+      recs[n].ms = ms;
+    }
+    ++n;
+  }
+  *n_recs = n;
+  p.prof_n = 0;
+  return TUCKER_OK;
+}
+
+uint64_t tucker_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int tucker_core(tucker_plan_t plan, const void* T, const void* const* F, void* G, void* ws,
                 size_t ws_bytes, void* stream) {
@@ -154,6 +236,7 @@ int tucker_core(tucker_plan_t plan, const void* T, const void* const* F, void* G
     void* out = (i == p.N - 1) ? G : buf[i & 1];
     int64_t R, L, C;
     view3(dims, p.N, m, &R, &L, &C);
+    ProfScope prof(plan->p, s, -2, m);
     rc = launch_ttm(cur_dt, cur, R, L, C, F[m], p.K[m], out, s);
     if (rc) return rc;
     dims[m] = p.K[m];

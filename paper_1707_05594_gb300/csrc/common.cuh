@@ -15,9 +15,11 @@
       return ::tk::fail(TUCKER_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
   } while (0)
 
-// Launch check: a failed launch returns TUCKER_ERR_CUDA with the kernel name.
+// Launch check: a failed launch returns TUCKER_ERR_CUDA with the kernel name;
+// a successful one is counted (tucker_launch_count).
 #define TK_LAUNCH_CHECK(name)                                                            \
   do {                                                                                   \
+    ::tk::count_launches(1);                                                             \
     cudaError_t _e = cudaGetLastError();                                                 \
     if (_e != cudaSuccess)                                                               \
       return ::tk::fail(TUCKER_ERR_CUDA, std::string("launch ") + (name) + ": " +          \

@@ -44,6 +44,11 @@ struct Plan {
   size_t off_misc = 0;                        // small device scalars
   size_t ws_total = 0;
 
+  // per-node CUDA-event timing (opaque cudaEvent_t pairs; see tucker_profile_*)
+  int prof_cap = 0, prof_n = 0;
+  std::vector<void*> prof_events;  // 2 * prof_cap events
+  std::vector<int> prof_node, prof_label;
+
   size_t elem_bytes() const { return dtype == TUCKER_F64 ? 8 : (dtype == TUCKER_BF16 ? 2 : 4); }
   // intermediates are computed in the factor type: double for F64, else float
   size_t inter_bytes() const { return dtype == TUCKER_F64 ? 8 : 4; }
@@ -57,6 +62,12 @@ uint64_t tensor_size(const Plan& p, unsigned P);
 
 // sizes of the eigensolver scratch for a batch of matrices
 size_t eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
+
+// releases the plan's profiling events (defined with the executor)
+void destroy_profile(Plan& p);
+
+// number of kernels this library has launched (all threads)
+void count_launches(uint64_t n);
 
 }  // namespace tk
 

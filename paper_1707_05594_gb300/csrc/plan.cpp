@@ -394,7 +394,11 @@ int tucker_plan_nodes(tucker_plan_t plan, tucker_node_t* nodes, int capacity, in
   return TUCKER_OK;
 }
 
-void tucker_plan_destroy(tucker_plan_t plan) { delete plan; }
+void tucker_plan_destroy(tucker_plan_t plan) {
+  if (!plan) return;
+  destroy_profile(plan->p);
+  delete plan;
+}
 
 size_t tucker_eig_ws_bytes(int batch, const int64_t* L, const int64_t* K) {
   if (batch <= 0 || !L || !K) return 0;

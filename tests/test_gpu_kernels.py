@@ -84,8 +84,10 @@ def test_gram_matches_oracle(tk, orc, shape, n, dtype):
     u = U64 * (Zd.size // L + 2) if dtype == "f64" else U32 * (256 + 2) + U64 * (Zd.size // L)
     err = np.abs(W.cpu().numpy() - ref)
     assert np.all(err <= u * bound + 1e-300), (err / (bound + 1e-300)).max()
+    # split-K partials are added with FP64 atomics, whose order differs between
+    # W[a, b] and W[b, a]: symmetric up to that rounding
     Wc = W.cpu().numpy()
-    assert np.array_equal(Wc, Wc.T)
+    assert np.all(np.abs(Wc - Wc.T) <= 2 * u * bound + 1e-300)
 
 
 def spectrum_matrix(L, evals, seed):
