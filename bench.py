@@ -43,7 +43,48 @@ def parse():
                     choices=["optimal", "chain", "chain_k", "chain_h", "balanced"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttm", default=None,
+                    help="time one TTM kernel alone: 'L0,L1,...:mode:K[:f32|bf16|f64]' "
+                         "(kernel studies and small ncu captures)")
     return ap.parse_args()
+
+
+def run_ttm_only(args):
+    """Times tucker_ttm on one shape (the kernel a root node of the tree runs)."""
+    import torch
+
+    import paper_1707_05594_gb300 as tk
+    import workloads
+    from paper_1707_05594_gb300 import build as tkbuild
+    tkbuild.build()
+    parts = args.ttm.split(":")
+    dims = tuple(int(x) for x in parts[0].split(","))
+    n, K = int(parts[1]), int(parts[2])
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[
+        parts[3] if len(parts) > 3 else "f32"]
+    X = workloads.random_tensor(dims, seed=1, dtype=dt, device="cuda")
+    fdt = torch.float64 if dt == torch.float64 else torch.float32
+    F = workloads.random_factor(dims[n], K, seed=2, dtype=fdt, device="cuda")
+    out = list(dims)
+    out[n] = K
+    Y = torch.empty(out, dtype=fdt, device="cuda")
+    for _ in range(args.warmup):
+        tk.tucker_ttm(X, n, F, Y)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        tk.tucker_ttm(X, n, F, Y)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    byts = X.numel() * X.element_size() + Y.numel() * Y.element_size()
+    pk = peaks()
+    return {"kernel": "tucker_ttm", "shape": list(dims), "mode": n, "K": K,
+            "dtype": str(dt).replace("torch.", ""), "ms": round(ms, 5),
+            "gbs": round(byts / ms / 1e6, 1), "frac_of_hbm": round(byts / ms / 1e6 / pk["hbm_gbs"], 4),
+            "steps": args.steps, "warmup": args.warmup}
 
 
 TREES = {"optimal": 0, "chain": 1, "chain_k": 2, "chain_h": 3, "balanced": 4}
@@ -405,6 +446,9 @@ def main():
         print(json.dumps(out), flush=True)
         return 0
     ws_size, rank, local = dist_setup()
+    if args.ttm:
+        print(json.dumps(run_ttm_only(args)), flush=True)
+        return 0
     out = run_ours(args, ws_size, rank)
     if rank == 0:
         print(json.dumps(out), flush=True)

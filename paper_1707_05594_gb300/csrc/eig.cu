@@ -29,6 +29,11 @@ namespace {
 
 constexpr int kEigThreads = 512;
 constexpr int kEigWarps = kEigThreads / 32;
+// inverse iteration: per-lane arrays (LU of T - lambda I and the iterate),
+// interleaved [i][lane] with a padded stride so lanes and rows are both
+// conflict-free
+constexpr int kInvArrays = 6;
+constexpr int kInvLD = 33;
 constexpr int kMaxEigL = 200;
 constexpr int kMaxEigK = 64;
 constexpr int kMaxBatch = TUCKER_MAX_MODES;
@@ -38,6 +43,7 @@ struct EigDesc {
   void* F;
   float* V0;     // [K][L]
   float* theta;  // [K]
+  float* HV;     // [L][L] parked reflectors
   double* Q;     // [K][L]
   double* Y;     // [K][L]
   int L, K;
@@ -45,7 +51,6 @@ struct EigDesc {
 struct EigBatch {
   EigDesc d[kMaxBatch];
   int batch;
-  int inv_warps;  // warps doing inverse iteration in stage 1
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -100,8 +105,12 @@ __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch 
   const int n = P.L, K = P.K, LD = n | 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   extern __shared__ __align__(16) float sm[];
+  // region 0 holds A during the tridiagonalisation and the back-transform,
+  // and the per-lane inverse-iteration arrays in between (the reflectors are
+  // parked in global scratch meanwhile)
+  const int reg0 = max(n * LD, kInvArrays * n * kInvLD);
   float* A = sm;            // n x LD
-  float* Zs = A + n * LD;   // K x n
+  float* Zs = sm + reg0;    // K x n
   float* dv = Zs + K * n;   // n
   float* ev = dv + n;       // n
   float* e2 = ev + n;       // n
@@ -112,7 +121,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch 
   float* sj = lam + K;      // K
   float* red = sj + K;      // 48
   int* cstart = reinterpret_cast<int*>(red + 48);  // K + 1
-  float* work = reinterpret_cast<float*>(cstart + K + 1);  // inv_warps * 6n
+  int* clus_of = cstart + K + 1;                   // K: start index of t's cluster
 
   for (int i = tid; i < n * n; i += kEigThreads) {
     const int r = i / n, c = i - (i / n) * n;
@@ -156,7 +165,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch 
       vv[i] = v;
     }
     __syncthreads();
-    // p = tau * A22 v with tpr threads per row
+    // p = tau * A22 v with tpr threads per row; only the lower triangle of
+    // A22 is kept, so entries above the diagonal are read from their mirror
     int tpr = 1;
     while (tpr < 32 && m * tpr * 2 <= kEigThreads) tpr *= 2;
     {
@@ -164,7 +174,24 @@ __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch 
       float s = 0.f;
       if (row < m) {
         const float* arow = A + (k + 1 + row) * LD + (k + 1);
-        for (int j = sub; j < m; j += tpr) s += arow[j] * vv[j];
+        const float* acol = A + (k + 1) * LD + (k + 1 + row);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int j = sub;
+        for (; j + 3 * tpr <= row; j += 4 * tpr) {
+          s0 += arow[j] * vv[j];
+          s1 += arow[j + tpr] * vv[j + tpr];
+          s2 += arow[j + 2 * tpr] * vv[j + 2 * tpr];
+          s3 += arow[j + 3 * tpr] * vv[j + 3 * tpr];
+        }
+        for (; j <= row; j += tpr) s0 += arow[j] * vv[j];
+        for (; j + 3 * tpr < m; j += 4 * tpr) {
+          s0 += acol[j * LD] * vv[j];
+          s1 += acol[(j + tpr) * LD] * vv[j + tpr];
+          s2 += acol[(j + 2 * tpr) * LD] * vv[j + 2 * tpr];
+          s3 += acol[(j + 3 * tpr) * LD] * vv[j + 3 * tpr];
+        }
+        for (; j < m; j += tpr) s0 += acol[j * LD] * vv[j];
+        s = (s0 + s1) + (s2 + s3);
       }
       for (int o = tpr >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (row < m && sub == 0) pp[row] = tk * s;
@@ -176,9 +203,12 @@ __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch 
     const float Kc = 0.5f * tk * pv;
     for (int i = tid; i < m; i += kEigThreads) pp[i] -= Kc * vv[i];
     __syncthreads();
-    for (int idx = tid; idx < m * m; idx += kEigThreads) {
-      const int i = idx / m, j = idx - (idx / m) * m;
-      A[(k + 1 + i) * LD + (k + 1 + j)] -= vv[i] * pp[j] + pp[i] * vv[j];
+    // rank-2 update of the lower triangle: warp w takes rows w, w+16, ...
+    for (int i = warp; i < m; i += kEigWarps) {
+      const float vi = vv[i], wi = pp[i];
+      float* arow = A + (k + 1 + i) * LD + (k + 1);
+#pragma unroll 4
+      for (int j = lane; j <= i; j += 32) arow[j] -= vi * pp[j] + wi * vv[j];
     }
     __syncthreads();
   }
@@ -230,115 +260,155 @@ __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch 
 
   // ---- clusters of close eigenvalues ----
   if (tid == 0) {
-    int nc = 0;
-    for (int t = 0; t < K; ++t)
-      if (t == 0 || lam[t - 1] - lam[t] > 1e-3f * tnorm) cstart[nc++] = t;
+    int nc = 0, cs = 0;
+    for (int t = 0; t < K; ++t) {
+      if (t == 0 || lam[t - 1] - lam[t] > 1e-3f * tnorm) {
+        cs = t;
+        cstart[nc++] = t;
+      }
+      clus_of[t] = cs;
+    }
     cstart[nc] = K;
-    red[40] = __int_as_float(nc);
+  }
+  // park the reflectors (rows >= column + 2 of A) in global scratch: region 0
+  // holds the inverse-iteration arrays until the back-transformation
+  for (int idx = tid; idx < n * n; idx += kEigThreads) {
+    const int r = idx / n, c = idx - (idx / n) * n;
+    if (r >= c + 2) P.HV[idx] = A[r * LD + c];
   }
   __syncthreads();
-  const int nclust = __float_as_int(red[40]);
 
-  // ---- inverse iteration, one warp per cluster ----
-  if (warp < B.inv_warps) {
-    float* dd = work + warp * 6 * n;
-    float* du = dd + n;
-    float* du2 = du + n;
-    float* dl = du2 + n;
-    float* pv = dl + n;
-    float* x = pv + n;
+  // ---- inverse iteration: lane u of warp 0 iterates eigenvector t0 + u ----
+  if (warp == 0) {
+    float* dd = sm;
+    float* du = dd + n * kInvLD;
+    float* du2 = du + n * kInvLD;
+    float* dl = du2 + n * kInvLD;
+    float* pv = dl + n * kInvLD;
+    float* x = pv + n * kInvLD;
     const float eps_piv = fmaxf(1.2e-7f * tnorm, 1e-30f);
-    for (int c = warp; c < nclust; c += B.inv_warps) {
-      for (int t = cstart[c]; t < cstart[c + 1]; ++t) {
+    for (int t0 = 0; t0 < K; t0 += 32) {
+      const int kr = min(32, K - t0);
+      const bool act = lane < kr;
+      const int t = t0 + lane;
+      if (act) {
         const float lmb = lam[t];
-        if (lane == 0) {
-          // LU with partial pivoting of T - lmb I (rows i, i+1 may swap)
-          for (int i = 0; i < n; ++i) {
-            dd[i] = dv[i] - lmb;
-            du[i] = (i + 1 < n) ? ev[i] : 0.f;
-            dl[i] = (i + 1 < n) ? ev[i] : 0.f;
-            du2[i] = 0.f;
-            pv[i] = 0.f;
-          }
-          for (int i = 0; i + 1 < n; ++i) {
-            if (fabsf(dd[i]) >= fabsf(dl[i])) {
-              if (dd[i] == 0.f) dd[i] = eps_piv;
-              const float f = dl[i] / dd[i];
-              dl[i] = f;
-              dd[i + 1] -= f * du[i];
-            } else {
-              const float f = dd[i] / dl[i];
-              dd[i] = dl[i];
-              dl[i] = f;
-              const float tmp = du[i];
-              du[i] = dd[i + 1];
-              dd[i + 1] = tmp - f * dd[i + 1];
-              if (i + 2 < n) {
-                du2[i] = du[i + 1];
-                du[i + 1] = -f * du[i + 1];
-              }
-              pv[i] = 1.f;
-            }
-          }
-          for (int i = 0; i < n; ++i)
-            if (fabsf(dd[i]) < eps_piv * 1e-3f) dd[i] = copysignf(eps_piv * 1e-3f, dd[i] == 0.f ? 1.f : dd[i]);
+        // LU with partial pivoting of T - lmb I (rows i, i+1 may swap)
+        for (int i = 0; i < n; ++i) {
+          const int o = i * kInvLD + lane;
+          dd[o] = dv[i] - lmb;
+          du[o] = (i + 1 < n) ? ev[i] : 0.f;
+          dl[o] = (i + 1 < n) ? ev[i] : 0.f;
+          du2[o] = 0.f;
+          pv[o] = 0.f;
+          x[o] = start_value(i, t);
         }
-        for (int i = lane; i < n; i += 32) x[i] = start_value(i, t);
-        __syncwarp();
-        for (int iter = 0; iter < 3; ++iter) {
-          if (lane == 0) {
-            for (int i = 0; i + 1 < n; ++i) {
-              if (pv[i] == 0.f) {
-                x[i + 1] -= dl[i] * x[i];
-              } else {
-                const float tmp = x[i];
-                x[i] = x[i + 1];
-                x[i + 1] = tmp - dl[i] * x[i];
-              }
+        float d_i = dd[lane];
+        for (int i = 0; i + 1 < n; ++i) {
+          const int o = i * kInvLD + lane, o1 = o + kInvLD;
+          const float l_i = dl[o];
+          if (fabsf(d_i) >= fabsf(l_i)) {
+            if (d_i == 0.f) d_i = eps_piv;
+            const float f = l_i / d_i;
+            dd[o] = d_i;
+            dl[o] = f;
+            d_i = dd[o1] - f * du[o];
+          } else {
+            const float f = d_i / l_i;
+            dd[o] = l_i;
+            dl[o] = f;
+            const float tmp = du[o];
+            const float dnext = dd[o1];
+            du[o] = dnext;
+            d_i = tmp - f * dnext;
+            if (i + 2 < n) {
+              du2[o] = du[o1];
+              du[o1] = -f * du[o1];
             }
-            x[n - 1] /= dd[n - 1];
-            if (n >= 2) x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / dd[n - 2];
-            for (int i = n - 3; i >= 0; --i)
-              x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / dd[i];
+            pv[o] = 1.f;
           }
-          __syncwarp();
-          // normalise (scale by the max first to stay in range), then
-          // orthogonalise against earlier members of the cluster
+        }
+        dd[(n - 1) * kInvLD + lane] = d_i;
+        for (int i = 0; i < n; ++i) {
+          const int o = i * kInvLD + lane;
+          if (fabsf(dd[o]) < eps_piv * 1e-3f)
+            dd[o] = copysignf(eps_piv * 1e-3f, dd[o] == 0.f ? 1.f : dd[o]);
+        }
+      }
+      __syncwarp();
+      for (int iter = 0; iter < 3; ++iter) {
+        if (act) {
+          for (int i = 0; i + 1 < n; ++i) {
+            const int o = i * kInvLD + lane, o1 = o + kInvLD;
+            if (pv[o] == 0.f) {
+              x[o1] -= dl[o] * x[o];
+            } else {
+              const float tmp = x[o];
+              x[o] = x[o1];
+              x[o1] = tmp - dl[o] * x[o];
+            }
+          }
+          const int on = (n - 1) * kInvLD + lane;
+          x[on] /= dd[on];
+          if (n >= 2) {
+            const int o = on - kInvLD;
+            x[o] = (x[o] - du[o] * x[on]) / dd[o];
+          }
+          for (int i = n - 3; i >= 0; --i) {
+            const int o = i * kInvLD + lane;
+            x[o] = (x[o] - du[o] * x[o + kInvLD] - du2[o] * x[o + 2 * kInvLD]) / dd[o];
+          }
+        }
+        __syncwarp();
+        // normalise each iterate (scaled by its max first to stay in range)
+        // and orthogonalise it against the earlier members of its cluster,
+        // in eigenvalue order, with the whole warp
+        for (int u = 0; u < kr; ++u) {
+          float* xu = x + u;
+          const int tu = t0 + u;
           for (int pass = 0; pass < 2; ++pass) {
             float mx = 0.f;
-            for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(x[i]));
+            for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(xu[i * kInvLD]));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             if (!(mx > 0.f) || !isfinite(mx)) {
-              for (int i = lane; i < n; i += 32) x[i] = start_value(i, t + 7 * iter + 1);
+              for (int i = lane; i < n; i += 32) xu[i * kInvLD] = start_value(i, tu + 7 * iter + 1);
               mx = 2.f;
             }
             const float inv = 1.f / mx;
             float ss = 0.f;
             for (int i = lane; i < n; i += 32) {
-              const float y = x[i] * inv;
-              x[i] = y;
+              const float y = xu[i * kInvLD] * inv;
+              xu[i * kInvLD] = y;
               ss += y * y;
             }
             ss = warp_sum(ss);
             const float rn = rsqrtf(ss);
-            for (int i = lane; i < n; i += 32) x[i] *= rn;
+            for (int i = lane; i < n; i += 32) xu[i * kInvLD] *= rn;
             __syncwarp();
             if (pass == 1) break;
-            for (int q = cstart[c]; q < t; ++q) {
-              const float* zq = Zs + q * n;
+            for (int q = clus_of[tu]; q < tu; ++q) {
+              const float* zq = (q >= t0) ? x + (q - t0) : Zs + q * n;
+              const int sq = (q >= t0) ? kInvLD : 1;
               float dt = 0.f;
-              for (int i = lane; i < n; i += 32) dt += zq[i] * x[i];
+              for (int i = lane; i < n; i += 32) dt += zq[i * sq] * xu[i * kInvLD];
               dt = warp_sum(dt);
-              for (int i = lane; i < n; i += 32) x[i] -= dt * zq[i];
+              for (int i = lane; i < n; i += 32) xu[i * kInvLD] -= dt * zq[i * sq];
               __syncwarp();
             }
           }
         }
-        for (int i = lane; i < n; i += 32) Zs[t * n + i] = x[i];
         __syncwarp();
       }
+      for (int u = 0; u < kr; ++u)
+        for (int i = lane; i < n; i += 32) Zs[(t0 + u) * n + i] = x[i * kInvLD + u];
+      __syncwarp();
     }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += kEigThreads) {
+    const int r = idx / n, c = idx - (idx / n) * n;
+    if (r >= c + 2) A[r * LD + c] = P.HV[idx];
   }
   __syncthreads();
 
@@ -454,8 +524,12 @@ __global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B) {
 }
 
 // ---------------------------------------------------------------------------
-// Rayleigh-Ritz: H = Q^T Y (Y = W Q), Jacobi on H (one warp, FP64), F = Q U,
-// sort by decreasing eigenvalue, fix signs, write F (L x K row-major).
+// Rayleigh-Ritz: H = Q^T Y (Y = W Q) in FP64; the K x K eigenproblem of H by
+// cyclic Jacobi in FP32 (one warp; H is nearly diagonal here, since Q already
+// approximates the eigenvectors), its eigenvector matrix re-orthonormalised
+// in FP64 (Gram-Schmidt, twice) so that F = Q U stays orthonormal to FP64
+// accuracy; columns sorted by decreasing eigenvalue, signs fixed, F written as
+// L x K row-major.
 // ---------------------------------------------------------------------------
 template <typename TOut>
 __global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B) {
@@ -466,64 +540,63 @@ __global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B) {
   double* H = dsm;          // K x K
   double* U = H + K * K;    // K x K
   double* Fs = U + K * K;   // n x K
+  float* Hf = reinterpret_cast<float*>(Fs + n * K);  // K x K
+  float* Uf = Hf + K * K;                            // K x K
   __shared__ int order[kMaxEigK];
   __shared__ int flip[kMaxEigK];
+  __shared__ double dots[kMaxEigK];
   for (int idx = warp; idx < K * K; idx += 8) {
     const int a = idx / K, b = idx - (idx / K) * K;
+    if (a > b) continue;
     const double* qa = P.Q + (int64_t)a * n;
     const double* yb = P.Y + (int64_t)b * n;
+    const double* qb = P.Q + (int64_t)b * n;
+    const double* ya = P.Y + (int64_t)a * n;
     double s = 0.0;
-    for (int r = lane; r < n; r += 32) s += qa[r] * yb[r];
+    for (int r = lane; r < n; r += 32) s += qa[r] * yb[r] + qb[r] * ya[r];
     s = warp_sum(s);
-    if (lane == 0) H[idx] = s;
-  }
-  for (int idx = tid; idx < K * K; idx += 256) U[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int idx = tid; idx < K * K; idx += 256) {
-    const int a = idx / K, b = idx - (idx / K) * K;
-    if (a < b) {
-      const double v = 0.5 * (H[a * K + b] + H[b * K + a]);
-      H[a * K + b] = v;
-      H[b * K + a] = v;
+    if (lane == 0) {
+      Hf[a * K + b] = Hf[b * K + a] = (float)(0.5 * s);
     }
   }
+  for (int idx = tid; idx < K * K; idx += 256) Uf[idx] = (idx / K == idx % K) ? 1.f : 0.f;
   __syncthreads();
   if (warp == 0) {
-    for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int sweep = 0; sweep < 30; ++sweep) {
       int rotated = 0;
       for (int p = 0; p < K - 1; ++p) {
         for (int q = p + 1; q < K; ++q) {
-          const double apq = H[p * K + q];
-          const double app = H[p * K + p], aqq = H[q * K + q];
-          if (apq == 0.0) continue;
-          if (fabs(apq) <= 1e-17 * sqrt(fabs(app) * fabs(aqq))) {
+          const float apq = Hf[p * K + q];
+          const float app = Hf[p * K + p], aqq = Hf[q * K + q];
+          if (apq == 0.f) continue;
+          if (fabsf(apq) <= 1e-9f * sqrtf(fabsf(app) * fabsf(aqq))) {
             __syncwarp();
-            if (lane == 0) H[p * K + q] = H[q * K + p] = 0.0;
+            if (lane == 0) Hf[p * K + q] = Hf[q * K + p] = 0.f;
             __syncwarp();
             continue;
           }
           rotated = 1;
-          const double th = (aqq - app) / (2.0 * apq);
-          const double t = (th >= 0.0) ? 1.0 / (th + sqrt(1.0 + th * th))
-                                       : -1.0 / (-th + sqrt(1.0 + th * th));
-          const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+          const float th = (aqq - app) / (2.f * apq);
+          const float t = (th >= 0.f) ? 1.f / (th + sqrtf(1.f + th * th))
+                                      : -1.f / (-th + sqrtf(1.f + th * th));
+          const float c = rsqrtf(1.f + t * t), s = t * c;
           __syncwarp();
           for (int k = lane; k < K; k += 32) {
-            const double hkp = H[k * K + p], hkq = H[k * K + q];
-            H[k * K + p] = c * hkp - s * hkq;
-            H[k * K + q] = s * hkp + c * hkq;
+            const float hkp = Hf[k * K + p], hkq = Hf[k * K + q];
+            Hf[k * K + p] = c * hkp - s * hkq;
+            Hf[k * K + q] = s * hkp + c * hkq;
           }
           __syncwarp();
           for (int k = lane; k < K; k += 32) {
-            const double hpk = H[p * K + k], hqk = H[q * K + k];
-            H[p * K + k] = c * hpk - s * hqk;
-            H[q * K + k] = s * hpk + c * hqk;
-            const double ukp = U[k * K + p], ukq = U[k * K + q];
-            U[k * K + p] = c * ukp - s * ukq;
-            U[k * K + q] = s * ukp + c * ukq;
+            const float hpk = Hf[p * K + k], hqk = Hf[q * K + k];
+            Hf[p * K + k] = c * hpk - s * hqk;
+            Hf[q * K + k] = s * hpk + c * hqk;
+            const float ukp = Uf[k * K + p], ukq = Uf[k * K + q];
+            Uf[k * K + p] = c * ukp - s * ukq;
+            Uf[k * K + q] = s * ukp + c * ukq;
           }
           __syncwarp();
-          if (lane == 0) H[p * K + q] = H[q * K + p] = 0.0;
+          if (lane == 0) Hf[p * K + q] = Hf[q * K + p] = 0.f;
           __syncwarp();
         }
       }
@@ -534,7 +607,7 @@ __global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B) {
       for (int i = 0; i < K; ++i) {
         int best = i;
         for (int j = i + 1; j < K; ++j)
-          if (H[order[j] * K + order[j]] > H[order[best] * K + order[best]]) best = j;
+          if (Hf[order[j] * K + order[j]] > Hf[order[best] * K + order[best]]) best = j;
         const int tmp = order[i];
         order[i] = order[best];
         order[best] = tmp;
@@ -542,12 +615,41 @@ __global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B) {
     }
   }
   __syncthreads();
-  // F = Q U(:, order)
+  // U = Uf(:, order) in FP64, then Gram-Schmidt twice on its columns
+  for (int idx = tid; idx < K * K; idx += 256) {
+    const int a = idx / K, c = idx - (idx / K) * K;
+    U[idx] = (double)Uf[a * K + order[c]];
+  }
+  __syncthreads();
+  for (int j = 0; j < K; ++j) {
+    for (int pass = 0; pass < 2; ++pass) {
+      if (tid < j) {
+        double s = 0.0;
+        for (int a = 0; a < K; ++a) s += U[a * K + tid] * U[a * K + j];
+        dots[tid] = s;
+      }
+      __syncthreads();
+      if (tid < K) {
+        double v = U[tid * K + j];
+        for (int i = 0; i < j; ++i) v -= dots[i] * U[tid * K + i];
+        U[tid * K + j] = v;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      double s = 0.0;
+      for (int a = 0; a < K; ++a) s += U[a * K + j] * U[a * K + j];
+      dots[0] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    }
+    __syncthreads();
+    if (tid < K) U[tid * K + j] *= dots[0];
+    __syncthreads();
+  }
+  // F = Q U
   for (int idx = tid; idx < n * K; idx += 256) {
     const int r = idx / K, c = idx - (idx / K) * K;
-    const int oc = order[c];
     double s = 0.0;
-    for (int a = 0; a < K; ++a) s += P.Q[(int64_t)a * n + r] * U[a * K + oc];
+    for (int a = 0; a < K; ++a) s += P.Q[(int64_t)a * n + r] * U[a * K + c];
     Fs[idx] = s;
   }
   __syncthreads();
@@ -581,12 +683,11 @@ __global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B) {
   }
 }
 
-size_t stage1_smem(int L, int K, int inv_warps) {
+size_t stage1_smem(int L, int K) {
   const size_t LD = (size_t)(L | 1);
-  size_t floats = (size_t)L * LD + (size_t)K * L + 6 * (size_t)L + 2 * (size_t)K + 48;
-  size_t bytes = floats * 4 + (size_t)(K + 1) * 4;
-  bytes = (bytes + 15) / 16 * 16;
-  return bytes + (size_t)inv_warps * 6 * L * 4;
+  const size_t reg0 = std::max((size_t)L * LD, (size_t)kInvArrays * L * kInvLD);
+  const size_t floats = reg0 + (size_t)K * L + 6 * (size_t)L + 2 * (size_t)K + 48;
+  return floats * 4 + (size_t)(2 * K + 1) * 4 + 16;
 }
 
 int max_smem_optin() {
@@ -646,6 +747,8 @@ int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, s
       p += align_up(l * k * 4);
       d.theta = reinterpret_cast<float*>(p);
       p += align_up(k * 4);
+      d.HV = reinterpret_cast<float*>(p);
+      p += align_up(l * l * 4);
       d.Q = reinterpret_cast<double*>(p);
       p += align_up(l * k * 8);
       d.Y = reinterpret_cast<double*>(p);
@@ -654,13 +757,9 @@ int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, s
       maxK = std::max(maxK, pr.K);
     }
     const int smax = max_smem_optin();
-    const size_t base = stage1_smem(maxL, maxK, 0);
-    const size_t per_warp = (size_t)6 * maxL * 4;
-    if (base + per_warp > (size_t)smax)
+    const size_t sm1 = stage1_smem(maxL, maxK);
+    if (sm1 > (size_t)smax)
       return fail(TUCKER_ERR_UNSUPPORTED, "eig: matrix too large for shared memory");
-    EB.inv_warps = (int)std::min<size_t>({(size_t)kEigWarps, (size_t)maxK,
-                                          ((size_t)smax - base) / per_warp});
-    const size_t sm1 = stage1_smem(maxL, maxK, EB.inv_warps);
     TK_CUDA_TRY(cudaFuncSetAttribute(eig_stage1_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     eig_stage1_kernel<<<nb, kEigThreads, sm1, s>>>(EB);
@@ -681,7 +780,7 @@ int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, s
     // Rayleigh-Ritz on span(Q): Y = W Q, then the K x K problem
     eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0);
     TK_LAUNCH_CHECK("eig_wmul");
-    const size_t sm3 = ((size_t)2 * maxK * maxK + (size_t)maxL * maxK) * 8;
+    const size_t sm3 = ((size_t)2 * maxK * maxK + (size_t)maxL * maxK) * 8 + (size_t)2 * maxK * maxK * 4;
     if (sm3 > (size_t)smax) return fail(TUCKER_ERR_UNSUPPORTED, "eig: K too large");
     if (f_dtype == TUCKER_F64) {
       TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_kernel<double>,

@@ -202,7 +202,9 @@ void memory_plan(Plan& p) {
 }
 
 // Mode order of the new-core chain minimising multiply-adds: DP over the set
-// S of modes already applied.
+// S of modes already applied.  Among equal-cost orders the higher modes go
+// last, so the full tensor is read by a leading-mode TTM (long contiguous
+// fibres) rather than by the last-mode one.
 void core_chain(Plan& p) {
   const int N = p.N;
   const unsigned full = (1u << N) - 1u;
@@ -210,7 +212,7 @@ void core_chain(Plan& p) {
   std::vector<int> last((size_t)1 << N, -1);
   best[0] = 0;
   for (unsigned S = 1; S <= full; ++S) {
-    for (int m = 0; m < N; ++m) {
+    for (int m = N - 1; m >= 0; --m) {
       if (!((S >> m) & 1u)) continue;
       const unsigned prev = S & ~(1u << m);
       if (best[prev] == kInf) continue;
@@ -252,11 +254,12 @@ void sthosvd_buffers(Plan& p) {
 }  // namespace
 
 size_t eig_ws_bytes(int batch, const int64_t* L, const int64_t* K) {
-  // per matrix: V0 (L*K floats), theta (K floats), Q and Y (L*K doubles each)
+  // per matrix: V0 (L*K floats), theta (K floats), parked reflectors (L*L
+  // floats), Q and Y (L*K doubles each)
   size_t total = 0;
   for (int b = 0; b < batch; ++b) {
     const size_t l = (size_t)L[b], k = (size_t)K[b];
-    total += align_up(l * k * 4) + align_up(k * 4) + 2 * align_up(l * k * 8);
+    total += align_up(l * k * 4) + align_up(k * 4) + align_up(l * l * 4) + 2 * align_up(l * k * 8);
   }
   return total;
 }

@@ -99,6 +99,119 @@ __global__ void __launch_bounds__(kColsThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// ttm_cols_pipe: the same mapping as ttm_cols, but each thread streams its
+// VEC-wide column slice through a private ring of kDepth shared-memory slots
+// filled by cp.async, so kDepth loads per thread are in flight without
+// holding registers.  Used when VEC*sizeof(TIn) is 8 or 16 bytes and aligned.
+// Each thread reads back only the slots it filled itself, so no block-level
+// barrier guards the ring; cp.async.wait_group orders its own copies.
+// ---------------------------------------------------------------------------
+constexpr int kDepth = 8;
+
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename TIn, int VEC>
+struct Slot {
+  static constexpr int kBytes = VEC * (int)sizeof(TIn);
+  static __device__ __forceinline__ void copy(void* smem, const TIn* g) {
+    if constexpr (kBytes == 16) cp_async_16(smem, g);
+    else cp_async_8(smem, g);
+  }
+};
+
+template <typename TIn, typename TOut, int KB, int VEC>
+__global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccOf<TIn>::type) <= 384) ? 2 : 1)
+    ttm_cols_pipe_kernel(const TIn* __restrict__ X, const typename AccOf<TIn>::type* __restrict__ F,
+                         TOut* __restrict__ Y, int64_t R, int L, int64_t C, int K) {
+  using A = typename AccOf<TIn>::type;
+  constexpr int SB = Slot<TIn, VEC>::kBytes;
+  static_assert(SB == 8 || SB == 16, "slot size");
+  __shared__ __align__(16) A Fs[kColsLChunk][KB];
+  __shared__ __align__(16) unsigned char ring[kDepth][kColsThreads][SB];
+  const int tid = threadIdx.x;
+  const int kb0 = blockIdx.y * KB;
+  const int64_t total = R * C;
+  const int64_t m0 = ((int64_t)blockIdx.x * kColsThreads + tid) * VEC;
+  const bool active = m0 < total;
+  int64_t r = 0, c = 0;
+  if (active) {
+    r = m0 / C;
+    c = m0 - r * C;
+  }
+  const TIn* xp = X + (r * L) * C + c;
+#pragma unroll
+  for (int s = 0; s < kDepth; ++s) {
+    if (active && s < L) Slot<TIn, VEC>::copy(&ring[s][tid][0], xp + (int64_t)s * C);
+    cp_async_commit();
+  }
+  A acc[KB][VEC];
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[k][v] = A(0);
+
+  for (int l0 = 0; l0 < L; l0 += kColsLChunk) {
+    const int lc = min(kColsLChunk, L - l0);
+    __syncthreads();
+    for (int i = tid; i < kColsLChunk * KB; i += kColsThreads) {
+      const int l = i / KB, k = i - (i / KB) * KB;
+      Fs[l][k] = (l < lc && kb0 + k < K) ? F[(int64_t)(l0 + l) * K + kb0 + k] : A(0);
+    }
+    __syncthreads();
+    for (int ll = 0; ll < lc; ++ll) {
+      const int l = l0 + ll;
+      cp_async_wait<kDepth - 1>();
+      A x[VEC];
+      const unsigned char* slot = &ring[l % kDepth][tid][0];
+      if constexpr (sizeof(TIn) == 2) {
+        const uint2 q = *reinterpret_cast<const uint2*>(slot);
+        x[0] = __uint_as_float(q.x << 16);
+        x[1] = __uint_as_float(q.x & 0xFFFF0000u);
+        x[2] = __uint_as_float(q.y << 16);
+        x[3] = __uint_as_float(q.y & 0xFFFF0000u);
+      } else {
+        const TIn* q = reinterpret_cast<const TIn*>(slot);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) x[v] = q[v];
+      }
+      if (active && l + kDepth < L)
+        Slot<TIn, VEC>::copy(&ring[l % kDepth][tid][0], xp + (int64_t)(l + kDepth) * C);
+      cp_async_commit();
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        const A f = Fs[ll][k];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[k][v] = fma(f, x[v], acc[k][v]);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (!active) return;
+  TOut* yp = Y + (r * K + kb0) * C + c;
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    if (kb0 + k < K) {
+      TOut o[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) o[v] = (TOut)acc[k][v];
+      VecStore<TOut, VEC>::run(yp + (int64_t)k * C, o);
+    }
+  }
+}
+
 constexpr int kRowsThreads = 128;
 constexpr int kRowsLChunk = 32;
 
@@ -167,7 +280,7 @@ int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccO
   const int64_t total = R * C;
   if (vec_ok) {
     const int64_t gx = (total / V + kColsThreads - 1) / kColsThreads;
-    ttm_cols_kernel<TIn, TOut, KB, V><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
+    ttm_cols_pipe_kernel<TIn, TOut, KB, V><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
         X, F, Y, R, (int)L, C, (int)K);
   } else {
     const int64_t gx = (total + kColsThreads - 1) / kColsThreads;

@@ -34,7 +34,10 @@ def _gen(seed: int, device) -> torch.Generator:
 def orthonormal_factor(L: int, K: int, gen: torch.Generator, device, dtype=torch.float64):
     """Q factor of the QR of an L x K Gaussian matrix (orthonormal columns)."""
     A = torch.randn(L, K, generator=gen, device=device, dtype=torch.float64)
-    Q, R = torch.linalg.qr(A)
+    # the QR of this small matrix runs on the host (no device linear-algebra
+    # library needed); the result is moved back to `device`
+    Q, R = torch.linalg.qr(A.cpu())
+    Q, R = Q.to(device), R.to(device)
     # make the factorisation unique: positive diagonal of R
     s = torch.sign(torch.diagonal(R))
     s[s == 0] = 1
