@@ -164,6 +164,23 @@ int tucker_eig_topk(int batch, const int64_t* L, const int64_t* K, const double*
                     void* const* F, int f_dtype, void* ws, size_t ws_bytes, void* stream);
 size_t tucker_eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
 
+/* Allocation-free variant of tucker_eig_topk (the paper has no counterpart:
+ * this serves callers that must not allocate device memory, e.g. when all
+ * device memory belongs to another allocator, or where cudaMalloc/cudaFree
+ * could synchronise the device).  Same arguments, results and ordering as
+ * tucker_eig_topk, but no workspace: the scratch is a fixed array of about
+ * 3.2 MiB compiled into the library, held on every GPU that loads it until the
+ * process exits.  Limits: batch <= 8, every L <= 200 and K <= min(L, 64);
+ * larger problems return TUCKER_ERR_UNSUPPORTED.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array: calls that may overlap on the GPU (different streams, or
+ * different host threads) race on it and must be serialised by the caller.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine). */
+int tucker_eig_topk_noalloc(int batch, const int64_t* L, const int64_t* K, const double* const* W,
+                            void* const* F, int f_dtype, void* stream);
+
 /* Per-node CUDA-event timing of a plan's calls (tracing).  While enabled,
  * tucker_hooi_sweep records a start/end event pair on its stream around each
  * tree node's launches (node = index in tucker_plan_nodes order, label = its

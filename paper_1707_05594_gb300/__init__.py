@@ -83,6 +83,8 @@ def lib():
                               ctypes.c_void_p, ctypes.c_void_p]
     L.tucker_eig_topk.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    L.tucker_eig_topk_noalloc.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
+                                          ctypes.c_void_p]
     L.tucker_eig_ws_bytes.argtypes = [ctypes.c_int, _i64p, _i64p]
     L.tucker_eig_ws_bytes.restype = ctypes.c_size_t
     L.tucker_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -250,6 +252,17 @@ def tucker_eig_topk(Ws: Sequence, Fs: Sequence, ws, stream=None):
     _check(lib().tucker_eig_topk(len(Ws), _i64(Ls), _i64(Ks), _ptrs(Ws), _ptrs(Fs),
                                  _dtype_code(Fs[0]), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                  _stream(stream)), "tucker_eig_topk")
+
+
+def tucker_eig_topk_noalloc(Ws: Sequence, Fs: Sequence, stream=None):
+    """Leading eigenvectors without any device allocation or workspace: for
+    callers that must not allocate (see include/tucker.h).  Uses a fixed
+    scratch array inside the library shared by all calls."""
+    Ls = [W.shape[0] for W in Ws]
+    Ks = [F.shape[1] for F in Fs]
+    _check(lib().tucker_eig_topk_noalloc(len(Ws), _i64(Ls), _i64(Ks), _ptrs(Ws), _ptrs(Fs),
+                                         _dtype_code(Fs[0]), _stream(stream)),
+           "tucker_eig_topk_noalloc")
 
 
 def tucker_profile_enable(plan: Plan, capacity: int) -> None:
