@@ -43,6 +43,8 @@ def parse():
                     choices=["optimal", "chain", "chain_k", "chain_h", "balanced"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-policy", type=int, default=0,
+                    help="0: tensor cores where supported (default); 1: CUDA cores only")
     ap.add_argument("--ttm", default=None,
                     help="time one TTM kernel alone: 'L0,L1,...:mode:K[:f32|bf16|f64]' "
                          "(kernel studies and small ncu captures)")
@@ -57,6 +59,7 @@ def run_ttm_only(args):
     import workloads
     from paper_1707_05594_gb300 import build as tkbuild
     tkbuild.build()
+    tk.lib().tucker_set_kernel_policy(args.kernel_policy)
     parts = args.ttm.split(":")
     dims = tuple(int(x) for x in parts[0].split(","))
     n, K = int(parts[1]), int(parts[2])
@@ -81,7 +84,8 @@ def run_ttm_only(args):
     ms = e0.elapsed_time(e1) / args.steps
     byts = X.numel() * X.element_size() + Y.numel() * Y.element_size()
     pk = peaks()
-    return {"kernel": "tucker_ttm", "shape": list(dims), "mode": n, "K": K,
+    return {"kernel": "tucker_ttm", "policy": args.kernel_policy, "shape": list(dims), "mode": n,
+            "K": K,
             "dtype": str(dt).replace("torch.", ""), "ms": round(ms, 5),
             "gbs": round(byts / ms / 1e6, 1), "frac_of_hbm": round(byts / ms / 1e6 / pk["hbm_gbs"], 4),
             "steps": args.steps, "warmup": args.warmup}

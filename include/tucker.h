@@ -203,6 +203,22 @@ int tucker_profile_read(tucker_plan_t plan, tucker_prof_rec_t* recs, int capacit
  * all plans); a monotone counter for accounting. */
 uint64_t tucker_launch_count(void);
 
+/* Storage conversion for the precision form: hi[i] = bf16(x[i]) rounded to
+ * nearest even and, if lo is not NULL, lo[i] = bf16(x[i] - hi[i]), so that
+ * hi + lo holds x to ~16 significand bits.  n elements; all three device
+ * buffers 16-byte aligned; BF16 values are raw uint16 bit patterns. */
+int tucker_convert_bf16(const float* x, uint16_t* hi, uint16_t* lo, int64_t n, void* stream);
+
+/* Kernel selection: 0 (default) lets BF16 tensors use the tensor-core TTM
+ * (tcgen05 + TMA) wherever the shape allows; 1 restricts every TTM to the
+ * CUDA-core kernels (used to compare the two).  Process-wide. */
+int tucker_set_kernel_policy(int policy);
+
+/* Device error word of the tensor-core kernels: 0, or TUCKER_ERR_TIMEOUT if a
+ * pipeline wait gave up (the kernel then returned early and its output is not
+ * valid).  Synchronous; reset != 0 clears the word. */
+int tucker_device_status(int* status, int reset);
+
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* tucker_last_error(void);
 

@@ -83,6 +83,10 @@ def lib():
                               ctypes.c_void_p, ctypes.c_void_p]
     L.tucker_eig_topk.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    L.tucker_convert_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_void_p]
+    L.tucker_set_kernel_policy.argtypes = [ctypes.c_int]
+    L.tucker_device_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     L.tucker_eig_topk_noalloc.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
                                           ctypes.c_void_p]
     L.tucker_eig_ws_bytes.argtypes = [ctypes.c_int, _i64p, _i64p]
@@ -263,6 +267,24 @@ def tucker_eig_topk_noalloc(Ws: Sequence, Fs: Sequence, stream=None):
     _check(lib().tucker_eig_topk_noalloc(len(Ws), _i64(Ls), _i64(Ks), _ptrs(Ws), _ptrs(Fs),
                                          _dtype_code(Fs[0]), _stream(stream)),
            "tucker_eig_topk_noalloc")
+
+
+def tucker_convert_bf16(x, hi, lo=None, stream=None):
+    """hi = bf16(x) (round to nearest even), lo = bf16(x - hi) when given."""
+    _req(x, "x")
+    _check(lib().tucker_convert_bf16(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(hi.data_ptr()),
+                                     ctypes.c_void_p(lo.data_ptr()) if lo is not None else None,
+                                     x.numel(), _stream(stream)), "tucker_convert_bf16")
+
+
+def tucker_set_kernel_policy(policy: int) -> None:
+    _check(lib().tucker_set_kernel_policy(int(policy)), "tucker_set_kernel_policy")
+
+
+def tucker_device_status(reset: bool = True) -> int:
+    st = ctypes.c_int(0)
+    _check(lib().tucker_device_status(ctypes.byref(st), 1 if reset else 0), "tucker_device_status")
+    return st.value
 
 
 def tucker_profile_enable(plan: Plan, capacity: int) -> None:

@@ -85,7 +85,8 @@ int tucker_ttm(int N, const int64_t* dims, const void* X, int x_dtype, int n, co
     if (dims[i] < 1) return fail(TUCKER_ERR_INVALID_ARG, "tucker_ttm: lengths must be >= 1");
   int64_t R, L, C;
   view3(dims, N, n, &R, &L, &C);
-  return launch_ttm(x_dtype, X, R, L, C, F, K, Y, static_cast<cudaStream_t>(stream));
+  return launch_ttm(x_dtype, X, R, L, C, F, K, Y, factor_dtype(x_dtype),
+                    static_cast<cudaStream_t>(stream));
 }
 
 int tucker_gram(int N, const int64_t* dims, const void* Z, int z_dtype, int n, double* W,
@@ -131,18 +132,19 @@ int tucker_hooi_sweep(tucker_plan_t plan, const void* T, const void* const* F_in
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* wsb = static_cast<char*>(ws);
   const int fdt = factor_dtype(p.dtype);
+  const int idt = p.inter_dtype();
   for (size_t i = 1; i < p.nodes.size(); ++i) {
     const PlanNode& nd = p.nodes[i];
     const PlanNode& par = p.nodes[(size_t)nd.parent];
     const bool from_root = nd.parent == 0;
     const void* in = from_root ? T : (const void*)(wsb + p.off_scratch + par.ws_off);
-    const int in_dt = from_root ? p.dtype : fdt;
+    const int in_dt = from_root ? p.dtype : idt;
     ProfScope prof(plan->p, s, (int)i, nd.label);
     if (nd.label >= 0) {
       int64_t R, L, C;
       view3(par.out_dims, p.N, nd.label, &R, &L, &C);
       rc = launch_ttm(in_dt, in, R, L, C, F_in[nd.label], p.K[nd.label],
-                      wsb + p.off_scratch + nd.ws_off, s);
+                      wsb + p.off_scratch + nd.ws_off, idt, s);
       if (rc) return rc;
     } else {
       const int n = -nd.label - 2;
@@ -237,11 +239,12 @@ int tucker_core(tucker_plan_t plan, const void* T, const void* const* F, void* G
     int64_t R, L, C;
     view3(dims, p.N, m, &R, &L, &C);
     ProfScope prof(plan->p, s, -2, m);
-    rc = launch_ttm(cur_dt, cur, R, L, C, F[m], p.K[m], out, s);
+    const int out_dt = (i == p.N - 1) ? fdt : p.inter_dtype();
+    rc = launch_ttm(cur_dt, cur, R, L, C, F[m], p.K[m], out, out_dt, s);
     if (rc) return rc;
     dims[m] = p.K[m];
     cur = out;
-    cur_dt = fdt;
+    cur_dt = out_dt;
   }
   return TUCKER_OK;
 }
@@ -279,11 +282,12 @@ int tucker_sthosvd(tucker_plan_t plan, const void* T, void* const* F, void* G, v
     rc = launch_eig_topk(&pr, 1, fdt, wsb + p.off_eig, p.bytes_eig, s);
     if (rc) return rc;
     void* out = (n == p.N - 1) ? G : buf[n & 1];
-    rc = launch_ttm(cur_dt, cur, R, L, C, F[n], p.K[n], out, s);
+    const int out_dt = (n == p.N - 1) ? fdt : p.inter_dtype();
+    rc = launch_ttm(cur_dt, cur, R, L, C, F[n], p.K[n], out, out_dt, s);
     if (rc) return rc;
     dims[n] = p.K[n];
     cur = out;
-    cur_dt = fdt;
+    cur_dt = out_dt;
   }
   return TUCKER_OK;
 }

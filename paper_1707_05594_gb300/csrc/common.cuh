@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <string>
 
 #include "internal.h"
@@ -48,6 +49,35 @@ struct bf16_t {
 __device__ __forceinline__ float bf16_to_float(uint16_t b) {
   return __uint_as_float(((uint32_t)b) << 16);
 }
+
+// FP32 -> BF16 with round-to-nearest-even (NaN stays NaN).
+__host__ __device__ __forceinline__ uint16_t f2bf(float f) {
+  uint32_t u;
+#ifdef __CUDA_ARCH__
+  u = __float_as_uint(f);
+#else
+  std::memcpy(&u, &f, 4);
+#endif
+  if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)((u >> 16) | ((u & 0xFFFFu) ? 0x40u : 0u));
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+// Accumulator -> output element conversion.
+template <typename T>
+struct OutCvt {
+  template <typename A>
+  static __device__ __forceinline__ T run(A v) {
+    return (T)v;
+  }
+};
+template <>
+struct OutCvt<bf16_t> {
+  template <typename A>
+  static __device__ __forceinline__ bf16_t run(A v) {
+    return bf16_t{f2bf((float)v)};
+  }
+};
 
 template <typename T>
 __device__ __forceinline__ typename AccOf<T>::type load_one(const T* p) {
@@ -123,9 +153,18 @@ int sm_count();
 
 // ---- launchers implemented in the .cu files --------------------------------
 // Y = X x_n F^T on a tensor viewed as [R][L][C] (R = modes before n, C = modes
-// after n).  x_dtype: TUCKER_F32 / F64 / BF16; F and Y in the factor type.
+// after n).  x_dtype: TUCKER_F32 / F64 / BF16; F in the factor type (double
+// for F64, else float); y_dtype: F64 for F64 input, F32 or BF16 otherwise.
 int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, const void* F,
-               int64_t K, void* Y, cudaStream_t s);
+               int64_t K, void* Y, int y_dtype, cudaStream_t s);
+// Tensor-core TTM for BF16 tensors (ttm_tc.cu): X, optionally plus a low part
+// X_lo, contracted with FP32 F; Y is FP32 or BF16.
+bool ttm_tc_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X,
+                      const void* X_lo);
+int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t C,
+                  const float* F, int64_t K, void* Y, bool y_bf16, cudaStream_t s);
+// kernel-selection policy (tucker_set_kernel_policy): 0 = auto, 1 = CUDA cores only
+int kernel_policy();
 // W += Z_(n) Z_(n)^T for Z viewed as [R][L][C] (W must be zeroed first).
 int launch_gram(int z_dtype, const void* Z, int64_t R, int64_t L, int64_t C, double* W,
                 cudaStream_t s);

@@ -18,10 +18,16 @@ constexpr int kMStep = 32;
 constexpr int kRun = 256;  // columns accumulated in FP32 before folding into FP64
 constexpr int kGramThreads = 256;
 
+constexpr int kPad = 4;  // row padding that keeps 16-byte alignment for vector reads
+
+// Loads the kTile x kMStep panel Z[row0 .. row0+63, m0 .. m0+31] into S[mm][a].
+// For C > 1 every thread keeps one column m = m0 + (tid % 32) for the whole
+// panel, so `base` (the address of Z[r, 0, c] for that column, or NULL past
+// the end) is computed once per panel by the caller.
 template <typename TIn>
 __device__ __forceinline__ void load_panel(const TIn* __restrict__ Z, int64_t L, int64_t C,
-                                           int64_t M, int row0, int64_t m0,
-                                           typename AccOf<TIn>::type (*S)[kTile + 1]) {
+                                           int64_t M, int row0, int64_t m0, const TIn* base,
+                                           typename AccOf<TIn>::type (*S)[kTile + kPad]) {
   using A = typename AccOf<TIn>::type;
   if (C == 1) {
     // element (l, m) at m*L + l: consecutive threads take consecutive l
@@ -32,15 +38,10 @@ __device__ __forceinline__ void load_panel(const TIn* __restrict__ Z, int64_t L,
     }
   } else {
     // element (l, m) at r*L*C + l*C + c: consecutive threads take consecutive m
-    for (int i = threadIdx.x; i < kTile * kMStep; i += kGramThreads) {
-      const int mm = i % kMStep, a = i / kMStep;
-      const int64_t l = row0 + a, m = m0 + mm;
-      A v = A(0);
-      if (l < L && m < M) {
-        const int64_t r = m / C, c = m - (m / C) * C;
-        v = load_one<TIn>(Z + (r * L + l) * C + c);
-      }
-      S[mm][a] = v;
+    const int mm = threadIdx.x % kMStep;
+    for (int a = threadIdx.x / kMStep; a < kTile; a += kGramThreads / kMStep) {
+      const int64_t l = row0 + a;
+      S[mm][a] = (base && l < L) ? load_one<TIn>(base + l * C) : A(0);
     }
   }
 }
@@ -50,8 +51,8 @@ __global__ void __launch_bounds__(kGramThreads)
     gram_kernel(const TIn* __restrict__ Z, int64_t R, int64_t L, int64_t C, double* __restrict__ W,
                 int ntiles, int64_t m_per_block) {
   using A = typename AccOf<TIn>::type;
-  __shared__ A As[kMStep][kTile + 1];
-  __shared__ A Bs[kMStep][kTile + 1];
+  __shared__ __align__(16) A As[kMStep][kTile + kPad];
+  __shared__ __align__(16) A Bs[kMStep][kTile + kPad];
   // lower-triangular tile index -> (ti, tj), ti >= tj
   int t = blockIdx.x, ti = 0;
   while (t > ti) {
@@ -75,9 +76,17 @@ __global__ void __launch_bounds__(kGramThreads)
     }
   int run = 0;
   for (int64_t m0 = mbeg; m0 < mend; m0 += kMStep) {
+    const TIn* base = nullptr;
+    if (C > 1) {
+      const int64_t m = m0 + threadIdx.x % kMStep;
+      if (m < mend) {
+        const int64_t r = m / C;
+        base = Z + r * L * C + (m - r * C);
+      }
+    }
     __syncthreads();
-    load_panel<TIn>(Z, L, C, mend, ti * kTile, m0, As);
-    load_panel<TIn>(Z, L, C, mend, tj * kTile, m0, Bs);
+    load_panel<TIn>(Z, L, C, mend, ti * kTile, m0, base, As);
+    load_panel<TIn>(Z, L, C, mend, tj * kTile, m0, base, Bs);
     __syncthreads();
 #pragma unroll 8
     for (int mm = 0; mm < kMStep; ++mm) {

@@ -50,8 +50,14 @@ struct Plan {
   std::vector<int> prof_node, prof_label;
 
   size_t elem_bytes() const { return dtype == TUCKER_F64 ? 8 : (dtype == TUCKER_BF16 ? 2 : 4); }
-  // intermediates are computed in the factor type: double for F64, else float
-  size_t inter_bytes() const { return dtype == TUCKER_F64 ? 8 : 4; }
+  // tree intermediates: FP64 for FP64 tensors, BF16 for BF16 tensors (the
+  // precision form), FP32 otherwise
+  int inter_dtype() const {
+    return dtype == TUCKER_F64 ? TUCKER_F64 : (dtype == TUCKER_BF16 ? TUCKER_BF16 : TUCKER_F32);
+  }
+  size_t inter_bytes() const {
+    return dtype == TUCKER_F64 ? 8 : (dtype == TUCKER_BF16 ? 2 : 4);
+  }
 };
 
 // thread-local error text

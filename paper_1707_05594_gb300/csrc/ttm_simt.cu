@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kColsThreads)
     if (kb0 + k < K) {
       TOut o[VEC];
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) o[v] = (TOut)acc[k][v];
+      for (int v = 0; v < VEC; ++v) o[v] = OutCvt<TOut>::run(acc[k][v]);
       VecStore<TOut, VEC>::run(yp + (int64_t)k * C, o);
     }
   }
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccO
     if (kb0 + k < K) {
       TOut o[VEC];
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) o[v] = (TOut)acc[k][v];
+      for (int v = 0; v < VEC; ++v) o[v] = OutCvt<TOut>::run(acc[k][v]);
       VecStore<TOut, VEC>::run(yp + (int64_t)k * C, o);
     }
   }
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kRowsThreads)
   TOut* yp = Y + r * K + kb0;
 #pragma unroll
   for (int k = 0; k < KB; ++k)
-    if (kb0 + k < K) yp[k] = (TOut)acc[k];
+    if (kb0 + k < K) yp[k] = OutCvt<TOut>::run(acc[k]);
 }
 
 int pick_kb(int64_t K) {
@@ -310,14 +310,26 @@ int launch_typed(const void* X, int64_t R, int64_t L, int64_t C, const void* F, 
 }  // namespace
 
 int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, const void* F,
-               int64_t K, void* Y, cudaStream_t s) {
+               int64_t K, void* Y, int y_dtype, cudaStream_t s) {
   if (R * C == 0 || K == 0) return TUCKER_OK;
   if (R * C / kColsThreads >= (int64_t)INT32_MAX || L > INT32_MAX || K > INT32_MAX)
     return fail(TUCKER_ERR_UNSUPPORTED, "ttm: tensor too large for the grid");
   switch (x_dtype) {
-    case TUCKER_F32: return launch_typed<float, float>(X, R, L, C, F, K, Y, s);
-    case TUCKER_F64: return launch_typed<double, double>(X, R, L, C, F, K, Y, s);
-    case TUCKER_BF16: return launch_typed<bf16_t, float>(X, R, L, C, F, K, Y, s);
+    case TUCKER_F32:
+      if (y_dtype != TUCKER_F32) return fail(TUCKER_ERR_UNSUPPORTED, "ttm: FP32 input needs FP32 output");
+      return launch_typed<float, float>(X, R, L, C, F, K, Y, s);
+    case TUCKER_F64:
+      if (y_dtype != TUCKER_F64) return fail(TUCKER_ERR_UNSUPPORTED, "ttm: FP64 input needs FP64 output");
+      return launch_typed<double, double>(X, R, L, C, F, K, Y, s);
+    case TUCKER_BF16: {
+      const bool ybf = y_dtype == TUCKER_BF16;
+      if (!ybf && y_dtype != TUCKER_F32)
+        return fail(TUCKER_ERR_UNSUPPORTED, "ttm: BF16 input needs FP32 or BF16 output");
+      if (kernel_policy() == 0 && ttm_tc_supported(R, L, C, K, X, nullptr))
+        return launch_ttm_tc(X, nullptr, R, L, C, static_cast<const float*>(F), K, Y, ybf, s);
+      return ybf ? launch_typed<bf16_t, bf16_t>(X, R, L, C, F, K, Y, s)
+                 : launch_typed<bf16_t, float>(X, R, L, C, F, K, Y, s);
+    }
     default: return fail(TUCKER_ERR_INVALID_ARG, "ttm: unknown dtype");
   }
 }

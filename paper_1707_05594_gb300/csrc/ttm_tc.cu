@@ -1,0 +1,530 @@
+// ttm_tc.cu -- mode-n TTM on the 5th-generation tensor cores (tcgen05) for
+// tensors stored in BF16: Out = In x_n F^T (Sec. 2.1), transposition-free.
+//
+// GEMM view (per tile): D[M = 128 free positions, N] += A[128 x L] * B[L x N]
+//   column case (mode not last, C > 1): the 128 positions are 128 consecutive
+//     c of one r; the A tile In[r, l0:l0+64, c0:c0+128] arrives by TMA as two
+//     64 x 64 boxes with the 128-byte swizzle and is used MN-major;
+//   row case (last mode, C = 1): the positions are 128 consecutive r; the A
+//     tile In[r0:r0+128, l0:l0+64] is K-major.
+// B holds F split into a high and a low BF16 part, [F_hi | F_lo] side by side
+// along N (N = 2*Np, Np = K rounded up to 16), so the product carries F to
+// ~16 bits while T keeps its storage precision; the epilogue adds the halves.
+// Optionally the tensor itself comes as two BF16 tensors hi + lo (a split of an
+// FP32 tensor): then each k-step issues a second MMA A_lo * F_hi into the
+// first half.  Accumulation is FP32 in tensor memory (TMEM).
+//
+// Warp roles (192 threads, one CTA per SM, persistent over tiles):
+//   warp 0  TMA producer (one lane) through a kStages-deep shared-memory ring;
+//   warp 1  TMEM allocation and the MMA issuer (one lane);
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator rows their TMEM lane
+//              quarter owns, FP32 sum of the two halves, global stores.
+// The accumulator is double-buffered in TMEM so the epilogue of tile i
+// overlaps the MMAs of tile i+1.  Every mbarrier wait is bounded by a
+// %globaltimer deadline; on expiry the kernel records an error word, drains
+// its own copies (bounded), frees TMEM and returns.
+#include <cuda.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace tk {
+
+__device__ int g_tk_status = 0;  // 0 = ok, else the code of the first timeout
+
+namespace {
+
+constexpr int kStagesPlain = 8;  // ring depth, one A tensor per stage
+constexpr int kStagesSplit = 5;  // ring depth, hi and lo A tensors per stage
+__host__ __device__ constexpr int stages_for(bool split) { return split ? kStagesSplit : kStagesPlain; }
+constexpr int kBoxL = 64;                       // l per stage (128 B of BF16)
+constexpr int kTileM = 128;                     // positions per tile
+constexpr int kStageBytes = kTileM * kBoxL * 2;  // one A tensor, 16 KB
+constexpr int kThreads = 192;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: true when the phase completed, false on timeout or when
+// another role has already given up (abort flag).
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        atomicCAS(&g_tk_status, 0, TUCKER_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (>> 4), version 1, swizzle mode in bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                              uint32_t swizzle) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)swizzle << 61);
+}
+constexpr uint32_t kSwizzleNone = 0, kSwizzle128 = 2;
+
+// Instruction descriptor for kind::f16 with BF16 A and B, FP32 accumulate,
+// M = 128, B K-major; A K-major (0) or MN-major (1).
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, int a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <typename TOut>
+__device__ __forceinline__ TOut to_out(float v) {
+  return OutCvt<TOut>::run(v);
+}
+
+struct TcParams {
+  int64_t R, C;   // view [R][L][C]
+  int L, K;       // contraction length, outputs per position
+  int Np;         // K rounded up to 16
+  int nk;         // number of 64-wide l chunks
+  int64_t tiles;  // number of 128-position tiles
+  int64_t ctiles; // column case: tiles per r
+  const float* F; // L x K row-major (FP32)
+};
+
+// SMEM layout (dynamic, 1024-aligned):
+//   [A ring: kStages x (1 or 2) x 16 KB][B: nk chunks x (2*Np rows) x 128 B]
+//   [barriers][tmem slot][abort flag]
+template <bool kRows, bool kSplitA, typename TOut>
+__global__ void __launch_bounds__(kThreads, 1)
+    ttm_tc_kernel(const __grid_constant__ CUtensorMap map_hi,
+                  const __grid_constant__ CUtensorMap map_lo, TOut* __restrict__ Y,
+                  const TcParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int kA = kSplitA ? 2 : 1;
+  constexpr uint32_t kStages = (uint32_t)stages_for(kSplitA);
+  unsigned char* ring = smem;
+  unsigned char* bsm = ring + (size_t)kStages * kA * kStageBytes;
+  const int N2 = 2 * P.Np;  // rows of B ([F_hi | F_lo] along N)
+  const size_t b_bytes = (size_t)P.nk * N2 * 128;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + ((b_bytes + 15) & ~size_t(15)));
+  uint64_t* full = bars;                // kStages
+  uint64_t* empty = bars + kStages;     // kStages
+  uint64_t* tfull = bars + 2 * kStages; // 2
+  uint64_t* tempty = tfull + 2;         // 2
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // TMEM: two accumulator buffers of N2 columns each
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(2 * N2)) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (uint32_t s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // B = [F_hi | F_lo]^T as BF16, K-major without swizzle: core matrices of 8
+  // rows x 8 l (16 B per row); LBO = 128 B between l-groups, SBO = (64/8)*128
+  // between 8-row groups, one 64-l chunk after another.
+  for (int idx = threadIdx.x; idx < N2 * P.nk * kBoxL; idx += kThreads) {
+    const int row = idx / (P.nk * kBoxL);
+    const int l = idx - row * (P.nk * kBoxL);
+    const int k = row < P.Np ? row : row - P.Np;
+    float f = 0.f;
+    if (k < P.K && l < P.L) f = P.F[(int64_t)l * P.K + k];
+    const uint16_t hi = f2bf(f);
+    const float rem = f - __uint_as_float((uint32_t)hi << 16);
+    const uint16_t v = row < P.Np ? hi : f2bf(rem);
+    const int chunk = l / kBoxL, lc = l - chunk * kBoxL;
+    const size_t off = (size_t)chunk * N2 * 128 + (size_t)(row >> 3) * 1024 + (size_t)(lc >> 3) * 128 +
+                       (size_t)(row & 7) * 16 + (size_t)(lc & 7) * 2;
+    *reinterpret_cast<uint16_t*>(bsm + off) = v;
+  }
+  // generic-proxy writes of B must be visible to the tensor core (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+        for (int kc = 0; kc < P.nk; ++kc, ++it) {
+          const uint32_t s = it % kStages, ph = (it / kStages) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], (uint32_t)(kA * kStageBytes));
+          unsigned char* dst = ring + (size_t)s * kA * kStageBytes;
+          if (kRows) {
+            const int r0 = (int)(t * kTileM);
+            tma_load_2d(dst, &map_hi, &full[s], kc * kBoxL, r0);
+            if (kSplitA) tma_load_2d(dst + kStageBytes, &map_lo, &full[s], kc * kBoxL, r0);
+          } else {
+            const int64_t r = t / P.ctiles;
+            const int c0 = (int)((t - r * P.ctiles) * kTileM);
+            tma_load_3d(dst, &map_hi, &full[s], c0, kc * kBoxL, (int)r);
+            tma_load_3d(dst + kStageBytes / 2, &map_hi, &full[s], c0 + 64, kc * kBoxL, (int)r);
+            if (kSplitA) {
+              tma_load_3d(dst + kStageBytes, &map_lo, &full[s], c0, kc * kBoxL, (int)r);
+              tma_load_3d(dst + kStageBytes + kStageBytes / 2, &map_lo, &full[s], c0 + 64,
+                          kc * kBoxL, (int)r);
+            }
+          }
+        }
+      }
+      // drain: wait (bounded) until every copy issued has landed
+      const uint32_t issued = it;
+      for (uint32_t j = (issued > kStages ? issued - kStages : 0); j < issued; ++j) {
+        const uint32_t s = j % kStages, ph = (j / kStages) & 1u;
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(&full[s], ph) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc_full = idesc_bf16(N2, kRows ? 0 : 1);
+      const uint32_t idesc_half = idesc_bf16(P.Np, kRows ? 0 : 1);
+      const uint32_t b_base = smem_u32(bsm);
+      uint32_t it = 0, tcount = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x, ++tcount) {
+        const uint32_t buf = tcount & 1u, aph = (tcount >> 1) & 1u;
+        if (!mbar_wait(&tempty[buf], aph ^ 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + buf * (uint32_t)N2;
+        for (int kc = 0; kc < P.nk; ++kc, ++it) {
+          const uint32_t s = it % kStages, ph = (it / kStages) & 1u;
+          if (!mbar_wait(&full[s], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(ring + (size_t)s * kA * kStageBytes);
+#pragma unroll
+          for (int ks = 0; ks < kBoxL / 16; ++ks) {
+            uint64_t ad_hi, ad_lo;
+            if (kRows) {
+              // K-major, 128 rows of 128 B: 8-row groups 1024 B apart,
+              // k-step of 16 elements = 32 B inside the swizzled row
+              ad_hi = smem_desc(a_base + ks * 32, 16, 1024, kSwizzle128);
+              ad_lo = smem_desc(a_base + kStageBytes + ks * 32, 16, 1024, kSwizzle128);
+            } else {
+              // MN-major: 64-position halves 8 KB apart (LBO), 8-row l-groups
+              // 1024 B apart (SBO), k-step of 16 l = 2048 B
+              ad_hi = smem_desc(a_base + ks * 2048, 8192, 1024, kSwizzle128);
+              ad_lo = smem_desc(a_base + kStageBytes + ks * 2048, 8192, 1024, kSwizzle128);
+            }
+            const uint32_t b_chunk = b_base + (uint32_t)(kc * N2 * 128);
+            const uint64_t bd = smem_desc(b_chunk + ks * 256, 128, 1024, kSwizzleNone);
+            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+            mma_bf16(d_tmem, ad_hi, bd, idesc_full, acc);
+            if (kSplitA) mma_bf16(d_tmem, ad_lo, bd, idesc_half, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[buf]);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;            // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;     // accumulator row = tile position
+    uint32_t tcount = 0;
+    for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x, ++tcount) {
+      const uint32_t buf = tcount & 1u, aph = (tcount >> 1) & 1u;
+      if (!mbar_wait(&tfull[buf], aph, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + buf * (uint32_t)N2;
+      float hi[16], lo[16];
+      for (int k0 = 0; k0 < P.Np; k0 += 16) {
+        tmem_ld16(tbase + k0, hi);
+        tmem_ld16(tbase + P.Np + k0, lo);
+        tmem_wait_ld();
+        if (kRows) {
+          const int64_t r = t * kTileM + row;
+          if (r < P.R) {
+            TOut* yp = Y + r * P.K;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (k0 + j < P.K) yp[k0 + j] = to_out<TOut>(hi[j] + lo[j]);
+          }
+        } else {
+          const int64_t r = t / P.ctiles;
+          const int64_t c = (t - r * P.ctiles) * kTileM + row;
+          if (c < P.C) {
+            TOut* yp = Y + (r * P.K) * P.C + c;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (k0 + j < P.K) yp[(int64_t)(k0 + j) * P.C] = to_out<TOut>(hi[j] + lo[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(ncols));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+int make_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims,
+             const cuuint64_t* strides_bytes, const cuuint32_t* box) {
+  EncodeFn enc = encoder();
+  if (!enc) return fail(TUCKER_ERR_CUDA, "ttm_tc: cuTensorMapEncodeTiled unavailable");
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank,
+                         const_cast<void*>(base), dims, strides_bytes, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TUCKER_ERR_CUDA, "ttm_tc: cuTensorMapEncodeTiled failed");
+  return TUCKER_OK;
+}
+
+size_t smem_bytes(int Np, int nk, bool split_a) {
+  const size_t stages = (size_t)stages_for(split_a);
+  const size_t ring = stages * (split_a ? 2 : 1) * kStageBytes;
+  const size_t b = (size_t)nk * 2 * Np * 128;
+  return 1024 + ring + ((b + 15) & ~size_t(15)) + (2 * stages + 4) * 8 + 16;
+}
+
+template <bool kRows, bool kSplitA, typename TOut>
+int launch_variant(const CUtensorMap& mh, const CUtensorMap& ml, void* Y, const TcParams& P,
+                   size_t smem, cudaStream_t s) {
+  auto kern = ttm_tc_kernel<kRows, kSplitA, TOut>;
+  TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t grid = std::min<int64_t>(P.tiles, sm_count());
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(mh, ml, static_cast<TOut*>(Y), P);
+  TK_LAUNCH_CHECK("ttm_tc");
+  return TUCKER_OK;
+}
+
+}  // namespace
+
+// Whether the tensor-core TTM handles this shape: BF16 tensor, 16-byte
+// aligned rows for TMA (C % 8 == 0 in the column case, L % 8 == 0 in the row
+// case), K <= 64 and L <= 1024 (B stays resident in shared memory).
+bool ttm_tc_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X, const void* X_lo) {
+  if (K < 1 || K > 64 || L < 1 || L > 1024) return false;
+  if ((uintptr_t)X % 16 != 0 || (X_lo && (uintptr_t)X_lo % 16 != 0)) return false;
+  if (R > INT32_MAX || C > INT32_MAX) return false;
+  if (C == 1) return L % 8 == 0 && R >= 1;
+  return C % 8 == 0 && C >= 64;
+}
+
+// Y (K outputs, FP32 or BF16) = X x_n F^T with X (and optionally X_lo) BF16.
+int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t C,
+                  const float* F, int64_t K, void* Y, bool y_bf16, cudaStream_t s) {
+  if (!ttm_tc_supported(R, L, C, K, X, X_lo))
+    return fail(TUCKER_ERR_UNSUPPORTED, "ttm_tc: shape or alignment not supported");
+  TcParams P{};
+  P.R = R;
+  P.C = C;
+  P.L = (int)L;
+  P.K = (int)K;
+  P.Np = (int)((K + 15) / 16 * 16);
+  P.nk = (int)((L + kBoxL - 1) / kBoxL);
+  P.F = F;
+  const bool rows = (C == 1);
+  CUtensorMap mh, ml;
+  if (rows) {
+    P.tiles = (R + kTileM - 1) / kTileM;
+    P.ctiles = 1;
+    const cuuint64_t dims[2] = {(cuuint64_t)L, (cuuint64_t)R};
+    const cuuint64_t str[1] = {(cuuint64_t)L * 2};
+    const cuuint32_t box[2] = {kBoxL, kTileM};
+    int rc = make_map(&mh, X, 2, dims, str, box);
+    if (rc) return rc;
+    rc = make_map(&ml, X_lo ? X_lo : X, 2, dims, str, box);
+    if (rc) return rc;
+  } else {
+    P.ctiles = (C + kTileM - 1) / kTileM;
+    P.tiles = R * P.ctiles;
+    const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)L, (cuuint64_t)R};
+    const cuuint64_t str[2] = {(cuuint64_t)C * 2, (cuuint64_t)C * L * 2};
+    const cuuint32_t box[3] = {64, kBoxL, 1};
+    int rc = make_map(&mh, X, 3, dims, str, box);
+    if (rc) return rc;
+    rc = make_map(&ml, X_lo ? X_lo : X, 3, dims, str, box);
+    if (rc) return rc;
+  }
+  const bool split = X_lo != nullptr;
+  const size_t smem = smem_bytes(P.Np, P.nk, split);
+  if (smem > 227 * 1024) return fail(TUCKER_ERR_UNSUPPORTED, "ttm_tc: shared memory");
+  if (rows) {
+    if (split)
+      return y_bf16 ? launch_variant<true, true, bf16_t>(mh, ml, Y, P, smem, s)
+                    : launch_variant<true, true, float>(mh, ml, Y, P, smem, s);
+    return y_bf16 ? launch_variant<true, false, bf16_t>(mh, ml, Y, P, smem, s)
+                  : launch_variant<true, false, float>(mh, ml, Y, P, smem, s);
+  }
+  if (split)
+    return y_bf16 ? launch_variant<false, true, bf16_t>(mh, ml, Y, P, smem, s)
+                  : launch_variant<false, true, float>(mh, ml, Y, P, smem, s);
+  return y_bf16 ? launch_variant<false, false, bf16_t>(mh, ml, Y, P, smem, s)
+                : launch_variant<false, false, float>(mh, ml, Y, P, smem, s);
+}
+
+}  // namespace tk
+
+namespace tk {
+namespace {
+std::atomic<int> g_policy{0};
+}
+int kernel_policy() { return g_policy.load(std::memory_order_relaxed); }
+}  // namespace tk
+
+extern "C" int tucker_set_kernel_policy(int policy) {
+  if (policy != 0 && policy != 1)
+    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be 0 or 1");
+  tk::g_policy.store(policy, std::memory_order_relaxed);
+  return TUCKER_OK;
+}
+
+extern "C" int tucker_device_status(int* status, int reset) {
+  if (!status) return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_device_status: NULL");
+  TK_CUDA_TRY(cudaMemcpyFromSymbol(status, tk::g_tk_status, sizeof(int)));
+  if (reset) {
+    const int zero = 0;
+    TK_CUDA_TRY(cudaMemcpyToSymbol(tk::g_tk_status, &zero, sizeof(int)));
+  }
+  return TUCKER_OK;
+}

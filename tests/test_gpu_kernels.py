@@ -66,6 +66,50 @@ def test_ttm_matches_oracle(tk, orc, shape, n, K, dtype):
     assert np.all(err <= (shape[n] + 2) * u * bound + 1e-300), err.max()
 
 
+TC_CASES = [
+    # column case (mode not last; C % 8 == 0, C >= 64): ragged tiles, l chunks
+    ((5, 200, 136), 1, 20), ((3, 37, 64), 1, 5), ((2, 64, 1000), 1, 16), ((130, 72), 0, 1),
+    ((64, 64, 64, 64), 2, 16), ((4, 256, 128), 1, 33), ((96, 512), 0, 64),
+    # row case (last mode; L % 8 == 0)
+    ((300, 64), 1, 16), ((257, 200), 1, 20), ((1000, 24), 1, 8), ((7, 9, 128), 2, 64),
+]
+
+
+def status_ok(tk):
+    import ctypes
+    st = ctypes.c_int(-99)
+    assert tk.lib().tucker_device_status(ctypes.byref(st), 1) == 0
+    return st.value == 0
+
+
+@pytest.mark.parametrize("shape,n,K", TC_CASES)
+@pytest.mark.parametrize("policy", [0, 1])
+def test_ttm_bf16_tensor_cores(tk, orc, shape, n, K, policy):
+    """BF16 tensor, FP32 factor: the tcgen05 path (policy 0) splits F into two
+    BF16 parts (error <= 2^-16 |f| per product) and accumulates in FP32 in
+    TMEM; the CUDA-core path (policy 1) converts exactly and accumulates with
+    FMAs.  Bound: (2^-15 + (L + 2) * 2^-23) * sum |x f|."""
+    X = workloads.random_tensor(shape, seed=sum(shape) * 3 + n, dtype=torch.bfloat16)
+    F = workloads.random_factor(shape[n], K, seed=K + 1, dtype=torch.float32, orthonormal=False)
+    out_shape = list(shape)
+    out_shape[n] = K
+    Y = torch.full(out_shape, float("nan"), dtype=torch.float32, device="cuda")
+    assert tk.lib().tucker_set_kernel_policy(policy) == 0
+    try:
+        tk.tucker_ttm(X.cuda(), n, F.cuda(), Y)
+        torch.cuda.synchronize()
+    finally:
+        tk.lib().tucker_set_kernel_policy(0)
+    assert status_ok(tk)
+    Xd = X.double().numpy()
+    Fd = F.double().numpy()
+    ref = orc.ttm(Xd, n, Fd.T)
+    bound = orc.ttm(np.abs(Xd), n, np.abs(Fd).T)
+    err = np.abs(Y.double().cpu().numpy() - ref)
+    tol = (2.0 ** -15 + (shape[n] + 2) * 2.0 ** -23) * bound + 1e-30
+    assert np.all(err <= tol), (err / (bound + 1e-30)).max()
+
+
 @pytest.mark.parametrize("shape,n", [((37, 29, 11), 0), ((37, 29, 11), 1), ((37, 29, 11), 2),
                                      ((130, 700), 0), ((700, 130), 1), ((3, 200, 41), 1),
                                      ((20, 20, 20, 200), 3), ((5, 6, 7), 1)])
