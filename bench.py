@@ -43,6 +43,8 @@ def parse():
                     choices=["optimal", "chain", "chain_k", "chain_h", "balanced"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--unfused", action="store_true",
+                    help="time hooi_sweep + a separate core chain + fit per step")
     ap.add_argument("--kernel-policy", type=int, default=0,
                     help="0: tensor cores where supported (default); 1: CUDA cores only")
     ap.add_argument("--ttm", default=None,
@@ -281,8 +283,24 @@ def run_ours(args, ws_size, rank):
     torch.cuda.synchronize()
     nodes = tk.tucker_plan_nodes(d.plan)
     cost = tk.tucker_plan_cost(d.plan)
+    step = d.sweep if args.unfused else d.sweep_fused
+    # the unfused step (sweep, then a separate core chain and fit), timed
+    # briefly for reference when the fused step is the headline
+    unfused_ms = None
+    if not args.unfused:
+        for _ in range(2):
+            d.sweep()
+        torch.cuda.synchronize()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nu = max(3, min(10, args.steps))
+        u0.record()
+        for _ in range(nu):
+            d.sweep()
+        u1.record()
+        torch.cuda.synchronize()
+        unfused_ms = u0.elapsed_time(u1) / nu
     for _ in range(args.warmup):
-        d.sweep()
+        step()
     torch.cuda.synchronize()
     # per-node event ring for the timed region
     per_step = len(nodes) + 1 + d.plan.N
@@ -297,7 +315,7 @@ def run_ours(args, ws_size, rank):
     sampler.start()
     ev0.record(s)
     for _ in range(args.steps):
-        d.sweep()
+        step()
     ev1.record(s)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -342,7 +360,7 @@ def run_ours(args, ws_size, rank):
     e0.record(s)
     for _ in range(e2e_steps):
         T.copy_(T_host, non_blocking=True)
-        d.sweep()
+        step()
         for fh, fd in zip(F_host, d.F):
             fh.copy_(fd, non_blocking=True)
         G_host.copy_(d.G, non_blocking=True)
@@ -362,7 +380,11 @@ def run_ours(args, ws_size, rank):
                                f"{str(T.dtype).replace('torch.', '')}, ranks {'x'.join(map(str, K))}, "
                                f"rho={spec['rho']}, seed {spec['seed']}",
                    "tree": args.tree, "tree_macs": cost["tree_macs"],
-                   "core_macs": cost["core_macs"], "step": "hooi_sweep + core + fit",
+                   "core_macs": cost["core_macs"],
+                   "step": ("hooi_sweep + core chain + fit" if args.unfused else
+                            "hooi_sweep_core (N new factors + the core of the sweep's input "
+                            "factors from the tree's smallest leaf input) + fit"),
+                   "unfused_step_ms": round(unfused_ms, 4) if unfused_ms else None,
                    "l2": "inputs exceed L2 (tensor 6.4 GB >> 129 MB), no flush",
                    "parallelism": "replicas" if ws_size > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "root TTM (ttm_cols, reads all of T)",

@@ -128,6 +128,17 @@ int tucker_sthosvd(tucker_plan_t plan, const void* T, void* const* F, void* G, v
 int tucker_hooi_sweep(tucker_plan_t plan, const void* T, const void* const* F_in,
                       void* const* F_out, void* ws, size_t ws_bytes, void* stream);
 
+/* tucker_hooi_sweep that also writes G_in = T x_0 F_in[0]^T ... x_{N-1}
+ * F_in[N-1]^T, the core of the INPUT factors (Fig. 2's new core, formed for
+ * F_in), at the cost of one small TTM: the input of the tree's smallest leaf
+ * is already T x_{j != n} F_in[j]^T, so G_in = that x_n F_in[n]^T.  Run in a
+ * loop, sweep s+1 therefore yields the core (and with tucker_fit the error) of
+ * sweep s's factors; the last sweep's core needs one tucker_core.  G_in may be
+ * NULL (then this is tucker_hooi_sweep). */
+int tucker_hooi_sweep_core(tucker_plan_t plan, const void* T, const void* const* F_in,
+                           void* const* F_out, void* G_in, void* ws, size_t ws_bytes,
+                           void* stream);
+
 /* New core (Fig. 2): G = T x_0 F_0^T ... x_{N-1} F_{N-1}^T, with the chain's
  * mode order chosen to minimise multiply-adds. */
 int tucker_core(tucker_plan_t plan, const void* T, const void* const* F, void* G, void* ws,
@@ -169,7 +180,7 @@ size_t tucker_eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
  * device memory belongs to another allocator, or where cudaMalloc/cudaFree
  * could synchronise the device).  Same arguments, results and ordering as
  * tucker_eig_topk, but no workspace: the scratch is a fixed array of about
- * 3.2 MiB compiled into the library, held on every GPU that loads it until the
+ * 4 MiB compiled into the library, held on every GPU that loads it until the
  * process exits.  Limits: batch <= 8, every L <= 200 and K <= min(L, 64);
  * larger problems return TUCKER_ERR_UNSUPPORTED.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
@@ -209,9 +220,14 @@ uint64_t tucker_launch_count(void);
  * buffers 16-byte aligned; BF16 values are raw uint16 bit patterns. */
 int tucker_convert_bf16(const float* x, uint16_t* hi, uint16_t* lo, int64_t n, void* stream);
 
-/* Kernel selection: 0 (default) lets BF16 tensors use the tensor-core TTM
- * (tcgen05 + TMA) wherever the shape allows; 1 restricts every TTM to the
- * CUDA-core kernels (used to compare the two).  Process-wide. */
+/* Kernel selection, a bit mask (process-wide; 0 is the default):
+ *   bit 0 (1): every TTM on the CUDA-core kernels (otherwise BF16 tensors use
+ *              the tensor-core TTM, tcgen05 + TMA, wherever the shape allows);
+ *   bit 1 (2): HOOI sweeps always run the full eigensolver (otherwise they start
+ *              from the input factors: two FP64 subspace-iteration steps and an
+ *              a-posteriori check, falling back to the full path on the GPU
+ *              when the check fails).
+ * Used to compare the paths. */
 int tucker_set_kernel_policy(int policy);
 
 /* Device error word of the tensor-core kernels: 0, or TUCKER_ERR_TIMEOUT if a

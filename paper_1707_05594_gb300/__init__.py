@@ -74,6 +74,9 @@ def lib():
                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
     L.tucker_core.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _vpp, ctypes.c_void_p,
                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    L.tucker_hooi_sweep_core.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _vpp, _vpp,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_void_p]
     L.tucker_norm2.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.tucker_fit.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                              ctypes.c_void_p]
@@ -215,6 +218,16 @@ def tucker_hooi_sweep(plan: Plan, T, F_in: Sequence, F_out: Sequence, ws, stream
                                    _stream(stream)), "tucker_hooi_sweep")
 
 
+def tucker_hooi_sweep_core(plan: Plan, T, F_in: Sequence, F_out: Sequence, G_in, ws, stream=None):
+    """HOOI sweep that also returns the core of its INPUT factors (from the tree)."""
+    _req(T, "T")
+    _check(lib().tucker_hooi_sweep_core(plan.handle, ctypes.c_void_p(T.data_ptr()), _ptrs(F_in),
+                                        _ptrs(F_out),
+                                        ctypes.c_void_p(G_in.data_ptr()) if G_in is not None else None,
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
+           "tucker_hooi_sweep_core")
+
+
 def tucker_core(plan: Plan, T, F: Sequence, G, ws, stream=None):
     _check(lib().tucker_core(plan.handle, ctypes.c_void_p(T.data_ptr()), _ptrs(F),
                              ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
@@ -339,11 +352,20 @@ class Decomposition:
         tucker_fit(self.plan, self.G, self.normT2, self.fit_out)
 
     def sweep(self, with_core: bool = True):
+        """One HOOI sweep; then the new core of the new factors and the fit."""
         tucker_hooi_sweep(self.plan, self.T, self.F, self.F_next, self.ws)
         self.F, self.F_next = self.F_next, self.F
         if with_core:
             tucker_core(self.plan, self.T, self.F, self.G, self.ws)
             tucker_fit(self.plan, self.G, self.normT2, self.fit_out)
+
+    def sweep_fused(self):
+        """One HOOI sweep whose tree also yields the core (and fit) of the
+        factors it starts from: after this call G and fit() describe the
+        previous factors, F holds the new ones."""
+        tucker_hooi_sweep_core(self.plan, self.T, self.F, self.F_next, self.G, self.ws)
+        tucker_fit(self.plan, self.G, self.normT2, self.fit_out)
+        self.F, self.F_next = self.F_next, self.F
 
     def fit(self) -> float:
         return float(self.fit_out[0].item())

@@ -117,6 +117,12 @@ int tucker_eig_topk(int batch, const int64_t* L, const int64_t* K, const double*
 
 int tucker_hooi_sweep(tucker_plan_t plan, const void* T, const void* const* F_in,
                       void* const* F_out, void* ws, size_t ws_bytes, void* stream) {
+  return tucker_hooi_sweep_core(plan, T, F_in, F_out, nullptr, ws, ws_bytes, stream);
+}
+
+int tucker_hooi_sweep_core(tucker_plan_t plan, const void* T, const void* const* F_in,
+                           void* const* F_out, void* G_in, void* ws, size_t ws_bytes,
+                           void* stream) {
   if (!plan || !T) return fail(TUCKER_ERR_INVALID_ARG, "tucker_hooi_sweep: NULL plan or T");
   const Plan& p = plan->p;
   int rc = check_ptrs(F_in, p.N, "tucker_hooi_sweep");
@@ -133,6 +139,17 @@ int tucker_hooi_sweep(tucker_plan_t plan, const void* T, const void* const* F_in
   char* wsb = static_cast<char*>(ws);
   const int fdt = factor_dtype(p.dtype);
   const int idt = p.inter_dtype();
+  // the core of the input factors comes from the smallest leaf input:
+  // G = Z_n x_n F_n^T with Z_n = T x_{j != n} F_j^T (Fig. 2 "New core" for F_in)
+  int core_leaf = -1;
+  if (G_in) {
+    uint64_t best = ~0ull;
+    for (size_t i = 1; i < p.nodes.size(); ++i)
+      if (p.nodes[i].label < -1 && p.nodes[i].in_elems < best) {
+        best = p.nodes[i].in_elems;
+        core_leaf = (int)i;
+      }
+  }
   for (size_t i = 1; i < p.nodes.size(); ++i) {
     const PlanNode& nd = p.nodes[i];
     const PlanNode& par = p.nodes[(size_t)nd.parent];
@@ -154,12 +171,17 @@ int tucker_hooi_sweep(tucker_plan_t plan, const void* T, const void* const* F_in
       TK_CUDA_TRY(cudaMemsetAsync(W, 0, (size_t)L * (size_t)L * sizeof(double), s));
       rc = launch_gram(in_dt, in, R, L, C, W, s);
       if (rc) return rc;
+      if ((int)i == core_leaf) {
+        rc = launch_ttm(in_dt, in, R, L, C, F_in[n], p.K[n], G_in, fdt, s);
+        if (rc) return rc;
+      }
     }
   }
+  // the input factors start the eigensolver (warm start, checked on the GPU)
   EigProblem probs[kMaxModes];
   for (int n = 0; n < p.N; ++n)
     probs[n] = EigProblem{reinterpret_cast<const double*>(wsb + p.off_gram[n]), F_out[n],
-                          (int)p.L[n], (int)p.K[n]};
+                          (int)p.L[n], (int)p.K[n], F_in[n]};
   ProfScope prof(plan->p, s, -1, -1);
   return launch_eig_topk(probs, p.N, fdt, wsb + p.off_eig, p.bytes_eig, s);
 }

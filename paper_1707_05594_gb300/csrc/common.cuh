@@ -175,9 +175,10 @@ int launch_fit(int g_dtype, const void* G, int64_t n, const double* normT2, doub
                cudaStream_t s);
 
 struct EigProblem {
-  const double* W;  // L x L
-  void* F;          // L x K output
+  const double* W;         // L x L
+  void* F;                 // L x K output
   int L, K;
+  const void* F0 = nullptr;  // optional L x K starting subspace (factor type)
 };
 int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, size_t ws_bytes,
                     cudaStream_t s);

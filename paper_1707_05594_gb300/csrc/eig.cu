@@ -41,11 +41,14 @@ constexpr int kMaxBatch = TUCKER_MAX_MODES;
 struct EigDesc {
   const double* W;
   void* F;
-  float* V0;     // [K][L]
-  float* theta;  // [K]
-  float* HV;     // [L][L] parked reflectors
-  double* Q;     // [K][L]
-  double* Y;     // [K][L]
+  const void* F0;  // warm start: L x K row-major input factor (or NULL)
+  float* V0;       // [K][L]
+  float* theta;    // [K]
+  float* HV;       // [L][L] parked reflectors
+  double* Q;       // [K][L]
+  double* Y;       // [K][L]
+  double* Qp;      // [K][L] previous basis (warm start)
+  double* stat;    // [0] delta1, [1] delta2; ((int*)stat)[4] = need_cold flag
   int L, K;
 };
 struct EigBatch {
@@ -97,11 +100,34 @@ __device__ __forceinline__ float start_value(int i, int t) {
   return 1.0f + 0.5f * ((float)(h & 0xFFFFu) / 65536.0f - 0.5f);
 }
 
+// Warm start bookkeeping: stat[0] / stat[1] hold the subspace movement of the
+// two warm subspace-iteration steps, the int at stat + 4 words says whether the
+// full (cold) path must run.  Kernels of the cold path launched with gate = 1
+// return at once when the warm result was accepted.
+__device__ __forceinline__ int& need_cold(const EigDesc& P) {
+  return reinterpret_cast<int*>(P.stat)[4];
+}
+__device__ __forceinline__ bool gated_off(const EigDesc& P, int gate) {
+  return gate && need_cold(P) == 0;
+}
+
+// Starting subspace from the input factor: V0[c][r] = F0[r][c].
+template <typename TF>
+__global__ void __launch_bounds__(256) eig_seed_kernel(const EigBatch B) {
+  const EigDesc P = B.d[blockIdx.x];
+  const TF* F0 = static_cast<const TF*>(P.F0);
+  for (int idx = threadIdx.x; idx < P.L * P.K; idx += 256) {
+    const int r = idx / P.K, c = idx - (idx / P.K) * P.K;
+    P.V0[c * P.L + r] = (float)F0[idx];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Stage 1: FP32 tridiagonalisation, bisection, inverse iteration, back-transform.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch B) {
+__global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch B, int gate) {
   const EigDesc P = B.d[blockIdx.x];
+  if (gated_off(P, gate)) return;
   const int n = P.L, K = P.K, LD = n | 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   extern __shared__ __align__(16) float sm[];
@@ -441,8 +467,9 @@ __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch 
 // One warp per row r; lanes split j.
 // ---------------------------------------------------------------------------
 template <typename TIn>
-__global__ void __launch_bounds__(256) eig_wmul_kernel(const EigBatch B, int use_v0) {
+__global__ void __launch_bounds__(256) eig_wmul_kernel(const EigBatch B, int use_v0, int gate) {
   const EigDesc P = B.d[blockIdx.y];
+  if (gated_off(P, gate)) return;
   const int n = P.L, K = P.K;
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -471,24 +498,84 @@ __global__ void __launch_bounds__(256) eig_wmul_kernel(const EigBatch B, int use
   }
 }
 
+// Block sum in FP64 for 256 threads; every thread receives the result.
+__device__ double block_sum256(double v, double* red) {
+  __syncthreads();
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) t += red[w];
+  return t;
+}
+
+// sum over a, b < K of (A_a . Q_b)^2 for [K][n] bases A (float or double) and Q
+template <typename TA>
+__device__ double proj_norm2(const TA* A, const double* Q, int n, int K, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double acc = 0.0;
+  for (int idx = warp; idx < K * K; idx += 8) {
+    const int a = idx / K, b = idx - (idx / K) * K;
+    double s = 0.0;
+    for (int r = lane; r < n; r += 32) s += (double)A[(int64_t)a * n + r] * Q[(int64_t)b * n + r];
+    s = warp_sum(s);
+    acc += s * s;  // identical in every lane
+  }
+  if (lane != 0) acc = 0.0;
+  return block_sum256(acc, red);
+}
+
 // ---------------------------------------------------------------------------
 // Q = orth(Y diag(1/theta)) by classical Gram-Schmidt applied twice, in FP64,
 // column by column in eigenvalue order.  Writes Q.
+//   mode 0 (full path): theta from stage 1, a negligible theta falls back to V0;
+//   mode 1 (warm step 1): theta_j = V0_j . Y_j (Rayleigh quotient of the
+//     starting vector); records delta1 = K - ||V0^T Q||_F^2 and keeps Q in Qp;
+//   mode 2 (warm step 2): theta_j = Qp_j . Y_j; records delta2 = K -
+//     ||Qp^T Q||_F^2 and accepts the warm result when delta2 <= tol and the
+//     iteration contracts (delta2 <= delta1 / 4, or delta1 <= tol too);
+//     otherwise it raises the need-cold flag for the full path.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B) {
+__global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B, int mode, int gate,
+                                                       double tol) {
   const EigDesc P = B.d[blockIdx.x];
+  if (gated_off(P, gate)) return;
   const int n = P.L, K = P.K;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ double dots[kMaxEigK];
+  __shared__ double th[kMaxEigK];
   __shared__ double red[8];
   double* Q = P.Q;
-  // scaled columns; fall back to V0 when theta is negligible
-  float tmax = 0.f;
-  for (int t = 0; t < K; ++t) tmax = fmaxf(tmax, fabsf(P.theta[t]));
+  if (mode == 0) {
+    float tmax = 0.f;
+    for (int t = 0; t < K; ++t) tmax = fmaxf(tmax, fabsf(P.theta[t]));
+    for (int t = tid; t < K; t += 256) {
+      const float v = P.theta[t];
+      th[t] = (fabsf(v) > 1e-20f * tmax && v != 0.f) ? (double)v : 0.0;
+    }
+  } else {
+    for (int t = warp; t < K; t += 8) {
+      double s = 0.0;
+      for (int r = lane; r < n; r += 32) {
+        const double v = (mode == 1) ? (double)P.V0[(int64_t)t * n + r] : P.Qp[(int64_t)t * n + r];
+        s += v * P.Y[(int64_t)t * n + r];
+      }
+      s = warp_sum(s);
+      if (lane == 0) th[t] = s;
+    }
+  }
+  __syncthreads();
+  double tmx = 0.0;
+  for (int t = 0; t < K; ++t) tmx = fmax(tmx, fabs(th[t]));
   for (int i = tid; i < K * n; i += 256) {
     const int t = i / n;
-    const float th = P.theta[t];
-    Q[i] = (fabsf(th) > 1e-20f * tmax && th != 0.f) ? P.Y[i] / (double)th : (double)P.V0[i];
+    const double v = th[t];
+    if (fabs(v) > 1e-30 * tmx && v != 0.0) {
+      Q[i] = P.Y[i] / v;
+    } else {
+      Q[i] = (mode == 2) ? P.Qp[i] : (double)P.V0[i];
+    }
   }
   __syncthreads();
   for (int j = 0; j < K; ++j) {
@@ -512,14 +599,23 @@ __global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B) {
     }
     double s = 0.0;
     for (int r = tid; r < n; r += 256) s += qj[r] * qj[r];
-    s = warp_sum(s);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    double tot = 0.0;
-    for (int w = 0; w < 8; ++w) tot += red[w];
+    const double tot = block_sum256(s, red);
     const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
     for (int r = tid; r < n; r += 256) qj[r] *= inv;
     __syncthreads();
+  }
+  if (mode == 1) {
+    const double pn = proj_norm2<float>(P.V0, Q, n, K, red);
+    for (int i = tid; i < K * n; i += 256) P.Qp[i] = Q[i];
+    if (tid == 0) P.stat[0] = fmax(0.0, (double)K - pn);
+  } else if (mode == 2) {
+    const double pn = proj_norm2<double>(P.Qp, Q, n, K, red);
+    if (tid == 0) {
+      const double d1 = P.stat[0], d2 = fmax(0.0, (double)K - pn);
+      P.stat[1] = d2;
+      const bool ok = (d2 == d2) && d2 <= tol && (d1 <= tol || d2 <= 0.25 * d1);
+      need_cold(P) = ok ? 0 : 1;
+    }
   }
 }
 
@@ -532,8 +628,9 @@ __global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B) {
 // L x K row-major.
 // ---------------------------------------------------------------------------
 template <typename TOut>
-__global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B) {
+__global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B, int gate) {
   const EigDesc P = B.d[blockIdx.x];
+  if (gated_off(P, gate)) return;
   const int n = P.L, K = P.K;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   extern __shared__ __align__(16) double dsm[];
@@ -735,12 +832,14 @@ int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, s
     EB.batch = nb;
     char* p = static_cast<char*>(ws);
     int maxL = 1, maxK = 1;
+    bool warm = (kernel_policy() & 2) == 0;
     for (int b = 0; b < nb; ++b) {
       const EigProblem& pr = probs[b0 + b];
       EigDesc& d = EB.d[b];
       const size_t l = (size_t)pr.L, k = (size_t)pr.K;
       d.W = pr.W;
       d.F = pr.F;
+      d.F0 = pr.F0;
       d.L = pr.L;
       d.K = pr.K;
       d.V0 = reinterpret_cast<float*>(p);
@@ -753,45 +852,81 @@ int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, s
       p += align_up(l * k * 8);
       d.Y = reinterpret_cast<double*>(p);
       p += align_up(l * k * 8);
+      d.Qp = reinterpret_cast<double*>(p);
+      p += align_up(l * k * 8);
+      d.stat = reinterpret_cast<double*>(p);
+      p += align_up(64);
       maxL = std::max(maxL, pr.L);
       maxK = std::max(maxK, pr.K);
+      if (!pr.F0) warm = false;
     }
     const int smax = max_smem_optin();
     const size_t sm1 = stage1_smem(maxL, maxK);
     if (sm1 > (size_t)smax)
       return fail(TUCKER_ERR_UNSUPPORTED, "eig: matrix too large for shared memory");
+    const size_t sm3 = ((size_t)2 * maxK * maxK + (size_t)maxL * maxK) * 8 + (size_t)2 * maxK * maxK * 4;
+    if (sm3 > (size_t)smax) return fail(TUCKER_ERR_UNSUPPORTED, "eig: K too large");
     TK_CUDA_TRY(cudaFuncSetAttribute(eig_stage1_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-    eig_stage1_kernel<<<nb, kEigThreads, sm1, s>>>(EB);
-    TK_LAUNCH_CHECK("eig_stage1");
+    if (f_dtype == TUCKER_F64)
+      TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    else
+      TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
     const dim3 gmul((unsigned)((maxL + 7) / 8), (unsigned)nb);
+    auto finalize = [&](int gate) -> int {
+      if (f_dtype == TUCKER_F64)
+        eig_finalize_kernel<double><<<nb, 256, sm3, s>>>(EB, gate);
+      else
+        eig_finalize_kernel<float><<<nb, 256, sm3, s>>>(EB, gate);
+      TK_LAUNCH_CHECK("eig_finalize");
+      return TUCKER_OK;
+    };
+    int gate = 0;
+    if (warm) {
+      // warm start from the input factors: two subspace-iteration steps with
+      // an a-posteriori check, then Rayleigh-Ritz; the full path below runs
+      // only where the check failed (need-cold flag)
+      const double tol = (f_dtype == TUCKER_F64) ? 1e-18 : 1e-12;
+      if (f_dtype == TUCKER_F64)
+        eig_seed_kernel<double><<<nb, 256, 0, s>>>(EB);
+      else
+        eig_seed_kernel<float><<<nb, 256, 0, s>>>(EB);
+      TK_LAUNCH_CHECK("eig_seed");
+      eig_wmul_kernel<float><<<gmul, 256, 0, s>>>(EB, 1, 0);
+      TK_LAUNCH_CHECK("eig_wmul");
+      eig_orth_kernel<<<nb, 256, 0, s>>>(EB, 1, 0, tol);
+      TK_LAUNCH_CHECK("eig_orth");
+      eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0, 0);
+      TK_LAUNCH_CHECK("eig_wmul");
+      eig_orth_kernel<<<nb, 256, 0, s>>>(EB, 2, 0, tol);
+      TK_LAUNCH_CHECK("eig_orth");
+      eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0, 0);
+      TK_LAUNCH_CHECK("eig_wmul");
+      int rc = finalize(0);
+      if (rc) return rc;
+      gate = 1;
+    }
+    eig_stage1_kernel<<<nb, kEigThreads, sm1, s>>>(EB, gate);
+    TK_LAUNCH_CHECK("eig_stage1");
     // one subspace-iteration step: Y = W V0, Q = orth(Y / theta)
-    eig_wmul_kernel<float><<<gmul, 256, 0, s>>>(EB, 1);
+    eig_wmul_kernel<float><<<gmul, 256, 0, s>>>(EB, 1, gate);
     TK_LAUNCH_CHECK("eig_wmul");
-    eig_orth_kernel<<<nb, 256, 0, s>>>(EB);
+    eig_orth_kernel<<<nb, 256, 0, s>>>(EB, 0, gate, 0.0);
     TK_LAUNCH_CHECK("eig_orth");
     if (f_dtype == TUCKER_F64) {
       // a second step for FP64 factors
-      eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0);
+      eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0, gate);
       TK_LAUNCH_CHECK("eig_wmul");
-      eig_orth_kernel<<<nb, 256, 0, s>>>(EB);
+      eig_orth_kernel<<<nb, 256, 0, s>>>(EB, 0, gate, 0.0);
       TK_LAUNCH_CHECK("eig_orth");
     }
     // Rayleigh-Ritz on span(Q): Y = W Q, then the K x K problem
-    eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0);
+    eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0, gate);
     TK_LAUNCH_CHECK("eig_wmul");
-    const size_t sm3 = ((size_t)2 * maxK * maxK + (size_t)maxL * maxK) * 8 + (size_t)2 * maxK * maxK * 4;
-    if (sm3 > (size_t)smax) return fail(TUCKER_ERR_UNSUPPORTED, "eig: K too large");
-    if (f_dtype == TUCKER_F64) {
-      TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_kernel<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-      eig_finalize_kernel<double><<<nb, 256, sm3, s>>>(EB);
-    } else {
-      TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_kernel<float>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-      eig_finalize_kernel<float><<<nb, 256, sm3, s>>>(EB);
-    }
-    TK_LAUNCH_CHECK("eig_finalize");
+    int rc = finalize(gate);
+    if (rc) return rc;
   }
   return TUCKER_OK;
 }

@@ -10,7 +10,7 @@
 // its inputs and outputs; the scratch comes from g_eig_scratch below.
 //
 // The array lives in every GPU that loads this library until the process
-// exits (kNoallocScratchBytes, about 3.2 MiB).  Host code must not hand the
+// exits (kNoallocScratchBytes, about 4 MiB).  Host code must not hand the
 // symbol itself to a kernel (on the host it names a host-side stand-in); the
 // device address is obtained once per device with cudaGetSymbolAddress.
 #include <atomic>
@@ -24,8 +24,8 @@ namespace {
 constexpr int kNoallocMaxBatch = 8;
 constexpr int kNoallocMaxL = 200;
 constexpr int kNoallocMaxK = 64;
-// eig_ws_bytes() of kNoallocMaxBatch matrices with L = 200, K = 64
-constexpr size_t kPerMatrix = (200 * 64 * 4) + 256 + (200 * 200 * 4) + 2 * (200 * 64 * 8);
+// eig_ws_bytes() of kNoallocMaxBatch matrices with L = 200, K = 64 (~4 MiB)
+constexpr size_t kPerMatrix = eig_bytes_per_matrix(kNoallocMaxL, kNoallocMaxK);
 constexpr size_t kNoallocScratchBytes = kNoallocMaxBatch * kPerMatrix;
 
 static __device__ __align__(256) unsigned char g_eig_scratch[kNoallocScratchBytes];

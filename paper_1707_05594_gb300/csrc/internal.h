@@ -66,6 +66,15 @@ int fail(int code, const std::string& msg);
 
 uint64_t tensor_size(const Plan& p, unsigned P);
 
+// eigensolver scratch of one L x L matrix with K wanted vectors: V0 (L*K
+// floats), theta (K floats), parked reflectors (L*L floats), Q, Y and the
+// previous basis Qp (L*K doubles each), warm-start status (64 bytes)
+constexpr size_t eig_bytes_per_matrix(size_t l, size_t k) {
+  return ((l * k * 4 + kAlign - 1) / kAlign * kAlign) + ((k * 4 + kAlign - 1) / kAlign * kAlign) +
+         ((l * l * 4 + kAlign - 1) / kAlign * kAlign) + 3 * ((l * k * 8 + kAlign - 1) / kAlign * kAlign) +
+         kAlign;
+}
+
 // sizes of the eigensolver scratch for a batch of matrices
 size_t eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
 

@@ -254,13 +254,8 @@ void sthosvd_buffers(Plan& p) {
 }  // namespace
 
 size_t eig_ws_bytes(int batch, const int64_t* L, const int64_t* K) {
-  // per matrix: V0 (L*K floats), theta (K floats), parked reflectors (L*L
-  // floats), Q and Y (L*K doubles each)
   size_t total = 0;
-  for (int b = 0; b < batch; ++b) {
-    const size_t l = (size_t)L[b], k = (size_t)K[b];
-    total += align_up(l * k * 4) + align_up(k * 4) + align_up(l * l * 4) + 2 * align_up(l * k * 8);
-  }
+  for (int b = 0; b < batch; ++b) total += eig_bytes_per_matrix((size_t)L[b], (size_t)K[b]);
   return total;
 }
 

@@ -513,8 +513,8 @@ int kernel_policy() { return g_policy.load(std::memory_order_relaxed); }
 }  // namespace tk
 
 extern "C" int tucker_set_kernel_policy(int policy) {
-  if (policy != 0 && policy != 1)
-    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be 0 or 1");
+  if (policy < 0 || policy > 3)
+    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 3]");
   tk::g_policy.store(policy, std::memory_order_relaxed);
   return TUCKER_OK;
 }

@@ -134,6 +134,69 @@ def test_sweep_from_common_input_factors(tk, orc):
     np.testing.assert_allclose(Ga, Go, rtol=0, atol=1e-3 * np.abs(Go).max())
 
 
+@pytest.mark.parametrize("L,K,dtype", [((28, 22, 19, 9), (5, 4, 6, 3), torch.float32),
+                                       ((20, 17, 15), (5, 4, 6), torch.float64),
+                                       ((64, 64, 64, 64), (16, 16, 16, 16), torch.bfloat16)])
+def test_sweep_core_equals_core_of_input_factors(tk, orc, L, K, dtype):
+    """tucker_hooi_sweep_core's G_in is the Fig. 2 core of the input factors."""
+    w = workloads.planted_tucker(L, K, 0.4, 23, dtype=torch.float32)
+    T32 = w["T"]
+    T = T32.to(dtype).cuda()
+    code = {torch.float32: tk.TUCKER_F32, torch.float64: tk.TUCKER_F64,
+            torch.bfloat16: tk.TUCKER_BF16}[dtype]
+    fdt = torch.float64 if dtype == torch.float64 else torch.float32
+    F0, _ = orc.sthosvd(T32.numpy(), K)
+    plan = tk.tucker_plan(L, K, code)
+    ws = tk.workspace(plan)
+    Fin = [torch.tensor(f, dtype=fdt, device="cuda") for f in F0]
+    Fout = [torch.empty_like(f) for f in Fin]
+    G1 = torch.empty(*K, dtype=fdt, device="cuda")
+    G2 = torch.empty(*K, dtype=fdt, device="cuda")
+    tk.tucker_hooi_sweep_core(plan, T, Fin, Fout, G1, ws)
+    tk.tucker_core(plan, T, Fin, G2, ws)
+    torch.cuda.synchronize()
+    Tin = T.double().cpu().numpy()
+    Gref = orc.core(Tin, [f.double().cpu().numpy() for f in Fin])
+    scale = np.abs(Gref).max()
+    tol = {torch.float32: 1e-5, torch.float64: 1e-12, torch.bfloat16: 2e-2}[dtype]
+    np.testing.assert_allclose(G1.double().cpu().numpy(), Gref, rtol=0, atol=tol * scale)
+    np.testing.assert_allclose(G2.double().cpu().numpy(), Gref, rtol=0, atol=tol * scale)
+
+
+@pytest.mark.parametrize("L,K,rho,seed,dtype", [
+    ((24, 20, 18), (4, 3, 5), 0.5, 7, torch.float32),
+    ((30, 30, 30), (6, 4, 5), 1.0, 8, torch.float32),      # slow convergence: warm check rejects
+    ((64, 64, 64), (8, 8, 8), 1e-3, 1, torch.float64),
+    ((48, 40, 32, 24), (8, 6, 6, 4), 1e-2, 61, torch.float32),
+])
+def test_warm_started_evd_matches_full_evd(tk, orc, L, K, rho, seed, dtype):
+    """Sweeps whose eigensolver starts from the input factors (policy 0) give
+    the factors of the full eigensolver (policy 2), sweep after sweep, and both
+    match the oracle."""
+    w = workloads.planted_tucker(L, K, rho, seed, dtype=dtype)
+    outs = {}
+    for policy in (0, 2):
+        tk.tucker_set_kernel_policy(policy)
+        try:
+            gpu, _ = run_gpu(tk, w["T"], K, 0, 4)
+        finally:
+            tk.tucker_set_kernel_policy(0)
+        outs[policy] = gpu
+    fit_bar, ang_bar = bars(dtype)
+    Tn = w["T"].numpy()
+    nT2 = orc.norm2(Tn)
+    Fo, Go = orc.sthosvd(Tn, K)
+    for s in range(1, 5):
+        Fo, Go = orc.hooi_sweep(Tn, Fo, K)
+        fit_o = orc.fit(nT2, orc.norm2(Go))
+        for policy in (0, 2):
+            Fg, _, fit_g = outs[policy][s]
+            assert abs(fit_g - fit_o) <= fit_bar * fit_o, (policy, s, fit_g, fit_o)
+            for n in range(len(L)):
+                assert sin_angle(Fg[n], Fo[n]) <= ang_bar, (policy, s, n)
+                assert np.abs(Fg[n].T @ Fg[n] - np.eye(K[n])).max() <= (1e-12 if dtype == torch.float64 else 1e-6)
+
+
 def test_fit_monotone_on_gpu(tk, orc):
     L, K = (30, 26, 22), (6, 5, 4)
     w = workloads.planted_tucker(L, K, 0.9, 31, dtype=torch.float32)
