@@ -43,6 +43,8 @@ def parse():
                     choices=["optimal", "chain", "chain_k", "chain_h", "balanced"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the BF16-vs-FP32 comparison on the 64^5 workload")
     ap.add_argument("--unfused", action="store_true",
                     help="time hooi_sweep + a separate core chain + fit per step")
     ap.add_argument("--kernel-policy", type=int, default=0,
@@ -402,6 +404,8 @@ def run_ours(args, ws_size, rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if not args.no_precision:
+        out["precision_form"] = run_precision_form(args)
     if rank == 0 and ws_size == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -413,6 +417,69 @@ def run_ours(args, ws_size, rank):
                                "sample": SAMPLE_TEXT, "sample_s": round(r["sample_s"], 2),
                                "parts_s": {k: round(v, 3) for k, v in r["parts"].items()}}
     return out
+
+
+def run_precision_form(args):
+    """BF16 vs FP32 form at equal fit error on the 64^5 workload (planted core
+    16^5 with geometric 0.8 mode scaling, rho 1e-2): both start from the same
+    STHOSVD; the FP32 form runs S sweeps on the FP32 tensor, the precision form
+    runs S-2 sweeps on the BF16 copy (tensor-core TTMs, BF16 intermediates) and
+    2 FP32 polish sweeps.  Times cover the sweeps (fused-core steps); the fit is
+    taken for the final factors against the FP32 tensor."""
+    import torch
+
+    import paper_1707_05594_gb300 as tk
+    import workloads
+    spec = workloads.WORKLOADS["precision5"]
+    L, K = spec["L"], spec["K"]
+    S = int(spec["sweeps"])
+    w = workloads.make_workload("precision5", device="cuda")
+    T32 = w["T"]
+    del w
+    T16 = torch.empty(T32.shape, dtype=torch.bfloat16, device="cuda")
+    tk.tucker_convert_bf16(T32, T16)
+    p32 = tk.tucker_plan(L, K, tk.TUCKER_F32)
+    p16 = tk.tucker_plan(L, K, tk.TUCKER_BF16)
+    ws = torch.empty(max(tk.tucker_plan_cost(p32)["ws_bytes"], tk.tucker_plan_cost(p16)["ws_bytes"]),
+                     dtype=torch.uint8, device="cuda")
+    F0 = [torch.empty(L[n], K[n], device="cuda") for n in range(len(L))]
+    G = torch.empty(*K, device="cuda")
+    nt = torch.empty(1, dtype=torch.float64, device="cuda")
+    fo = torch.empty(2, dtype=torch.float64, device="cuda")
+    tk.tucker_norm2(p32, T32, nt)
+    tk.tucker_sthosvd(p32, T32, F0, G, ws)
+    torch.cuda.synchronize()
+
+    def run(schedule):
+        F = [f.clone() for f in F0]
+        Fn = [torch.empty_like(f) for f in F0]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for plan, T in schedule:
+            tk.tucker_hooi_sweep_core(plan, T, F, Fn, G, ws)
+            tk.tucker_fit(plan, G, nt, fo)
+            F, Fn = Fn, F
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tk.tucker_core(p32, T32, F, G, ws)
+        tk.tucker_fit(p32, G, nt, fo)
+        torch.cuda.synchronize()
+        return ms, fo[0].item()
+
+    run([(p32, T32)] * 2)  # warm-up
+    ms32, fit32 = run([(p32, T32)] * S)
+    ms16, fit16 = run([(p16, T16)] * (S - 2) + [(p32, T32)] * 2)
+    rel = abs(fit16 - fit32) / fit32
+    return {"workload": "64^5 planted Tucker, ranks 16, geometric 0.8 core scaling, rho 1e-2, seed 3",
+            "sweeps": S,
+            "fp32_form": {"ms_total": round(ms32, 3), "ms_per_sweep": round(ms32 / S, 4),
+                          "fit": fit32},
+            "bf16_polish_form": {"schedule": f"{S - 2} BF16 + 2 FP32", "ms_total": round(ms16, 3),
+                                 "ms_per_sweep": round(ms16 / S, 4), "fit": fit16},
+            "rel_fit_diff": rel, "bar": 1e-3, "meets_bar": rel <= 1e-3,
+            "speedup_bf16_polish_vs_fp32": round(ms32 / ms16, 3)}
 
 
 # ------------------------------------------------------ reference arm ------

@@ -212,6 +212,78 @@ __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccO
   }
 }
 
+// ---------------------------------------------------------------------------
+// ttm_rows_pipe: last mode (C == 1) with each thread owning one fibre (row r)
+// and streaming it VEC elements at a time through its private cp.async ring;
+// F is broadcast from shared memory.  Requires L % VEC == 0 and aligned rows.
+// Consecutive threads read rows L apart; the two halves of each 32-byte sector
+// are used by consecutive steps of the same thread (cp.async.ca keeps them in
+// L1 for 8-byte slots; 16-byte slots fetch whole sectors).
+// ---------------------------------------------------------------------------
+template <typename TIn, typename TOut, int KB, int VEC>
+__global__ void __launch_bounds__(kColsThreads, (KB * sizeof(typename AccOf<TIn>::type) <= 96) ? 2 : 1)
+    ttm_rows_pipe_kernel(const TIn* __restrict__ X, const typename AccOf<TIn>::type* __restrict__ F,
+                         TOut* __restrict__ Y, int64_t R, int L, int K) {
+  using A = typename AccOf<TIn>::type;
+  constexpr int SB = Slot<TIn, VEC>::kBytes;
+  __shared__ __align__(16) A Fs[kColsLChunk][KB];
+  __shared__ __align__(16) unsigned char ring[kDepth][kColsThreads][SB];
+  const int tid = threadIdx.x;
+  const int kb0 = blockIdx.y * KB;
+  const int64_t r = (int64_t)blockIdx.x * kColsThreads + tid;
+  const bool active = r < R;
+  const TIn* xp = X + (active ? r : 0) * L;
+  const int nsteps = L / VEC;
+#pragma unroll
+  for (int s = 0; s < kDepth; ++s) {
+    if (active && s < nsteps) Slot<TIn, VEC>::copy(&ring[s][tid][0], xp + s * VEC);
+    cp_async_commit();
+  }
+  A acc[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) acc[k] = A(0);
+  for (int l0 = 0; l0 < L; l0 += kColsLChunk) {
+    const int lc = min(kColsLChunk, L - l0);
+    __syncthreads();
+    for (int i = tid; i < kColsLChunk * KB; i += kColsThreads) {
+      const int l = i / KB, k = i - (i / KB) * KB;
+      Fs[l][k] = (l < lc && kb0 + k < K) ? F[(int64_t)(l0 + l) * K + kb0 + k] : A(0);
+    }
+    __syncthreads();
+    for (int ll = 0; ll < lc; ll += VEC) {
+      const int step = (l0 + ll) / VEC;
+      cp_async_wait<kDepth - 1>();
+      A x[VEC];
+      const unsigned char* slot = &ring[step % kDepth][tid][0];
+      if constexpr (sizeof(TIn) == 2) {
+        const uint2 q = *reinterpret_cast<const uint2*>(slot);
+        x[0] = __uint_as_float(q.x << 16);
+        x[1] = __uint_as_float(q.x & 0xFFFF0000u);
+        x[2] = __uint_as_float(q.y << 16);
+        x[3] = __uint_as_float(q.y & 0xFFFF0000u);
+      } else {
+        const TIn* q = reinterpret_cast<const TIn*>(slot);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) x[v] = q[v];
+      }
+      if (active && step + kDepth < nsteps)
+        Slot<TIn, VEC>::copy(&ring[step % kDepth][tid][0], xp + (step + kDepth) * VEC);
+      cp_async_commit();
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+#pragma unroll
+        for (int k = 0; k < KB; ++k) acc[k] = fma(Fs[ll + v][k], x[v], acc[k]);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (!active) return;
+  TOut* yp = Y + r * K + kb0;
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+    if (kb0 + k < K) yp[k] = OutCvt<TOut>::run(acc[k]);
+}
+
 constexpr int kRowsThreads = 128;
 constexpr int kRowsLChunk = 32;
 
@@ -267,6 +339,14 @@ template <typename TIn, typename TOut, int KB>
 int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccOf<TIn>::type* F,
               int64_t K, TOut* Y, cudaStream_t s) {
   const unsigned gy = (unsigned)((K + KB - 1) / KB);
+  constexpr int V = sizeof(TIn) == 8 ? 2 : 4;
+  if (C == 1 && L % V == 0 && (uintptr_t)X % (V * sizeof(TIn)) == 0) {
+    const int64_t gx = (R + kColsThreads - 1) / kColsThreads;
+    ttm_rows_pipe_kernel<TIn, TOut, KB, V><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
+        X, F, Y, R, (int)L, (int)K);
+    TK_LAUNCH_CHECK("ttm_rows_pipe");
+    return TUCKER_OK;
+  }
   if (C == 1) {
     const int64_t gx = (R + kRowsThreads - 1) / kRowsThreads;
     ttm_rows_kernel<TIn, TOut, KB><<<dim3((unsigned)gx, gy), kRowsThreads, 0, s>>>(X, F, Y, R,
@@ -274,7 +354,6 @@ int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccO
     TK_LAUNCH_CHECK("ttm_rows");
     return TUCKER_OK;
   }
-  constexpr int V = sizeof(TIn) == 8 ? 2 : 4;
   const bool vec_ok = (C % V == 0) && ((uintptr_t)X % (V * sizeof(TIn)) == 0) &&
                       ((uintptr_t)Y % (V * sizeof(TOut)) == 0);
   const int64_t total = R * C;

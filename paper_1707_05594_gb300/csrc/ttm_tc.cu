@@ -14,13 +14,15 @@
 // FP32 tensor): then each k-step issues a second MMA A_lo * F_hi into the
 // first half.  Accumulation is FP32 in tensor memory (TMEM).
 //
-// Warp roles (192 threads, one CTA per SM, persistent over tiles):
+// Warp roles (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0  TMA producer (one lane) through a kStages-deep shared-memory ring;
 //   warp 1  TMEM allocation and the MMA issuer (one lane);
-//   warps 2-5  epilogue: tcgen05.ld of the accumulator rows their TMEM lane
-//              quarter owns, FP32 sum of the two halves, global stores.
-// The accumulator is double-buffered in TMEM so the epilogue of tile i
-// overlaps the MMAs of tile i+1.  Every mbarrier wait is bounded by a
+//   warps 2-9  epilogue, two groups of four taking alternate tiles:
+//              tcgen05.ld of the accumulator rows their TMEM lane quarter
+//              owns, FP32 sum of the two halves, global stores.
+// Four accumulator buffers in TMEM let the epilogues of earlier tiles overlap
+// the MMAs of later ones (with one 64-wide l chunk per tile, as for L = 64, the
+// epilogue is the longest stage).  Every mbarrier wait is bounded by a
 // %globaltimer deadline; on expiry the kernel records an error word, drains
 // its own copies (bounded), frees TMEM and returns.
 #include <cuda.h>
@@ -42,7 +44,9 @@ __host__ __device__ constexpr int stages_for(bool split) { return split ? kStage
 constexpr int kBoxL = 64;                       // l per stage (128 B of BF16)
 constexpr int kTileM = 128;                     // positions per tile
 constexpr int kStageBytes = kTileM * kBoxL * 2;  // one A tensor, 16 KB
-constexpr int kThreads = 192;
+constexpr int kAccBufs = 4;      // TMEM accumulator buffers
+constexpr int kEpiGroups = 2;    // epilogue warp groups (4 warps each), alternate tiles
+constexpr int kThreads = 64 + kEpiGroups * 128;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -174,6 +178,8 @@ struct TcParams {
   int nk;         // number of 64-wide l chunks
   int64_t tiles;  // number of 128-position tiles
   int64_t ctiles; // column case: tiles per r
+  int pack2;      // column case with C == 64: one tile = two consecutive r
+  int vec_rows;   // row case: output rows 16-byte aligned (vector stores)
   const float* F; // L x K row-major (FP32)
 };
 
@@ -197,22 +203,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + ((b_bytes + 15) & ~size_t(15)));
   uint64_t* full = bars;                // kStages
   uint64_t* empty = bars + kStages;     // kStages
-  uint64_t* tfull = bars + 2 * kStages; // 2
-  uint64_t* tempty = tfull + 2;         // 2
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* tfull = bars + 2 * kStages;  // kAccBufs
+  uint64_t* tempty = tfull + kAccBufs;   // kAccBufs
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + kAccBufs);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // TMEM: two accumulator buffers of N2 columns each
+  // TMEM: kAccBufs accumulator buffers of N2 columns each
   uint32_t ncols = 32;
-  while (ncols < (uint32_t)(2 * N2)) ncols <<= 1;
+  while (ncols < (uint32_t)(kAccBufs * N2)) ncols <<= 1;
 
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kAccBufs; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 4);
     }
@@ -268,6 +274,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_load_2d(dst, &map_hi, &full[s], kc * kBoxL, r0);
             if (kSplitA) tma_load_2d(dst + kStageBytes, &map_lo, &full[s], kc * kBoxL, r0);
           } else {
+            if (P.pack2) {
+              // one {64 c, 64 l, 2 r} box: r and r+1 land 8 KB apart, the same
+              // layout as the two 64-position halves of a wide tile
+              tma_load_3d(dst, &map_hi, &full[s], 0, kc * kBoxL, (int)(2 * t));
+              if (kSplitA) tma_load_3d(dst + kStageBytes, &map_lo, &full[s], 0, kc * kBoxL, (int)(2 * t));
+              continue;
+            }
             const int64_t r = t / P.ctiles;
             const int c0 = (int)((t - r * P.ctiles) * kTileM);
             tma_load_3d(dst, &map_hi, &full[s], c0, kc * kBoxL, (int)r);
@@ -298,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t it = 0, tcount = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x, ++tcount) {
-        const uint32_t buf = tcount & 1u, aph = (tcount >> 1) & 1u;
+        const uint32_t buf = tcount % kAccBufs, aph = (tcount / kAccBufs) & 1u;
         if (!mbar_wait(&tempty[buf], aph ^ 1u, abort_flag)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + buf * (uint32_t)N2;
@@ -338,11 +351,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // group g (warps 2+4g .. 5+4g) takes every kEpiGroups-th tile
     const int q = warp & 3;            // TMEM lane quarter of this warp
     const int row = q * 32 + lane;     // accumulator row = tile position
-    uint32_t tcount = 0;
-    for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x, ++tcount) {
-      const uint32_t buf = tcount & 1u, aph = (tcount >> 1) & 1u;
+    const uint32_t group = (uint32_t)(warp - 2) / 4u;
+    uint32_t tcount = group;
+    for (int64_t t = blockIdx.x + (int64_t)group * gridDim.x; t < P.tiles;
+         t += (int64_t)kEpiGroups * gridDim.x, tcount += kEpiGroups) {
+      const uint32_t buf = tcount % kAccBufs, aph = (tcount / kAccBufs) & 1u;
       if (!mbar_wait(&tfull[buf], aph, abort_flag)) break;
       tc_fence_after();
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + buf * (uint32_t)N2;
@@ -351,13 +367,39 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld16(tbase + k0, hi);
         tmem_ld16(tbase + P.Np + k0, lo);
         tmem_wait_ld();
+        if (k0 + 16 >= P.Np) {
+          // the whole accumulator is in registers: hand the buffer back
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
         if (kRows) {
           const int64_t r = t * kTileM + row;
           if (r < P.R) {
-            TOut* yp = Y + r * P.K;
+            TOut* yp = Y + r * P.K + k0;
+            if (P.vec_rows && k0 + 16 <= P.K) {
+              // 16 consecutive outputs of this row: 16-byte vector stores
+              TOut o[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) o[j] = to_out<TOut>(hi[j] + lo[j]);
+              const uint4* src = reinterpret_cast<const uint4*>(o);
+              uint4* dst = reinterpret_cast<uint4*>(yp);
+#pragma unroll
+              for (int v = 0; v < (int)(16 * sizeof(TOut) / 16); ++v) dst[v] = src[v];
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (k0 + j < P.K) yp[j] = to_out<TOut>(hi[j] + lo[j]);
+            }
+          }
+        } else if (P.pack2) {
+          const int64_t r = 2 * t + (row >> 6);
+          const int64_t c = row & 63;
+          if (r < P.R) {
+            TOut* yp = Y + (r * P.K) * P.C + c;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              if (k0 + j < P.K) yp[k0 + j] = to_out<TOut>(hi[j] + lo[j]);
+              if (k0 + j < P.K) yp[(int64_t)(k0 + j) * P.C] = to_out<TOut>(hi[j] + lo[j]);
           }
         } else {
           const int64_t r = t / P.ctiles;
@@ -370,9 +412,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[buf]);
     }
   }
   tc_fence_before();
@@ -423,7 +462,7 @@ size_t smem_bytes(int Np, int nk, bool split_a) {
   const size_t stages = (size_t)stages_for(split_a);
   const size_t ring = stages * (split_a ? 2 : 1) * kStageBytes;
   const size_t b = (size_t)nk * 2 * Np * 128;
-  return 1024 + ring + ((b + 15) & ~size_t(15)) + (2 * stages + 4) * 8 + 16;
+  return 1024 + ring + ((b + 15) & ~size_t(15)) + (2 * stages + 2 * kAccBufs) * 8 + 16;
 }
 
 template <bool kRows, bool kSplitA, typename TOut>
@@ -464,6 +503,9 @@ int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t
   P.nk = (int)((L + kBoxL - 1) / kBoxL);
   P.F = F;
   const bool rows = (C == 1);
+  const size_t ysz = y_bf16 ? 2 : 4;
+  P.vec_rows = rows && ((uintptr_t)Y % 16 == 0) && ((size_t)K * ysz % 16 == 0);
+  P.pack2 = (!rows && C == 64) ? 1 : 0;
   CUtensorMap mh, ml;
   if (rows) {
     P.tiles = (R + kTileM - 1) / kTileM;
@@ -477,10 +519,10 @@ int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t
     if (rc) return rc;
   } else {
     P.ctiles = (C + kTileM - 1) / kTileM;
-    P.tiles = R * P.ctiles;
+    P.tiles = P.pack2 ? (R + 1) / 2 : R * P.ctiles;
     const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)L, (cuuint64_t)R};
     const cuuint64_t str[2] = {(cuuint64_t)C * 2, (cuuint64_t)C * L * 2};
-    const cuuint32_t box[3] = {64, kBoxL, 1};
+    const cuuint32_t box[3] = {64, kBoxL, P.pack2 ? 2u : 1u};
     int rc = make_map(&mh, X, 3, dims, str, box);
     if (rc) return rc;
     rc = make_map(&ml, X_lo ? X_lo : X, 3, dims, str, box);

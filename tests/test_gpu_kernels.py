@@ -70,6 +70,8 @@ TC_CASES = [
     # column case (mode not last; C % 8 == 0, C >= 64): ragged tiles, l chunks
     ((5, 200, 136), 1, 20), ((3, 37, 64), 1, 5), ((2, 64, 1000), 1, 16), ((130, 72), 0, 1),
     ((64, 64, 64, 64), 2, 16), ((4, 256, 128), 1, 33), ((96, 512), 0, 64),
+    # C == 64: two r per tile (odd R leaves the last tile half empty)
+    ((7, 64, 64), 1, 16), ((4, 100, 64), 1, 20), ((3, 5, 40, 64), 2, 7),
     # row case (last mode; L % 8 == 0)
     ((300, 64), 1, 16), ((257, 200), 1, 20), ((1000, 24), 1, 8), ((7, 9, 128), 2, 64),
 ]
