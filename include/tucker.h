@@ -170,7 +170,8 @@ int tucker_gram(int N, const int64_t* dims, const void* Z, int z_dtype, int n, d
  * W[b]: L[b] x L[b] device doubles (read only); F[b]: L[b] x K[b] row-major
  * output of type f_dtype (TUCKER_F64: double, else float), columns ordered by
  * decreasing eigenvalue, sign as in tucker_hooi_sweep.  ws: device scratch of
- * at least tucker_eig_ws_bytes(batch, L, K) bytes.  Requires L[b] <= 224. */
+ * at least tucker_eig_ws_bytes(batch, L, K) bytes.  Requires L[b] <= 200 and
+ * K[b] <= min(L[b], 64). */
 int tucker_eig_topk(int batch, const int64_t* L, const int64_t* K, const double* const* W,
                     void* const* F, int f_dtype, void* ws, size_t ws_bytes, void* stream);
 size_t tucker_eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
@@ -234,6 +235,67 @@ int tucker_set_kernel_policy(int policy);
  * pipeline wait gave up (the kernel then returned early and its output is not
  * valid).  Synchronous; reset != 0 clears the word. */
 int tucker_device_status(int* status, int reset);
+
+/* ---- Batched form: many small independent tensors ------------------------
+ * A batch holds `count` FP32 tensors with the same order N but their own
+ * lengths dims[i*N + n] and core lengths ranks[i*N + n] (i = tensor).  Each
+ * tensor is planned with its own optimal TTM-tree (Sec. 3.3); a sweep runs the
+ * trees level by level, so it is a fixed short sequence of launches, each over
+ * every tensor of the batch, that can be recorded once in a CUDA graph.  The
+ * method per tensor is tucker_hooi_sweep_core's (Fig. 2): the result equals
+ * running that call on every tensor in turn.
+ *
+ * Data are packed back to back (offsets in elements, from
+ * tucker_batch_offsets): T holds tensor i at t_off[i] (row-major), F holds
+ * factor n of tensor i (dims x ranks, row-major) at f_off[i*N + n], G holds
+ * core i at g_off[i].  Factors, cores and tensors are float; normT2 and fit
+ * are `count` doubles.  All of them are device buffers owned by the caller.
+ *
+ * Limits: every dims <= 200, every ranks <= 32 and <= the product of the
+ * other ranks of its tensor, count * N <= 65535. */
+typedef struct tucker_batch_s* tucker_batch_t;
+/* Plans the batch (host only). */
+int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* ranks,
+                      tucker_batch_t* out);
+/* Workspace bytes and the total element counts of T, F and G (any NULL). */
+int tucker_batch_info(tucker_batch_t b, size_t* ws_bytes, int64_t* t_elems, int64_t* f_elems,
+                      int64_t* g_elems);
+/* Element offsets: t_off[count], f_off[count*N], g_off[count] (any NULL). */
+int tucker_batch_offsets(tucker_batch_t b, int64_t* t_off, int64_t* f_off, int64_t* g_off);
+void tucker_batch_destroy(tucker_batch_t b);
+/* Uploads the batch's work tables into `ws` (synchronises `stream`).  Every
+ * later call of this batch must pass the same workspace. */
+int tucker_batch_prepare(tucker_batch_t b, void* ws, size_t ws_bytes, void* stream);
+/* STHOSVD of every tensor (natural mode order, as tucker_sthosvd): writes F
+ * and G. */
+int tucker_batch_sthosvd(tucker_batch_t b, const float* T, float* F, float* G, void* ws,
+                         size_t ws_bytes, void* stream);
+/* One HOOI sweep of every tensor: F_out from F_in, and G_in (if not NULL) the
+ * core of the input factors, as tucker_hooi_sweep_core.  F_out may not alias
+ * F_in. */
+int tucker_batch_sweep(tucker_batch_t b, const float* T, const float* F_in, float* F_out,
+                       float* G_in, void* ws, size_t ws_bytes, void* stream);
+/* normT2[i] = ||T_i||^2 (double accumulation). */
+int tucker_batch_norm2(tucker_batch_t b, const float* T, double* normT2, void* ws,
+                       size_t ws_bytes, void* stream);
+/* fit[i] = 1 - ||T_i - G_i x_0 F_i0 ... x_{N-1} F_i,N-1|| / ||T_i|| (Sec. 2.2's
+ * error metric) for the factors F and cores G, from the residual itself: the
+ * reconstruction is formed mode by mode and its last step is compared with
+ * T, the squared differences summed in double.  (With FP32 factors and cores
+ * the shortcut ||T||^2 - ||G||^2 of tucker_fit cancels badly when the
+ * residual is below about 1e-2 of ||T||.)  normT2 from tucker_batch_norm2. */
+int tucker_batch_fit(tucker_batch_t b, const float* T, const float* F, const float* G,
+                     const double* normT2, double* fit, void* ws, size_t ws_bytes, void* stream);
+/* Records tucker_batch_sweep (and, when G_in, normT2 and fit are all non-NULL,
+ * tucker_batch_fit of F_in and G_in) with these buffers into an executable CUDA graph
+ * (*graph_exec, a cudaGraphExec_t).  Nothing runs until
+ * tucker_batch_graph_launch; each launch is one sweep of the whole batch on
+ * the given stream.  The buffers must stay valid while the graph is used. */
+int tucker_batch_graph_create(tucker_batch_t b, const float* T, const float* F_in, float* F_out,
+                              float* G_in, const double* normT2, double* fit, void* ws,
+                              size_t ws_bytes, void** graph_exec);
+int tucker_batch_graph_launch(tucker_batch_t b, void* graph_exec, void* stream);
+void tucker_batch_graph_destroy(void* graph_exec);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* tucker_last_error(void);

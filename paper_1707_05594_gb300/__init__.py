@@ -98,6 +98,21 @@ def lib():
     L.tucker_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(ProfRec), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int)]
     L.tucker_launch_count.restype = ctypes.c_uint64
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    L.tucker_batch_plan.argtypes = [ctypes.c_int, ctypes.c_int, _i64p, _i64p, ctypes.POINTER(vp)]
+    L.tucker_batch_info.argtypes = [vp, ctypes.POINTER(sz), _i64p, _i64p, _i64p]
+    L.tucker_batch_offsets.argtypes = [vp, _i64p, _i64p, _i64p]
+    L.tucker_batch_destroy.argtypes = [vp]
+    L.tucker_batch_destroy.restype = None
+    L.tucker_batch_prepare.argtypes = [vp, vp, sz, vp]
+    L.tucker_batch_sthosvd.argtypes = [vp, vp, vp, vp, vp, sz, vp]
+    L.tucker_batch_sweep.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
+    L.tucker_batch_norm2.argtypes = [vp, vp, vp, vp, sz, vp]
+    L.tucker_batch_fit.argtypes = [vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.tucker_batch_graph_create.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, sz, ctypes.POINTER(vp)]
+    L.tucker_batch_graph_launch.argtypes = [vp, vp, vp]
+    L.tucker_batch_graph_destroy.argtypes = [vp]
+    L.tucker_batch_graph_destroy.restype = None
     L.tucker_last_error.restype = ctypes.c_char_p
     L.tucker_version.restype = ctypes.c_int
     _lib = L
@@ -369,3 +384,157 @@ class Decomposition:
 
     def fit(self) -> float:
         return float(self.fit_out[0].item())
+
+
+# ---------------------------------------------------------- batched form ---
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class BatchPlan:
+    """Owns a tucker_batch_t: `count` FP32 tensors of order N with their own
+    lengths dims[i][n] and core lengths ranks[i][n], packed back to back."""
+
+    def __init__(self, dims: Sequence[Sequence[int]], ranks: Sequence[Sequence[int]]):
+        self.count = len(dims)
+        self.N = len(dims[0]) if self.count else 0
+        flat_d = [int(x) for d in dims for x in d]
+        flat_r = [int(x) for r in ranks for x in r]
+        if len(flat_d) != self.count * self.N or len(flat_r) != self.count * self.N:
+            raise ValueError("dims and ranks need count x N entries")
+        self.dims = [tuple(int(x) for x in d) for d in dims]
+        self.ranks = [tuple(int(x) for x in r) for r in ranks]
+        h = ctypes.c_void_p()
+        _check(lib().tucker_batch_plan(self.count, self.N, _i64(flat_d), _i64(flat_r),
+                                       ctypes.byref(h)), "tucker_batch_plan")
+        self.handle = h
+        ws = ctypes.c_size_t()
+        te, fe, ge = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().tucker_batch_info(h, ctypes.byref(ws), ctypes.byref(te), ctypes.byref(fe),
+                                       ctypes.byref(ge)), "tucker_batch_info")
+        self.ws_bytes, self.t_elems, self.f_elems, self.g_elems = ws.value, te.value, fe.value, ge.value
+        t_off = (ctypes.c_int64 * self.count)()
+        f_off = (ctypes.c_int64 * (self.count * self.N))()
+        g_off = (ctypes.c_int64 * self.count)()
+        _check(lib().tucker_batch_offsets(h, t_off, f_off, g_off), "tucker_batch_offsets")
+        self.t_off, self.f_off, self.g_off = list(t_off), list(f_off), list(g_off)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tucker_batch_destroy(self.handle)
+
+    # views of the packed buffers
+    def tensor(self, T, i: int):
+        n = 1
+        for x in self.dims[i]:
+            n *= x
+        return T[self.t_off[i]:self.t_off[i] + n].view(*self.dims[i])
+
+    def factor(self, F, i: int, n: int):
+        o = self.f_off[i * self.N + n]
+        L, K = self.dims[i][n], self.ranks[i][n]
+        return F[o:o + L * K].view(L, K)
+
+    def core(self, G, i: int):
+        n = 1
+        for x in self.ranks[i]:
+            n *= x
+        return G[self.g_off[i]:self.g_off[i] + n].view(*self.ranks[i])
+
+
+def tucker_batch_prepare(b: BatchPlan, ws, stream=None):
+    _check(lib().tucker_batch_prepare(b.handle, _vp(ws), ws.numel() * ws.element_size(),
+                                      _stream(stream)), "tucker_batch_prepare")
+
+
+def tucker_batch_sthosvd(b: BatchPlan, T, F, G, ws, stream=None):
+    _check(lib().tucker_batch_sthosvd(b.handle, _vp(T), _vp(F), _vp(G), _vp(ws),
+                                      ws.numel() * ws.element_size(), _stream(stream)),
+           "tucker_batch_sthosvd")
+
+
+def tucker_batch_sweep(b: BatchPlan, T, F_in, F_out, G_in, ws, stream=None):
+    _check(lib().tucker_batch_sweep(b.handle, _vp(T), _vp(F_in), _vp(F_out), _vp(G_in), _vp(ws),
+                                    ws.numel() * ws.element_size(), _stream(stream)),
+           "tucker_batch_sweep")
+
+
+def tucker_batch_norm2(b: BatchPlan, T, normT2, ws, stream=None):
+    _check(lib().tucker_batch_norm2(b.handle, _vp(T), _vp(normT2), _vp(ws),
+                                    ws.numel() * ws.element_size(), _stream(stream)),
+           "tucker_batch_norm2")
+
+
+def tucker_batch_fit(b: BatchPlan, T, F, G, normT2, fit, ws, stream=None):
+    """fit[i] = 1 - ||T_i - G_i x F_i|| / ||T_i|| from the residual itself."""
+    _check(lib().tucker_batch_fit(b.handle, _vp(T), _vp(F), _vp(G), _vp(normT2), _vp(fit),
+                                  _vp(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "tucker_batch_fit")
+
+
+class BatchGraph:
+    """An executable CUDA graph of one batched sweep (tucker_batch_graph_*)."""
+
+    def __init__(self, b: BatchPlan, T, F_in, F_out, G_in, normT2, fit, ws):
+        self.b = b
+        self._keep = (T, F_in, F_out, G_in, normT2, fit, ws)
+        h = ctypes.c_void_p()
+        _check(lib().tucker_batch_graph_create(b.handle, _vp(T), _vp(F_in), _vp(F_out), _vp(G_in),
+                                               _vp(normT2), _vp(fit), _vp(ws),
+                                               ws.numel() * ws.element_size(), ctypes.byref(h)),
+               "tucker_batch_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().tucker_batch_graph_launch(self.b.handle, self.handle, _stream(stream)),
+               "tucker_batch_graph_launch")
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tucker_batch_graph_destroy(self.handle)
+
+
+class BatchDecomposition:
+    """Batched driver: STHOSVD, then sweeps that alternate between two factor
+    buffers (through two recorded graphs, A -> B and B -> A, or direct calls).
+    After each sweep G and fit describe the factors the sweep started from;
+    factors() is the newest factor buffer."""
+
+    def __init__(self, T, dims, ranks):
+        import torch
+        self.T = T
+        self.b = BatchPlan(dims, ranks)
+        if T.numel() != self.b.t_elems or T.dtype != torch.float32:
+            raise ValueError("T must hold the packed FP32 tensors of the batch")
+        dev = T.device
+        self.ws = torch.empty(self.b.ws_bytes, dtype=torch.uint8, device=dev)
+        tucker_batch_prepare(self.b, self.ws)
+        self.Fbuf = [torch.empty(self.b.f_elems, dtype=torch.float32, device=dev) for _ in range(2)]
+        self.cur = 0
+        self.G = torch.empty(self.b.g_elems, dtype=torch.float32, device=dev)
+        self.normT2 = torch.empty(self.b.count, dtype=torch.float64, device=dev)
+        self.fit_out = torch.empty(self.b.count, dtype=torch.float64, device=dev)
+        tucker_batch_norm2(self.b, T, self.normT2, self.ws)
+        self._graphs = None
+
+    def sthosvd(self):
+        tucker_batch_sthosvd(self.b, self.T, self.Fbuf[self.cur], self.G, self.ws)
+        tucker_batch_fit(self.b, self.T, self.Fbuf[self.cur], self.G, self.normT2, self.fit_out,
+                         self.ws)
+
+    def sweep(self, graph: bool = True):
+        src, dst = self.Fbuf[self.cur], self.Fbuf[1 - self.cur]
+        if graph:
+            if self._graphs is None:
+                A, B = self.Fbuf
+                self._graphs = (
+                    BatchGraph(self.b, self.T, A, B, self.G, self.normT2, self.fit_out, self.ws),
+                    BatchGraph(self.b, self.T, B, A, self.G, self.normT2, self.fit_out, self.ws))
+            self._graphs[self.cur].launch()
+        else:
+            tucker_batch_sweep(self.b, self.T, src, dst, self.G, self.ws)
+            tucker_batch_fit(self.b, self.T, src, self.G, self.normT2, self.fit_out, self.ws)
+        self.cur ^= 1
+
+    def factors(self):
+        return self.Fbuf[self.cur]

@@ -174,6 +174,29 @@ int launch_norm2(int dtype, const void* X, int64_t n, double* out, cudaStream_t 
 int launch_fit(int g_dtype, const void* G, int64_t n, const double* normT2, double* out,
                cudaStream_t s);
 
+// Per-matrix state of the eigensolver (pointers into its scratch).
+struct EigDesc {
+  const double* W;
+  void* F;
+  const void* F0;  // warm start: L x K row-major input factor (or NULL)
+  float* V0;       // [K][L]
+  float* theta;    // [K]
+  float* HV;       // [L][L] parked reflectors
+  double* Q;       // [K][L]
+  double* Y;       // [K][L]
+  double* Qp;      // [K][L] previous basis (warm start)
+  double* stat;    // [0] delta1, [1] delta2; ((int*)stat)[4] = need_cold flag
+  int L, K;
+};
+// Carves one matrix's scratch (eig_bytes_per_matrix(L, K) bytes at p).
+void eig_desc_layout(EigDesc& d, char* p, int L, int K);
+// The eigensolver over `count` matrices whose descriptors are in device
+// memory (dev; their F / F0 fields are byte offsets from f_base / f0_base),
+// with maxL / maxK bounding every L / K.  A non-NULL f0_base selects the warm
+// start from the input factors, with the gated full-path fallback.
+int launch_eig_batched(const EigDesc* dev, int count, int maxL, int maxK, int f_dtype,
+                       char* f_base, const char* f0_base, cudaStream_t s);
+
 struct EigProblem {
   const double* W;         // L x L
   void* F;                 // L x K output

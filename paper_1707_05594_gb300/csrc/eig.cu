@@ -38,23 +38,24 @@ constexpr int kMaxEigL = 200;
 constexpr int kMaxEigK = 64;
 constexpr int kMaxBatch = TUCKER_MAX_MODES;
 
-struct EigDesc {
-  const double* W;
-  void* F;
-  const void* F0;  // warm start: L x K row-major input factor (or NULL)
-  float* V0;       // [K][L]
-  float* theta;    // [K]
-  float* HV;       // [L][L] parked reflectors
-  double* Q;       // [K][L]
-  double* Y;       // [K][L]
-  double* Qp;      // [K][L] previous basis (warm start)
-  double* stat;    // [0] delta1, [1] delta2; ((int*)stat)[4] = need_cold flag
-  int L, K;
-};
+// Descriptors come either by value (up to kMaxBatch matrices) or, for large
+// batches, from a device array (dev != NULL).
+// In a device array F and F0 are byte offsets from f_base / f0_base (so the
+// table does not change when the caller swaps factor buffers).
 struct EigBatch {
   EigDesc d[kMaxBatch];
   int batch;
+  const EigDesc* dev;
+  char* f_base;
+  const char* f0_base;
 };
+__device__ __forceinline__ EigDesc get_desc(const EigBatch& B, unsigned i) {
+  if (!B.dev) return B.d[i];
+  EigDesc d = B.dev[i];
+  d.F = B.f_base + reinterpret_cast<size_t>(d.F);
+  d.F0 = B.f0_base ? static_cast<const void*>(B.f0_base + reinterpret_cast<size_t>(d.F0)) : nullptr;
+  return d;
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -114,7 +115,7 @@ __device__ __forceinline__ bool gated_off(const EigDesc& P, int gate) {
 // Starting subspace from the input factor: V0[c][r] = F0[r][c].
 template <typename TF>
 __global__ void __launch_bounds__(256) eig_seed_kernel(const EigBatch B) {
-  const EigDesc P = B.d[blockIdx.x];
+  const EigDesc P = get_desc(B, blockIdx.x);
   const TF* F0 = static_cast<const TF*>(P.F0);
   for (int idx = threadIdx.x; idx < P.L * P.K; idx += 256) {
     const int r = idx / P.K, c = idx - (idx / P.K) * P.K;
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(256) eig_seed_kernel(const EigBatch B) {
 // Stage 1: FP32 tridiagonalisation, bisection, inverse iteration, back-transform.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch B, int gate) {
-  const EigDesc P = B.d[blockIdx.x];
+  const EigDesc P = get_desc(B, blockIdx.x);
   if (gated_off(P, gate)) return;
   const int n = P.L, K = P.K, LD = n | 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch 
 // ---------------------------------------------------------------------------
 template <typename TIn>
 __global__ void __launch_bounds__(256) eig_wmul_kernel(const EigBatch B, int use_v0, int gate) {
-  const EigDesc P = B.d[blockIdx.y];
+  const EigDesc P = get_desc(B, blockIdx.y);
   if (gated_off(P, gate)) return;
   const int n = P.L, K = P.K;
   const int lane = threadIdx.x & 31;
@@ -539,7 +540,7 @@ __device__ double proj_norm2(const TA* A, const double* Q, int n, int K, double*
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B, int mode, int gate,
                                                        double tol) {
-  const EigDesc P = B.d[blockIdx.x];
+  const EigDesc P = get_desc(B, blockIdx.x);
   if (gated_off(P, gate)) return;
   const int n = P.L, K = P.K;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -629,7 +630,7 @@ __global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B, int mod
 // ---------------------------------------------------------------------------
 template <typename TOut>
 __global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B, int gate) {
-  const EigDesc P = B.d[blockIdx.x];
+  const EigDesc P = get_desc(B, blockIdx.x);
   if (gated_off(P, gate)) return;
   const int n = P.L, K = P.K;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -813,6 +814,11 @@ int sm_count() {
   return cached[dev];
 }
 
+namespace {
+int run_eig(const EigBatch& EB, int nb, int maxL, int maxK, int f_dtype, bool warm,
+            cudaStream_t s);
+}  // namespace
+
 int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, size_t ws_bytes,
                     cudaStream_t s) {
   if (batch <= 0) return TUCKER_OK;
@@ -830,36 +836,49 @@ int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, s
     if (!ws || ws_bytes < need) return fail(TUCKER_ERR_WORKSPACE, "eig: workspace too small");
     EigBatch EB{};
     EB.batch = nb;
+    EB.dev = nullptr;
     char* p = static_cast<char*>(ws);
     int maxL = 1, maxK = 1;
     bool warm = (kernel_policy() & 2) == 0;
     for (int b = 0; b < nb; ++b) {
       const EigProblem& pr = probs[b0 + b];
       EigDesc& d = EB.d[b];
-      const size_t l = (size_t)pr.L, k = (size_t)pr.K;
+      eig_desc_layout(d, p, pr.L, pr.K);
+      p += eig_bytes_per_matrix((size_t)pr.L, (size_t)pr.K);
       d.W = pr.W;
       d.F = pr.F;
       d.F0 = pr.F0;
-      d.L = pr.L;
-      d.K = pr.K;
-      d.V0 = reinterpret_cast<float*>(p);
-      p += align_up(l * k * 4);
-      d.theta = reinterpret_cast<float*>(p);
-      p += align_up(k * 4);
-      d.HV = reinterpret_cast<float*>(p);
-      p += align_up(l * l * 4);
-      d.Q = reinterpret_cast<double*>(p);
-      p += align_up(l * k * 8);
-      d.Y = reinterpret_cast<double*>(p);
-      p += align_up(l * k * 8);
-      d.Qp = reinterpret_cast<double*>(p);
-      p += align_up(l * k * 8);
-      d.stat = reinterpret_cast<double*>(p);
-      p += align_up(64);
       maxL = std::max(maxL, pr.L);
       maxK = std::max(maxK, pr.K);
       if (!pr.F0) warm = false;
     }
+    const int rc = run_eig(EB, nb, maxL, maxK, f_dtype, warm, s);
+    if (rc) return rc;
+  }
+  return TUCKER_OK;
+}
+
+int launch_eig_batched(const EigDesc* dev, int count, int maxL, int maxK, int f_dtype,
+                       char* f_base, const char* f0_base, cudaStream_t s) {
+  if (count <= 0) return TUCKER_OK;
+  if (maxL > kMaxEigL || maxK > kMaxEigK || maxK > maxL)
+    return fail(TUCKER_ERR_UNSUPPORTED, "eig: need K <= min(L, 64) and L <= 200");
+  if (count > 65535) return fail(TUCKER_ERR_UNSUPPORTED, "eig: at most 65535 matrices per launch");
+  EigBatch EB{};
+  EB.batch = count;
+  EB.dev = dev;
+  EB.f_base = f_base;
+  EB.f0_base = f0_base;
+  const bool warm = f0_base != nullptr && (kernel_policy() & 2) == 0;
+  return run_eig(EB, count, maxL, maxK, f_dtype, warm, s);
+}
+
+namespace {
+
+// The launch sequence for nb matrices described by EB (by value or device).
+int run_eig(const EigBatch& EB, int nb, int maxL, int maxK, int f_dtype, bool warm,
+            cudaStream_t s) {
+  {
     const int smax = max_smem_optin();
     const size_t sm1 = stage1_smem(maxL, maxK);
     if (sm1 > (size_t)smax)
@@ -929,6 +948,28 @@ int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, s
     if (rc) return rc;
   }
   return TUCKER_OK;
+}
+
+}  // namespace
+
+void eig_desc_layout(EigDesc& d, char* p, int L, int K) {
+  const size_t l = (size_t)L, k = (size_t)K;
+  d.L = L;
+  d.K = K;
+  d.F0 = nullptr;
+  d.V0 = reinterpret_cast<float*>(p);
+  p += align_up(l * k * 4);
+  d.theta = reinterpret_cast<float*>(p);
+  p += align_up(k * 4);
+  d.HV = reinterpret_cast<float*>(p);
+  p += align_up(l * l * 4);
+  d.Q = reinterpret_cast<double*>(p);
+  p += align_up(l * k * 8);
+  d.Y = reinterpret_cast<double*>(p);
+  p += align_up(l * k * 8);
+  d.Qp = reinterpret_cast<double*>(p);
+  p += align_up(l * k * 8);
+  d.stat = reinterpret_cast<double*>(p);
 }
 
 }  // namespace tk

@@ -149,3 +149,33 @@ def test_elems_cost_model(tk, orc):
         assert cm["tree_macs"] <= ce["tree_macs"]
         labels, parents, _ = tree_of(tk, pe)
         assert orc.tree_cost(L, K, labels, parents) == ce["tree_macs"]
+
+
+def test_batch_plan_layout(tk):
+    """The batched form packs tensors, factors and cores back to back in the
+    order of the batch (host only)."""
+    import math
+
+    import workloads
+    dims, ranks = workloads.batch_shapes(37, 4)
+    b = tk.BatchPlan(dims, ranks)
+    sizes = [math.prod(d) for d in dims]
+    assert b.t_elems == sum(sizes)
+    assert b.t_off == [sum(sizes[:i]) for i in range(37)]
+    fs = [dims[i][n] * ranks[i][n] for i in range(37) for n in range(3)]
+    assert b.f_off == [sum(fs[:j]) for j in range(len(fs))]
+    assert b.f_elems == sum(fs)
+    gs = [math.prod(r) for r in ranks]
+    assert b.g_off == [sum(gs[:i]) for i in range(37)] and b.g_elems == sum(gs)
+    assert b.ws_bytes > 4 * b.t_elems // 10
+
+
+@pytest.mark.parametrize("dims,ranks,msg", [
+    ([(20, 20, 201)], [(4, 4, 4)], "L_n <= 200"),
+    ([(40, 40, 40)], [(33, 33, 33)], "K_n <= 32"),
+    ([(10, 10, 10)], [(9, 1, 1)], "product of the other"),
+])
+def test_batch_plan_validation(tk, dims, ranks, msg):
+    with pytest.raises(tk.TuckerError) as e:
+        tk.BatchPlan(dims, ranks)
+    assert msg in str(e.value)

@@ -16,6 +16,11 @@ random data, Sec. 6 "Tensors"):
                1e-2 relative noise, ranks 16, seed 3 (stored BF16).
   uneven6      64x56x48x40x32x24, core 16x14x12x10x8x6 N(0,1), Student-t
                (nu = 3) noise at 1e-2 relative, seed 5 (stored BF16).
+  batch4096    4096 independent 3-way FP32 tensors: every mode length uniform
+               on [16, 96], every rank uniform on [4, min(16, length)], core
+               N(0,1), QR factors, 1e-3 relative Gaussian noise; tensor i is
+               drawn from seed 1000003 * seed + i (so the first m tensors of
+               any batch with the same seed agree), batch seed 4.
 """
 from __future__ import annotations
 
@@ -136,6 +141,46 @@ WORKLOADS = {
                        noise="gauss", dtype=torch.float32, sweeps=10),
     "uneven6": dict(L=(64, 56, 48, 40, 32, 24), K=(16, 14, 12, 10, 8, 6), rho=1e-2, seed=5,
                     spectrum=None, noise="student_t3", dtype=torch.float32, sweeps=8),
+}
+
+
+def batch_shapes(count: int, seed: int, N: int = 3, lmin: int = 16, lmax: int = 96,
+                 kmin: int = 4, kmax: int = 16):
+    """Per-tensor mode lengths and ranks of a batch: L uniform on [lmin, lmax],
+    K uniform on [kmin, min(kmax, L)] (integers, bounds included).  Row i is
+    drawn from its own generator, so a shorter batch is a prefix of a longer
+    one with the same seed."""
+    dims, ranks = [], []
+    for i in range(count):
+        g = _gen(7919 * seed + i, torch.device("cpu"))
+        L = torch.randint(lmin, lmax + 1, (N,), generator=g)
+        u = torch.rand(N, generator=g, dtype=torch.float64)
+        hi = torch.clamp(L, max=kmax)
+        K = torch.minimum(kmin + torch.floor(u * (hi - kmin + 1).double()).long(), hi)
+        dims.append(tuple(int(x) for x in L))
+        ranks.append(tuple(int(x) for x in K))
+    return dims, ranks
+
+
+def planted_batch(count: int, seed: int, rho: float = 1e-3, N: int = 3, device="cpu",
+                  lmin: int = 16, lmax: int = 96, kmin: int = 4, kmax: int = 16):
+    """`count` planted Tucker tensors (FP32) packed back to back, row-major each.
+    Returns dict(T flat tensor, dims, ranks, t_off)."""
+    dims, ranks = batch_shapes(count, seed, N, lmin, lmax, kmin, kmax)
+    sizes = [math.prod(d) for d in dims]
+    t_off = [0]
+    for n in sizes[:-1]:
+        t_off.append(t_off[-1] + n)
+    T = torch.empty(sum(sizes), dtype=torch.float32, device=device)
+    for i in range(count):
+        w = planted_tucker(dims[i], ranks[i], rho, 1000003 * seed + i, dtype=torch.float32,
+                           device=device, build_dtype=torch.float64)
+        T[t_off[i]:t_off[i] + sizes[i]] = w["T"].reshape(-1)
+    return {"T": T, "dims": dims, "ranks": ranks, "t_off": t_off}
+
+
+BATCH_WORKLOADS = {
+    "batch4096": dict(count=4096, seed=4, rho=1e-3, sweeps=5),
 }
 
 
