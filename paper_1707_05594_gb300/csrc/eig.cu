@@ -114,8 +114,7 @@ __device__ __forceinline__ bool gated_off(const EigDesc& P, int gate) {
 
 // Starting subspace from the input factor: V0[c][r] = F0[r][c].
 template <typename TF>
-__global__ void __launch_bounds__(256) eig_seed_kernel(const EigBatch B) {
-  const EigDesc P = get_desc(B, blockIdx.x);
+__device__ __forceinline__ void eig_seed_body(const EigDesc& P) {
   const TF* F0 = static_cast<const TF*>(P.F0);
   for (int idx = threadIdx.x; idx < P.L * P.K; idx += 256) {
     const int r = idx / P.K, c = idx - (idx / P.K) * P.K;
@@ -123,12 +122,15 @@ __global__ void __launch_bounds__(256) eig_seed_kernel(const EigBatch B) {
   }
 }
 
+template <typename TF>
+__global__ void __launch_bounds__(256) eig_seed_kernel(const EigBatch B) {
+  for (unsigned m = blockIdx.x; m < (unsigned)B.batch; m += gridDim.x) eig_seed_body<TF>(get_desc(B, m));
+}
+
 // ---------------------------------------------------------------------------
 // Stage 1: FP32 tridiagonalisation, bisection, inverse iteration, back-transform.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch B, int gate) {
-  const EigDesc P = get_desc(B, blockIdx.x);
-  if (gated_off(P, gate)) return;
+__device__ __forceinline__ void eig_stage1_body(const EigDesc& P) {
   const int n = P.L, K = P.K, LD = n | 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   extern __shared__ __align__(16) float sm[];
@@ -463,44 +465,98 @@ __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch 
   for (int t = tid; t < K; t += kEigThreads) P.theta[t] = lam[t];
 }
 
+// Matrices are taken in a grid-stride loop, so a gated launch costs one flag
+// read per matrix; the barrier keeps the previous matrix's shared data live
+// until every thread is done with it.
+__global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch B, int gate) {
+  for (unsigned m = blockIdx.x; m < (unsigned)B.batch; m += gridDim.x) {
+    const EigDesc P = get_desc(B, m);
+    if (gated_off(P, gate)) continue;
+    __syncthreads();
+    eig_stage1_body(P);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Out[c][r] = sum_j W[r][j] * In[c][j] in FP64 (In: [K][L], float or double).
-// One warp per row r; lanes split j.
+// A block computes 32 rows r and every column c; W and In pass through shared
+// memory in chunks of 32 j.  Thread t owns row r0 + t % 32 and the columns
+// c = t / 32 + 8 q, so W is read with one row per lane and In is broadcast:
+// the FP64 multiply-adds are the whole inner loop.
 // ---------------------------------------------------------------------------
-template <typename TIn>
+constexpr int kMulJ = 32;
+
+template <typename TIn, int ROWS>
 __global__ void __launch_bounds__(256) eig_wmul_kernel(const EigBatch B, int use_v0, int gate) {
-  const EigDesc P = get_desc(B, blockIdx.y);
-  if (gated_off(P, gate)) return;
-  const int n = P.L, K = P.K;
-  const int lane = threadIdx.x & 31;
-  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (r >= n) return;
-  const double* wr = P.W + (int64_t)r * n;
-  double* out = P.Y;
-  const TIn* in = use_v0 ? reinterpret_cast<const TIn*>(P.V0) : reinterpret_cast<const TIn*>(P.Q);
-  for (int c0 = 0; c0 < K; c0 += 32) {
-    const int cn = min(32, K - c0);
-    double acc[32];
+  constexpr int kGroups = 256 / ROWS;                       // column groups
+  constexpr int kCPer = (kMaxEigK + kGroups - 1) / kGroups;  // columns per thread
+  __shared__ double Ws[ROWS][kMulJ + 1];
+  __shared__ double Vs[kMulJ][kMaxEigK + 1];
+  const int tid = threadIdx.x, rl = tid % ROWS, cg = tid / ROWS;
+  const int r0 = blockIdx.x * ROWS;
+  for (unsigned m = blockIdx.y; m < (unsigned)B.batch; m += gridDim.y) {
+    const EigDesc P = get_desc(B, m);
+    if (gated_off(P, gate)) continue;
+    const int n = P.L, K = P.K;
+    if (r0 >= n) continue;
+    const TIn* in = use_v0 ? reinterpret_cast<const TIn*>(P.V0) : reinterpret_cast<const TIn*>(P.Q);
+    double acc[kCPer];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-    for (int j = lane; j < n; j += 32) {
-      const double w = wr[j];
+    for (int q = 0; q < kCPer; ++q) acc[q] = 0.0;
+    for (int j0 = 0; j0 < n; j0 += kMulJ) {
+      __syncthreads();
+      for (int i = tid; i < ROWS * kMulJ; i += 256) {
+        const int rr = i / kMulJ, jj = i % kMulJ;
+        const int r = r0 + rr, j = j0 + jj;
+        Ws[rr][jj] = (r < n && j < n) ? P.W[(int64_t)r * n + j] : 0.0;
+      }
+      for (int i = tid; i < K * kMulJ; i += 256) {
+        const int c = i / kMulJ, jj = i % kMulJ;
+        const int j = j0 + jj;
+        Vs[jj][c] = j < n ? (double)in[(int64_t)c * n + j] : 0.0;
+      }
+      __syncthreads();
+      // one branch around a whole run of multiply-adds per column: the
+      // condition is the same for the lanes of a warp (all of them for
+      // 32-row blocks), so absent columns issue no FP64 instructions
 #pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c < cn) acc[c] = fma(w, (double)in[(int64_t)(c0 + c) * n + j], acc[c]);
+      for (int q = 0; q < kCPer; ++q) {
+        const int c = cg + kGroups * q;
+        if (c < K) {
+          double a = acc[q];
+#pragma unroll 8
+          for (int jj = 0; jj < kMulJ; ++jj) a = fma(Ws[rl][jj], Vs[jj][c], a);
+          acc[q] = a;
+        }
+      }
     }
+    const int r = r0 + rl;
+    if (r < n) {
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      if (c < cn) {
-        const double s = warp_sum(acc[c]);
-        if (lane == 0) out[(int64_t)(c0 + c) * n + r] = s;
+      for (int q = 0; q < kCPer; ++q) {
+        const int c = cg + kGroups * q;
+        if (c < K) P.Y[(int64_t)c * n + r] = acc[q];
       }
     }
   }
 }
 
+// Y = W In for every matrix of the batch: 32-row blocks when the batch alone
+// fills the GPU, 8-row blocks (four times the blocks) otherwise.
+template <typename TIn>
+void launch_wmul(const EigBatch& EB, int nb, int maxL, int use_v0, int gate, cudaStream_t s) {
+  const int rows = ((int64_t)nb * ((maxL + 31) / 32) >= 2 * (int64_t)sm_count()) ? 32 : 8;
+  const int per_y = (maxL + rows - 1) / rows;
+  const int cap = std::max(1, 8 * sm_count() / per_y);
+  const dim3 g((unsigned)per_y, (unsigned)std::min(nb, cap));
+  if (rows == 32)
+    eig_wmul_kernel<TIn, 32><<<g, 256, 0, s>>>(EB, use_v0, gate);
+  else
+    eig_wmul_kernel<TIn, 8><<<g, 256, 0, s>>>(EB, use_v0, gate);
+}
+
 // Block sum in FP64 for 256 threads; every thread receives the result.
-__device__ double block_sum256(double v, double* red) {
+__device__ __forceinline__ double block_sum256(double v, double* red) {
   __syncthreads();
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -513,7 +569,7 @@ __device__ double block_sum256(double v, double* red) {
 
 // sum over a, b < K of (A_a . Q_b)^2 for [K][n] bases A (float or double) and Q
 template <typename TA>
-__device__ double proj_norm2(const TA* A, const double* Q, int n, int K, double* red) {
+__device__ __forceinline__ double proj_norm2(const TA* A, const double* Q, int n, int K, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc = 0.0;
   for (int idx = warp; idx < K * K; idx += 8) {
@@ -527,9 +583,101 @@ __device__ double proj_norm2(const TA* A, const double* Q, int n, int K, double*
   return block_sum256(acc, red);
 }
 
+// One Cholesky-QR pass on the K columns of length n held in shared memory
+// (Qs[c * n + r]): S = Qs^T Qs, S = R^T R, Qs <- Qs R^-1.  Returns false (and
+// leaves Qs unchanged) when a pivot is not clearly positive, i.e. when the
+// columns are too far from independent for this pass to be accurate.
+__device__ __forceinline__ bool chol_qr_pass(double* Qs, double* S, int n, int K) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int bad;
+  // S (upper triangle), a warp per entry
+  for (int idx = warp; idx < K * K; idx += 8) {
+    const int a = idx / K, b = idx - (idx / K) * K;
+    if (a > b) continue;
+    double acc = 0.0;
+    for (int r = lane; r < n; r += 32) acc = fma(Qs[a * n + r], Qs[b * n + r], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) S[a * K + b] = acc;
+  }
+  __syncthreads();
+  // Cholesky S = R^T R in place (upper triangle), by warp 0: row j of R is
+  // finished before row j + 1 starts; lanes take the entries of a row
+  if (warp == 0) {
+    double smax = 0.0;
+    for (int j = 0; j < K; ++j) smax = fmax(smax, S[j * K + j]);
+    int fail = 0;
+    for (int j = 0; j < K && !fail; ++j) {
+      double d = 0.0;
+      for (int a = lane; a < j; a += 32) d = fma(S[a * K + j], S[a * K + j], d);
+      d = S[j * K + j] - warp_sum(d);
+      // a pivot below 1e-10 of the largest diagonal entry means the columns
+      // are close to dependent (cond > ~1e5): leave it to Gram-Schmidt
+      if (!(d > 1e-10 * smax)) {
+        fail = 1;
+        break;
+      }
+      const double rjj = sqrt(d);
+      __syncwarp();
+      for (int b = j + 1 + lane; b < K; b += 32) {
+        double v = S[j * K + b];
+        for (int a = 0; a < j; ++a) v -= S[a * K + j] * S[a * K + b];
+        S[j * K + b] = v / rjj;
+      }
+      __syncwarp();
+      if (lane == 0) S[j * K + j] = rjj;
+      __syncwarp();
+    }
+    if (lane == 0) bad = fail;
+  }
+  __syncthreads();
+  if (bad) return false;
+  // Qs <- Qs R^-1, row by row (forward substitution along c)
+  for (int r = tid; r < n; r += 256) {
+    for (int c = 0; c < K; ++c) {
+      double v = Qs[c * n + r];
+      for (int a = 0; a < c; ++a) v -= S[a * K + c] * Qs[a * n + r];
+      Qs[c * n + r] = v / S[c * K + c];
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Classical Gram-Schmidt applied twice, column by column (the fallback of
+// chol_qr_pass for nearly dependent columns).
+__device__ __forceinline__ void cgs2(double* Q, int n, int K, double* dots, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = 0; j < K; ++j) {
+    double* qj = Q + (int64_t)j * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = warp; i < j; i += 8) {
+        const double* qi = Q + (int64_t)i * n;
+        double s = 0.0;
+        for (int r = lane; r < n; r += 32) s += qi[r] * qj[r];
+        s = warp_sum(s);
+        if (lane == 0) dots[i] = s;
+      }
+      __syncthreads();
+      for (int r = tid; r < n; r += 256) {
+        double v = qj[r];
+        for (int i = 0; i < j; ++i) v -= dots[i] * Q[(int64_t)i * n + r];
+        qj[r] = v;
+      }
+      __syncthreads();
+    }
+    double s = 0.0;
+    for (int r = tid; r < n; r += 256) s += qj[r] * qj[r];
+    const double tot = block_sum256(s, red);
+    const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+    for (int r = tid; r < n; r += 256) qj[r] *= inv;
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Q = orth(Y diag(1/theta)) by classical Gram-Schmidt applied twice, in FP64,
-// column by column in eigenvalue order.  Writes Q.
+// Q = orth(Y diag(1/theta)) in FP64, in shared memory: two Cholesky-QR passes
+// (CholeskyQR2), or Gram-Schmidt applied twice where the first Cholesky pass
+// finds the scaled columns nearly dependent.  Writes Q.
 //   mode 0 (full path): theta from stage 1, a negligible theta falls back to V0;
 //   mode 1 (warm step 1): theta_j = V0_j . Y_j (Rayleigh quotient of the
 //     starting vector); records delta1 = K - ||V0^T Q||_F^2 and keeps Q in Qp;
@@ -537,17 +685,17 @@ __device__ double proj_norm2(const TA* A, const double* Q, int n, int K, double*
 //     ||Qp^T Q||_F^2 and accepts the warm result when delta2 <= tol and the
 //     iteration contracts (delta2 <= delta1 / 4, or delta1 <= tol too);
 //     otherwise it raises the need-cold flag for the full path.
+// Dynamic shared memory: (K * L + K * K) doubles.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B, int mode, int gate,
-                                                       double tol) {
-  const EigDesc P = get_desc(B, blockIdx.x);
-  if (gated_off(P, gate)) return;
+__device__ __forceinline__ void eig_orth_body(const EigDesc& P, int mode, double tol) {
   const int n = P.L, K = P.K;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ double dots[kMaxEigK];
   __shared__ double th[kMaxEigK];
   __shared__ double red[8];
-  double* Q = P.Q;
+  extern __shared__ __align__(16) double osm[];
+  double* Qs = osm;             // [K][n]
+  double* S = osm + K * n;      // [K][K]
   if (mode == 0) {
     float tmax = 0.f;
     for (int t = 0; t < K; ++t) tmax = fmaxf(tmax, fabsf(P.theta[t]));
@@ -573,50 +721,41 @@ __global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B, int mod
     const int t = i / n;
     const double v = th[t];
     if (fabs(v) > 1e-30 * tmx && v != 0.0) {
-      Q[i] = P.Y[i] / v;
+      Qs[i] = P.Y[i] / v;
     } else {
-      Q[i] = (mode == 2) ? P.Qp[i] : (double)P.V0[i];
+      Qs[i] = (mode == 2) ? P.Qp[i] : (double)P.V0[i];
     }
   }
   __syncthreads();
-  for (int j = 0; j < K; ++j) {
-    double* qj = Q + (int64_t)j * n;
-    for (int pass = 0; pass < 2; ++pass) {
-      // dots with the previous columns (warp per column)
-      for (int i = warp; i < j; i += 8) {
-        const double* qi = Q + (int64_t)i * n;
-        double s = 0.0;
-        for (int r = lane; r < n; r += 32) s += qi[r] * qj[r];
-        s = warp_sum(s);
-        if (lane == 0) dots[i] = s;
-      }
-      __syncthreads();
-      for (int r = tid; r < n; r += 256) {
-        double v = qj[r];
-        for (int i = 0; i < j; ++i) v -= dots[i] * Q[(int64_t)i * n + r];
-        qj[r] = v;
-      }
-      __syncthreads();
-    }
-    double s = 0.0;
-    for (int r = tid; r < n; r += 256) s += qj[r] * qj[r];
-    const double tot = block_sum256(s, red);
-    const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
-    for (int r = tid; r < n; r += 256) qj[r] *= inv;
-    __syncthreads();
+  if (chol_qr_pass(Qs, S, n, K)) {
+    if (!chol_qr_pass(Qs, S, n, K)) cgs2(Qs, n, K, dots, red);
+  } else {
+    cgs2(Qs, n, K, dots, red);
   }
+  double* Q = P.Q;
+  for (int i = tid; i < K * n; i += 256) Q[i] = Qs[i];
   if (mode == 1) {
-    const double pn = proj_norm2<float>(P.V0, Q, n, K, red);
-    for (int i = tid; i < K * n; i += 256) P.Qp[i] = Q[i];
+    const double pn = proj_norm2<float>(P.V0, Qs, n, K, red);
+    for (int i = tid; i < K * n; i += 256) P.Qp[i] = Qs[i];
     if (tid == 0) P.stat[0] = fmax(0.0, (double)K - pn);
   } else if (mode == 2) {
-    const double pn = proj_norm2<double>(P.Qp, Q, n, K, red);
+    const double pn = proj_norm2<double>(P.Qp, Qs, n, K, red);
     if (tid == 0) {
       const double d1 = P.stat[0], d2 = fmax(0.0, (double)K - pn);
       P.stat[1] = d2;
       const bool ok = (d2 == d2) && d2 <= tol && (d1 <= tol || d2 <= 0.25 * d1);
       need_cold(P) = ok ? 0 : 1;
     }
+  }
+}
+
+__global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B, int mode, int gate,
+                                                       double tol) {
+  for (unsigned m = blockIdx.x; m < (unsigned)B.batch; m += gridDim.x) {
+    const EigDesc P = get_desc(B, m);
+    if (gated_off(P, gate)) continue;
+    __syncthreads();
+    eig_orth_body(P, mode, tol);
   }
 }
 
@@ -629,9 +768,7 @@ __global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B, int mod
 // L x K row-major.
 // ---------------------------------------------------------------------------
 template <typename TOut>
-__global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B, int gate) {
-  const EigDesc P = get_desc(B, blockIdx.x);
-  if (gated_off(P, gate)) return;
+__device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
   const int n = P.L, K = P.K;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   extern __shared__ __align__(16) double dsm[];
@@ -781,6 +918,16 @@ __global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B, int
   }
 }
 
+template <typename TOut>
+__global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B, int gate) {
+  for (unsigned m = blockIdx.x; m < (unsigned)B.batch; m += gridDim.x) {
+    const EigDesc P = get_desc(B, m);
+    if (gated_off(P, gate)) continue;
+    __syncthreads();
+    eig_finalize_body<TOut>(P);
+  }
+}
+
 size_t stage1_smem(int L, int K) {
   const size_t LD = (size_t)(L | 1);
   const size_t reg0 = std::max((size_t)L * LD, (size_t)kInvArrays * L * kInvLD);
@@ -880,6 +1027,8 @@ int run_eig(const EigBatch& EB, int nb, int maxL, int maxK, int f_dtype, bool wa
             cudaStream_t s) {
   {
     const int smax = max_smem_optin();
+    // grids of at most a few blocks per SM; kernels loop over their matrices
+    const int gb = std::min(nb, 8 * sm_count());
     const size_t sm1 = stage1_smem(maxL, maxK);
     if (sm1 > (size_t)smax)
       return fail(TUCKER_ERR_UNSUPPORTED, "eig: matrix too large for shared memory");
@@ -893,12 +1042,15 @@ int run_eig(const EigBatch& EB, int nb, int maxL, int maxK, int f_dtype, bool wa
     else
       TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_kernel<float>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    const dim3 gmul((unsigned)((maxL + 7) / 8), (unsigned)nb);
+    const size_t smo = ((size_t)maxK * maxL + (size_t)maxK * maxK) * 8;
+    if (smo > (size_t)smax) return fail(TUCKER_ERR_UNSUPPORTED, "eig: L * K too large");
+    TK_CUDA_TRY(cudaFuncSetAttribute(eig_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smo));
     auto finalize = [&](int gate) -> int {
       if (f_dtype == TUCKER_F64)
-        eig_finalize_kernel<double><<<nb, 256, sm3, s>>>(EB, gate);
+        eig_finalize_kernel<double><<<gb, 256, sm3, s>>>(EB, gate);
       else
-        eig_finalize_kernel<float><<<nb, 256, sm3, s>>>(EB, gate);
+        eig_finalize_kernel<float><<<gb, 256, sm3, s>>>(EB, gate);
       TK_LAUNCH_CHECK("eig_finalize");
       return TUCKER_OK;
     };
@@ -909,40 +1061,40 @@ int run_eig(const EigBatch& EB, int nb, int maxL, int maxK, int f_dtype, bool wa
       // only where the check failed (need-cold flag)
       const double tol = (f_dtype == TUCKER_F64) ? 1e-18 : 1e-12;
       if (f_dtype == TUCKER_F64)
-        eig_seed_kernel<double><<<nb, 256, 0, s>>>(EB);
+        eig_seed_kernel<double><<<gb, 256, 0, s>>>(EB);
       else
-        eig_seed_kernel<float><<<nb, 256, 0, s>>>(EB);
+        eig_seed_kernel<float><<<gb, 256, 0, s>>>(EB);
       TK_LAUNCH_CHECK("eig_seed");
-      eig_wmul_kernel<float><<<gmul, 256, 0, s>>>(EB, 1, 0);
+      launch_wmul<float>(EB, nb, maxL, 1, 0, s);
       TK_LAUNCH_CHECK("eig_wmul");
-      eig_orth_kernel<<<nb, 256, 0, s>>>(EB, 1, 0, tol);
+      eig_orth_kernel<<<gb, 256, smo, s>>>(EB, 1, 0, tol);
       TK_LAUNCH_CHECK("eig_orth");
-      eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0, 0);
+      launch_wmul<double>(EB, nb, maxL, 0, 0, s);
       TK_LAUNCH_CHECK("eig_wmul");
-      eig_orth_kernel<<<nb, 256, 0, s>>>(EB, 2, 0, tol);
+      eig_orth_kernel<<<gb, 256, smo, s>>>(EB, 2, 0, tol);
       TK_LAUNCH_CHECK("eig_orth");
-      eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0, 0);
+      launch_wmul<double>(EB, nb, maxL, 0, 0, s);
       TK_LAUNCH_CHECK("eig_wmul");
       int rc = finalize(0);
       if (rc) return rc;
       gate = 1;
     }
-    eig_stage1_kernel<<<nb, kEigThreads, sm1, s>>>(EB, gate);
+    eig_stage1_kernel<<<gb, kEigThreads, sm1, s>>>(EB, gate);
     TK_LAUNCH_CHECK("eig_stage1");
     // one subspace-iteration step: Y = W V0, Q = orth(Y / theta)
-    eig_wmul_kernel<float><<<gmul, 256, 0, s>>>(EB, 1, gate);
+    launch_wmul<float>(EB, nb, maxL, 1, gate, s);
     TK_LAUNCH_CHECK("eig_wmul");
-    eig_orth_kernel<<<nb, 256, 0, s>>>(EB, 0, gate, 0.0);
+    eig_orth_kernel<<<gb, 256, smo, s>>>(EB, 0, gate, 0.0);
     TK_LAUNCH_CHECK("eig_orth");
     if (f_dtype == TUCKER_F64) {
       // a second step for FP64 factors
-      eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0, gate);
+      launch_wmul<double>(EB, nb, maxL, 0, gate, s);
       TK_LAUNCH_CHECK("eig_wmul");
-      eig_orth_kernel<<<nb, 256, 0, s>>>(EB, 0, gate, 0.0);
+      eig_orth_kernel<<<gb, 256, smo, s>>>(EB, 0, gate, 0.0);
       TK_LAUNCH_CHECK("eig_orth");
     }
     // Rayleigh-Ritz on span(Q): Y = W Q, then the K x K problem
-    eig_wmul_kernel<double><<<gmul, 256, 0, s>>>(EB, 0, gate);
+    launch_wmul<double>(EB, nb, maxL, 0, gate, s);
     TK_LAUNCH_CHECK("eig_wmul");
     int rc = finalize(gate);
     if (rc) return rc;
