@@ -50,11 +50,137 @@ struct BGram {
   int32_t L, ti, tj, z_src;
 };
 
+// Tiles of a node: nodes whose rows are at least 32 elements long (C >= 32)
+// take 256 consecutive (r, c) positions per tile and read along c; shorter
+// rows take 256 / C whole rows per tile, staged through shared memory.
+constexpr int kStageC = 32;
+inline int64_t node_tiles(int64_t R, int64_t C) {
+  if (C < kStageC) {
+    const int64_t rt = kBThreads / C;
+    return (R + rt - 1) / rt;
+  }
+  return (R * C + kBThreads - 1) / kBThreads;
+}
+
+// Division by a small runtime divisor d (1 <= d < 2^16) for numerators below
+// 2^16: q = floor(x * ceil(2^32 / d) / 2^32) is exact there (the error of the
+// scaled reciprocal stays below 2^-16 <= 1/d).
+struct SmallDiv {
+  unsigned m;
+  int d;
+  __device__ __forceinline__ explicit SmallDiv(int d_) : m(0), d(d_) {
+    if (d_ > 1) m = (unsigned)((0x100000000ull + (unsigned)d_ - 1) / (unsigned)d_);
+  }
+  __device__ __forceinline__ int div(int x) const { return d == 1 ? x : (int)__umulhi((unsigned)x, m); }
+};
+
+// Out[r, k, c] = sum_l F[l, k] In[r, l, c] for one tile of one node, F in
+// chunks of 32 l through shared memory.  Each thread accumulates the K
+// outputs of one position (KB >= K registers).  Staged tiles (C < 32) copy
+// the rows of the chunk into shared memory transposed, Ts[l][position], with
+// coalesced loads, and write their outputs back the same way.
 template <int KB>
+__device__ __forceinline__ void bttm_tile(const BNode& nd, int64_t t, const float* __restrict__ T,
+                                          const float* __restrict__ F, float* __restrict__ inter,
+                                          float* __restrict__ G, float* Fs /* [32][KB] */,
+                                          float (*Ts)[kBThreads + 1]) {
+  const int tid = threadIdx.x;
+  const bool staged = nd.C < kStageC;
+  const float* src = (nd.in_src ? inter : T) + nd.in_off;
+  float* dst = (nd.out_dst ? G : inter) + nd.out_off;
+  const float* f = F + nd.f_off;
+  // staged: rows r0 .. r0 + nrows - 1, position tid = (r - r0) * C + c
+  // direct: position p = t * 256 + tid
+  int64_t r0 = 0, r = 0, c = 0;
+  int nrows = 0, C = (int)(staged ? nd.C : 0);
+  bool active;
+  if (staged) {
+    const int rt = kBThreads / C;
+    r0 = t * rt;
+    nrows = (int)min((int64_t)rt, nd.R - r0);
+    active = tid < nrows * C;
+  } else {
+    const int64_t p = t * kBThreads + tid;
+    active = p < nd.R * nd.C;
+    if (active) {
+      r = p / nd.C;
+      c = p - r * nd.C;
+    }
+  }
+  float acc[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) acc[k] = 0.f;
+  for (int l0 = 0; l0 < nd.L; l0 += 32) {
+    const int lc = min(32, nd.L - l0);
+    __syncthreads();
+    for (int i = tid; i < 32 * KB; i += kBThreads) {
+      const int l = i / KB, k = i - (i / KB) * KB;
+      Fs[i] = (l < lc && k < nd.K) ? f[(int64_t)(l0 + l) * nd.K + k] : 0.f;
+    }
+    if (staged) {
+      // row rr of the chunk: lc * C contiguous elements
+      const int seg = lc * C;
+      const SmallDiv dseg(seg), dc(C);
+      for (int i = tid; i < nrows * seg; i += kBThreads) {
+        const int rr = dseg.div(i), o = i - rr * seg;
+        const int l = dc.div(o), cc = o - l * C;
+        Ts[l][rr * C + cc] = src[((r0 + rr) * nd.L + l0) * C + o];
+      }
+      __syncthreads();
+      if (active) {
+        for (int l = 0; l < lc; ++l) {
+          const float x = Ts[l][tid];
+#pragma unroll
+          for (int k = 0; k < KB; ++k) acc[k] = fmaf(Fs[l * KB + k], x, acc[k]);
+        }
+      }
+    } else {
+      __syncthreads();
+      if (active) {
+        const float* in = src + (r * nd.L + l0) * nd.C + c;
+#pragma unroll 4
+        for (int l = 0; l < lc; ++l) {
+          const float x = __ldg(in + (int64_t)l * nd.C);
+#pragma unroll
+          for (int k = 0; k < KB; ++k) acc[k] = fmaf(Fs[l * KB + k], x, acc[k]);
+        }
+      }
+    }
+  }
+  if (staged) {
+    // outputs through shared memory: row rr owns K * C contiguous elements
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < KB; ++k)
+        if (k < nd.K) Ts[k][tid] = acc[k];
+    }
+    __syncthreads();
+    const int seg = nd.K * C;
+    const SmallDiv dseg(seg), dc(C);
+    for (int i = tid; i < nrows * seg; i += kBThreads) {
+      const int rr = dseg.div(i), o = i - rr * seg;
+      const int k = dc.div(o), cc = o - k * C;
+      dst[(r0 + rr) * seg + o] = Ts[k][rr * C + cc];
+    }
+    return;
+  }
+  if (!active) return;
+  float* out = dst + (r * nd.K) * nd.C + c;
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+    if (k < nd.K) out[(int64_t)k * nd.C] = acc[k];
+}
+
+// One block per tile; the block runs the variant whose KB is the smallest of
+// 4, 8, 12, 16, 24, 32 that holds its node's K (KMAX bounds the variants so
+// that the kernel's register count follows the batch's largest rank).
+template <int KMAX>
 __global__ void __launch_bounds__(kBThreads)
     bttm_kernel(const BNode* __restrict__ nodes, int nnodes, const float* __restrict__ T,
                 const float* __restrict__ F, float* __restrict__ inter, float* __restrict__ G) {
-  __shared__ float Fs[64][KB];
+  __shared__ __align__(16) float Fs[32 * KMAX];
+  __shared__ float Ts[32][kBThreads + 1];
   __shared__ int node_idx;
   const int64_t tile = blockIdx.x;
   if (threadIdx.x == 0) {
@@ -68,40 +194,13 @@ __global__ void __launch_bounds__(kBThreads)
   }
   __syncthreads();
   const BNode nd = nodes[node_idx];
-  const int64_t p = (tile - nd.tile0) * kBThreads + threadIdx.x;
-  const bool active = p < nd.R * nd.C;
-  int64_t r = 0, c = 0;
-  if (active) {
-    r = p / nd.C;
-    c = p - r * nd.C;
-  }
-  const float* in = (nd.in_src ? inter : T) + nd.in_off + (r * nd.L) * nd.C + c;
-  const float* f = F + nd.f_off;
-  float acc[KB];
-#pragma unroll
-  for (int k = 0; k < KB; ++k) acc[k] = 0.f;
-  for (int l0 = 0; l0 < nd.L; l0 += 64) {
-    const int lc = min(64, nd.L - l0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64 * KB; i += kBThreads) {
-      const int l = i / KB, k = i - (i / KB) * KB;
-      Fs[l][k] = (l < lc && k < nd.K) ? f[(int64_t)(l0 + l) * nd.K + k] : 0.f;
-    }
-    __syncthreads();
-    if (active) {
-#pragma unroll 4
-      for (int l = 0; l < lc; ++l) {
-        const float x = __ldg(in + (int64_t)(l0 + l) * nd.C);
-#pragma unroll
-        for (int k = 0; k < KB; ++k) acc[k] = fmaf(Fs[l][k], x, acc[k]);
-      }
-    }
-  }
-  if (!active) return;
-  float* out = (nd.out_dst ? G : inter) + nd.out_off + (r * nd.K) * nd.C + c;
-#pragma unroll
-  for (int k = 0; k < KB; ++k)
-    if (k < nd.K) out[(int64_t)k * nd.C] = acc[k];
+  const int64_t t = tile - nd.tile0;
+  if (nd.K <= 4) bttm_tile<4>(nd, t, T, F, inter, G, Fs, Ts);
+  else if (nd.K <= 8 || KMAX <= 8) bttm_tile<(KMAX < 8 ? KMAX : 8)>(nd, t, T, F, inter, G, Fs, Ts);
+  else if (nd.K <= 12 || KMAX <= 12) bttm_tile<(KMAX < 12 ? KMAX : 12)>(nd, t, T, F, inter, G, Fs, Ts);
+  else if (nd.K <= 16 || KMAX <= 16) bttm_tile<(KMAX < 16 ? KMAX : 16)>(nd, t, T, F, inter, G, Fs, Ts);
+  else if (nd.K <= 24 || KMAX <= 24) bttm_tile<(KMAX < 24 ? KMAX : 24)>(nd, t, T, F, inter, G, Fs, Ts);
+  else bttm_tile<KMAX>(nd, t, T, F, inter, G, Fs, Ts);
 }
 
 // 32 x 32 Gram tile over all M = R*C columns: FP32 products summed in runs of
@@ -308,6 +407,7 @@ struct tucker_batch_s {
   size_t off_gram = 0, bytes_gram = 0;        // doubles
   size_t off_eig = 0, bytes_eig = 0;
   size_t off_res = 0;                         // count doubles: residuals
+  size_t off_cold = 0;                        // 1 + count * N ints: full-path list
   size_t off_tables = 0, bytes_tables = 0;
   size_t ws_total = 0;
   // device table addresses (valid after prepare)
@@ -331,12 +431,20 @@ struct tucker_batch_s {
 
 namespace {
 
-template <typename Item>
-void add_tiles(std::vector<Item>& v, int64_t* total) {
+void add_tiles(std::vector<BNode>& v, int64_t* total) {
   int64_t t = 0;
-  for (Item& nd : v) {
+  for (BNode& nd : v) {
     nd.tile0 = t;
-    t += (nd.R * nd.C + kBThreads - 1) / kBThreads;
+    t += node_tiles(nd.R, nd.C);
+  }
+  *total = t;
+}
+
+void add_tiles(std::vector<BExp>& v, int64_t* total) {
+  int64_t t = 0;
+  for (BExp& e : v) {
+    e.tile0 = t;
+    t += (e.R * e.C + kBThreads - 1) / kBThreads;
   }
   *total = t;
 }
@@ -535,13 +643,15 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
         prev_src = 1;
       }
     }
-    // reconstruction for the fit: expand the modes from the core, the mode of
-    // smallest rank last (its step, fused with the comparison against T, is
-    // the only one over |T| positions); the others by increasing L_n / K_n
+    // reconstruction for the fit: expand the modes from the core; the last
+    // step, fused with the comparison against T, is the only one over |T|
+    // positions, so it takes the mode of smallest rank among modes 0..N-2
+    // (a mode before the last keeps its reads of T along contiguous rows);
+    // the others go by increasing L_n / K_n
     {
       int last = 0;
-      for (int n = 1; n < N; ++n)
-        if (K[n] < K[last] || (K[n] == K[last] && last == N - 1)) last = n;
+      for (int n = 1; n < N - 1; ++n)
+        if (K[n] < K[last]) last = n;
       std::vector<int> order;
       for (int n = 0; n < N; ++n)
         if (n != last) order.push_back(n);
@@ -595,6 +705,8 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
   off += b->bytes_eig;
   b->off_res = off;
   off += align_up((size_t)count * sizeof(double));
+  b->off_cold = off;
+  off += align_up((size_t)(1 + (size_t)count * N) * sizeof(int));
   b->off_tables = off;
   size_t tb = 0;
   for (auto& v : b->fit_steps) tb += align_up(v.size() * sizeof(BExp));
@@ -723,7 +835,8 @@ int tucker_batch_sweep(tucker_batch_t b, const float* T, const float* F_in, floa
     if (rc) return rc;
   }
   return launch_eig_batched(b->d_eig, b->count * b->N, b->maxL, b->maxK, TUCKER_F32,
-                            reinterpret_cast<char*>(F_out), reinterpret_cast<const char*>(F_in), s);
+                            reinterpret_cast<char*>(F_out), reinterpret_cast<const char*>(F_in),
+                            reinterpret_cast<int*>(base + b->off_cold), s);
 }
 
 int tucker_batch_sthosvd(tucker_batch_t b, const float* T, float* F, float* G, void* ws,
@@ -740,7 +853,8 @@ int tucker_batch_sthosvd(tucker_batch_t b, const float* T, float* F, float* G, v
                                                                              inter, gram);
     TK_LAUNCH_CHECK("batch_gram");
     rc = launch_eig_batched(b->d_eig + (size_t)n * b->count, b->count, b->maxL, b->maxK, TUCKER_F32,
-                            reinterpret_cast<char*>(F), nullptr, s);
+                            reinterpret_cast<char*>(F), nullptr,
+                            reinterpret_cast<int*>(base + b->off_cold), s);
     if (rc) return rc;
     rc = launch_bttm(*b, b->d_sth_ttm[(size_t)n], (int64_t)b->sth_ttm[(size_t)n].size(),
                      b->sth_tiles[(size_t)n], T, F, inter, G, s);

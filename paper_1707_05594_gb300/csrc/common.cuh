@@ -193,9 +193,10 @@ void eig_desc_layout(EigDesc& d, char* p, int L, int K);
 // The eigensolver over `count` matrices whose descriptors are in device
 // memory (dev; their F / F0 fields are byte offsets from f_base / f0_base),
 // with maxL / maxK bounding every L / K.  A non-NULL f0_base selects the warm
-// start from the input factors, with the gated full-path fallback.
+// start from the input factors, with the full path for the matrices whose
+// warm check fails; `cold` (1 + count ints of device memory) lists them.
 int launch_eig_batched(const EigDesc* dev, int count, int maxL, int maxK, int f_dtype,
-                       char* f_base, const char* f0_base, cudaStream_t s);
+                       char* f_base, const char* f0_base, int* cold, cudaStream_t s);
 
 struct EigProblem {
   const double* W;         // L x L

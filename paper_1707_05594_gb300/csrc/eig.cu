@@ -48,9 +48,23 @@ struct EigBatch {
   const EigDesc* dev;
   char* f_base;
   const char* f0_base;
+  int* cold;  // list of matrices sent to the full path: cold[0] = count, cold[1 ..]
 };
 __device__ __forceinline__ EigDesc get_desc(const EigBatch& B, unsigned i) {
-  if (!B.dev) return B.d[i];
+  if (!B.dev) {
+    // constant offsets into the parameter block (a run-time index would make
+    // every thread copy the whole block to local memory first)
+    switch (i) {
+      case 0: return B.d[0];
+      case 1: return B.d[1];
+      case 2: return B.d[2];
+      case 3: return B.d[3];
+      case 4: return B.d[4];
+      case 5: return B.d[5];
+      case 6: return B.d[6];
+      default: return B.d[7];
+    }
+  }
   EigDesc d = B.dev[i];
   d.F = B.f_base + reinterpret_cast<size_t>(d.F);
   d.F0 = B.f0_base ? static_cast<const void*>(B.f0_base + reinterpret_cast<size_t>(d.F0)) : nullptr;
@@ -103,13 +117,18 @@ __device__ __forceinline__ float start_value(int i, int t) {
 
 // Warm start bookkeeping: stat[0] / stat[1] hold the subspace movement of the
 // two warm subspace-iteration steps, the int at stat + 4 words says whether the
-// full (cold) path must run.  Kernels of the cold path launched with gate = 1
-// return at once when the warm result was accepted.
+// full (cold) path must run, and such matrices are also appended to the list
+// B.cold.  Kernels of the full path launched with gate = 1 visit only the
+// listed matrices (an empty list costs each block one load); with gate = 0
+// they visit all of them.  Blocks take their matrices in a grid-stride loop.
 __device__ __forceinline__ int& need_cold(const EigDesc& P) {
   return reinterpret_cast<int*>(P.stat)[4];
 }
-__device__ __forceinline__ bool gated_off(const EigDesc& P, int gate) {
-  return gate && need_cold(P) == 0;
+__device__ __forceinline__ int visit_count(const EigBatch& B, int gate) {
+  return gate ? *reinterpret_cast<volatile const int*>(B.cold) : B.batch;
+}
+__device__ __forceinline__ unsigned visit_index(const EigBatch& B, int gate, int i) {
+  return gate ? (unsigned)B.cold[1 + i] : (unsigned)i;
 }
 
 // Starting subspace from the input factor: V0[c][r] = F0[r][c].
@@ -465,13 +484,12 @@ __device__ __forceinline__ void eig_stage1_body(const EigDesc& P) {
   for (int t = tid; t < K; t += kEigThreads) P.theta[t] = lam[t];
 }
 
-// Matrices are taken in a grid-stride loop, so a gated launch costs one flag
-// read per matrix; the barrier keeps the previous matrix's shared data live
-// until every thread is done with it.
+// The barrier at the top of each iteration keeps the previous matrix's shared
+// data live until every thread is done with it.
 __global__ void __launch_bounds__(kEigThreads) eig_stage1_kernel(const EigBatch B, int gate) {
-  for (unsigned m = blockIdx.x; m < (unsigned)B.batch; m += gridDim.x) {
-    const EigDesc P = get_desc(B, m);
-    if (gated_off(P, gate)) continue;
+  const int cnt = visit_count(B, gate);
+  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const EigDesc P = get_desc(B, visit_index(B, gate, i));
     __syncthreads();
     eig_stage1_body(P);
   }
@@ -494,9 +512,9 @@ __global__ void __launch_bounds__(256) eig_wmul_kernel(const EigBatch B, int use
   __shared__ double Vs[kMulJ][kMaxEigK + 1];
   const int tid = threadIdx.x, rl = tid % ROWS, cg = tid / ROWS;
   const int r0 = blockIdx.x * ROWS;
-  for (unsigned m = blockIdx.y; m < (unsigned)B.batch; m += gridDim.y) {
-    const EigDesc P = get_desc(B, m);
-    if (gated_off(P, gate)) continue;
+  const int cnt = visit_count(B, gate);
+  for (int i = blockIdx.y; i < cnt; i += gridDim.y) {
+    const EigDesc P = get_desc(B, visit_index(B, gate, i));
     const int n = P.L, K = P.K;
     if (r0 >= n) continue;
     const TIn* in = use_v0 ? reinterpret_cast<const TIn*>(P.V0) : reinterpret_cast<const TIn*>(P.Q);
@@ -567,44 +585,51 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
   return t;
 }
 
-// sum over a, b < K of (A_a . Q_b)^2 for [K][n] bases A (float or double) and Q
-template <typename TA>
-__device__ __forceinline__ double proj_norm2(const TA* A, const double* Q, int n, int K, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double acc = 0.0;
-  for (int idx = warp; idx < K * K; idx += 8) {
-    const int a = idx / K, b = idx - (idx / K) * K;
-    double s = 0.0;
-    for (int r = lane; r < n; r += 32) s += (double)A[(int64_t)a * n + r] * Q[(int64_t)b * n + r];
-    s = warp_sum(s);
-    acc += s * s;  // identical in every lane
-  }
-  if (lane != 0) acc = 0.0;
-  return block_sum256(acc, red);
-}
+
+// The dot products below give each thread whole (a, b) entries: on GB300 the
+// FP64 pipe is narrow, and a warp-wide reduction spends five FP64 additions
+// per entry, more than the products themselves for columns of a few dozen.
+// Columns in shared memory have an odd stride ld so that the threads of a
+// warp, which read column b = b0 .. b0 + 15 at one row, hit distinct banks.
 
 // One Cholesky-QR pass on the K columns of length n held in shared memory
-// (Qs[c * n + r]): S = Qs^T Qs, S = R^T R, Qs <- Qs R^-1.  Returns false (and
+// (Qs[c * ld + r]): S = Qs^T Qs, S = R^T R, Qs <- Qs R^-1.  Returns 0 (and
 // leaves Qs unchanged) when a pivot is not clearly positive, i.e. when the
-// columns are too far from independent for this pass to be accurate.
-__device__ __forceinline__ bool chol_qr_pass(double* Qs, double* S, int n, int K) {
+// columns are too far from independent for this pass to be accurate; 2 when
+// the columns were already close to orthonormal (K max|S - I| <= 0.1, so the
+// condition number is below 1.3 and this one pass leaves them orthonormal to
+// rounding), else 1.
+__device__ __forceinline__ int chol_qr_pass(double* Qs, int ld, double* S, int n, int K) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ int bad;
-  // S (upper triangle), a warp per entry
-  for (int idx = warp; idx < K * K; idx += 8) {
+  __shared__ int bad, near;
+  __shared__ double rdiag[kMaxEigK];  // 1 / R[j][j]
+  // S (upper triangle), a thread per entry
+  for (int idx = tid; idx < K * K; idx += 256) {
     const int a = idx / K, b = idx - (idx / K) * K;
     if (a > b) continue;
-    double acc = 0.0;
-    for (int r = lane; r < n; r += 32) acc = fma(Qs[a * n + r], Qs[b * n + r], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) S[a * K + b] = acc;
+    const double* qa = Qs + a * ld;
+    const double* qb = Qs + b * ld;
+    double s0 = 0.0, s1 = 0.0;
+    int r = 0;
+    for (; r + 1 < n; r += 2) {
+      s0 = fma(qa[r], qb[r], s0);
+      s1 = fma(qa[r + 1], qb[r + 1], s1);
+    }
+    if (r < n) s0 = fma(qa[r], qb[r], s0);
+    S[a * K + b] = s0 + s1;
   }
   __syncthreads();
   // Cholesky S = R^T R in place (upper triangle), by warp 0: row j of R is
   // finished before row j + 1 starts; lanes take the entries of a row
   if (warp == 0) {
-    double smax = 0.0;
+    double smax = 0.0, dev = 0.0;
     for (int j = 0; j < K; ++j) smax = fmax(smax, S[j * K + j]);
+    for (int idx = lane; idx < K * K; idx += 32) {
+      const int a = idx / K, b = idx - (idx / K) * K;
+      if (a <= b) dev = fmax(dev, fabs(S[idx] - (a == b ? 1.0 : 0.0)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
     int fail = 0;
     for (int j = 0; j < K && !fail; ++j) {
       double d = 0.0;
@@ -616,42 +641,47 @@ __device__ __forceinline__ bool chol_qr_pass(double* Qs, double* S, int n, int K
         fail = 1;
         break;
       }
-      const double rjj = sqrt(d);
+      const double rjj = sqrt(d), rinv = 1.0 / rjj;
       __syncwarp();
       for (int b = j + 1 + lane; b < K; b += 32) {
         double v = S[j * K + b];
         for (int a = 0; a < j; ++a) v -= S[a * K + j] * S[a * K + b];
-        S[j * K + b] = v / rjj;
+        S[j * K + b] = v * rinv;
       }
+      if (lane == 0) rdiag[j] = rinv;
       __syncwarp();
       if (lane == 0) S[j * K + j] = rjj;
       __syncwarp();
     }
-    if (lane == 0) bad = fail;
-  }
-  __syncthreads();
-  if (bad) return false;
-  // Qs <- Qs R^-1, row by row (forward substitution along c)
-  for (int r = tid; r < n; r += 256) {
-    for (int c = 0; c < K; ++c) {
-      double v = Qs[c * n + r];
-      for (int a = 0; a < c; ++a) v -= S[a * K + c] * Qs[a * n + r];
-      Qs[c * n + r] = v / S[c * K + c];
+    if (lane == 0) {
+      bad = fail;
+      near = dev * K <= 0.1;
     }
   }
   __syncthreads();
-  return true;
+  if (bad) return 0;
+  const int result = near ? 2 : 1;
+  // Qs <- Qs R^-1, row by row (forward substitution along c)
+  for (int r = tid; r < n; r += 256) {
+    for (int c = 0; c < K; ++c) {
+      double v = Qs[c * ld + r];
+      for (int a = 0; a < c; ++a) v -= S[a * K + c] * Qs[a * ld + r];
+      Qs[c * ld + r] = v * rdiag[c];
+    }
+  }
+  __syncthreads();
+  return result;
 }
 
 // Classical Gram-Schmidt applied twice, column by column (the fallback of
 // chol_qr_pass for nearly dependent columns).
-__device__ __forceinline__ void cgs2(double* Q, int n, int K, double* dots, double* red) {
+__device__ __forceinline__ void cgs2(double* Q, int ld, int n, int K, double* dots, double* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int j = 0; j < K; ++j) {
-    double* qj = Q + (int64_t)j * n;
+    double* qj = Q + (int64_t)j * ld;
     for (int pass = 0; pass < 2; ++pass) {
       for (int i = warp; i < j; i += 8) {
-        const double* qi = Q + (int64_t)i * n;
+        const double* qi = Q + (int64_t)i * ld;
         double s = 0.0;
         for (int r = lane; r < n; r += 32) s += qi[r] * qj[r];
         s = warp_sum(s);
@@ -660,7 +690,7 @@ __device__ __forceinline__ void cgs2(double* Q, int n, int K, double* dots, doub
       __syncthreads();
       for (int r = tid; r < n; r += 256) {
         double v = qj[r];
-        for (int i = 0; i < j; ++i) v -= dots[i] * Q[(int64_t)i * n + r];
+        for (int i = 0; i < j; ++i) v -= dots[i] * Q[(int64_t)i * ld + r];
         qj[r] = v;
       }
       __syncthreads();
@@ -674,28 +704,59 @@ __device__ __forceinline__ void cgs2(double* Q, int n, int K, double* dots, doub
   }
 }
 
+// K - ||A^T Q||_F^2 for the K x n basis A ([K][n] in global memory) and the
+// columns Q in shared memory (stride ld), a thread per entry of A^T Q.
+__device__ __forceinline__ double subspace_gap(const double* A, const double* Qs, int ld, int n,
+                                               int K, double* red) {
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < K * K; idx += 256) {
+    const int a = idx / K, b = idx - (idx / K) * K;
+    const double* pa = A + (int64_t)a * n;
+    const double* qb = Qs + b * ld;
+    double s0 = 0.0, s1 = 0.0;
+    int r = 0;
+    for (; r + 1 < n; r += 2) {
+      s0 = fma(pa[r], qb[r], s0);
+      s1 = fma(pa[r + 1], qb[r + 1], s1);
+    }
+    if (r < n) s0 = fma(pa[r], qb[r], s0);
+    const double v = s0 + s1;
+    acc = fma(v, v, acc);
+  }
+  return fmax(0.0, (double)K - block_sum256(acc, red));
+}
+
 // ---------------------------------------------------------------------------
 // Q = orth(Y diag(1/theta)) in FP64, in shared memory: two Cholesky-QR passes
-// (CholeskyQR2), or Gram-Schmidt applied twice where the first Cholesky pass
-// finds the scaled columns nearly dependent.  Writes Q.
+// (CholeskyQR2; one where the scaled columns are already close to
+// orthonormal), or Gram-Schmidt applied twice where the first Cholesky pass
+// finds them nearly dependent.  Writes Q.
 //   mode 0 (full path): theta from stage 1, a negligible theta falls back to V0;
 //   mode 1 (warm step 1): theta_j = V0_j . Y_j (Rayleigh quotient of the
 //     starting vector); records delta1 = K - ||V0^T Q||_F^2 and keeps Q in Qp;
 //   mode 2 (warm step 2): theta_j = Qp_j . Y_j; records delta2 = K -
 //     ||Qp^T Q||_F^2 and accepts the warm result when delta2 <= tol and the
 //     iteration contracts (delta2 <= delta1 / 4, or delta1 <= tol too);
-//     otherwise it raises the need-cold flag for the full path.
-// Dynamic shared memory: (K * L + K * K) doubles.
+//     otherwise it raises the need-cold flag and lists the matrix for the
+//     full path.
+// Dynamic shared memory: (K * (L + 1) + K * K) doubles.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void eig_orth_body(const EigDesc& P, int mode, double tol) {
-  const int n = P.L, K = P.K;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ void eig_orth_body(const EigDesc& P, int mode, double tol, unsigned m,
+                                              int* cold) {
+  const int n = P.L, K = P.K, ld = n | 1;
+  const int tid = threadIdx.x;
   __shared__ double dots[kMaxEigK];
   __shared__ double th[kMaxEigK];
+  __shared__ double thinv[kMaxEigK];
   __shared__ double red[8];
   extern __shared__ __align__(16) double osm[];
-  double* Qs = osm;             // [K][n]
-  double* S = osm + K * n;      // [K][K]
+  double* Qs = osm;             // [K][ld]
+  double* S = osm + K * ld;     // [K][K]
+  // warm step 1: the starting basis V0 converted to FP64 once, into Qp (Qp
+  // receives Q at the end of this step)
+  if (mode == 1)
+    for (int i = tid; i < K * n; i += 256) P.Qp[i] = (double)P.V0[i];
+  __syncthreads();
   if (mode == 0) {
     float tmax = 0.f;
     for (int t = 0; t < K; ++t) tmax = fmaxf(tmax, fabsf(P.theta[t]));
@@ -704,58 +765,70 @@ __device__ __forceinline__ void eig_orth_body(const EigDesc& P, int mode, double
       th[t] = (fabsf(v) > 1e-20f * tmax && v != 0.f) ? (double)v : 0.0;
     }
   } else {
-    for (int t = warp; t < K; t += 8) {
+    for (int t = tid; t < K; t += 256) {
+      const double* a = P.Qp + (int64_t)t * n;
+      const double* y = P.Y + (int64_t)t * n;
       double s = 0.0;
-      for (int r = lane; r < n; r += 32) {
-        const double v = (mode == 1) ? (double)P.V0[(int64_t)t * n + r] : P.Qp[(int64_t)t * n + r];
-        s += v * P.Y[(int64_t)t * n + r];
-      }
-      s = warp_sum(s);
-      if (lane == 0) th[t] = s;
+      for (int r = 0; r < n; ++r) s = fma(a[r], y[r], s);
+      th[t] = s;
     }
   }
   __syncthreads();
-  double tmx = 0.0;
-  for (int t = 0; t < K; ++t) tmx = fmax(tmx, fabs(th[t]));
+  // 1 / theta once per column (element-wise FP64 divisions are costly on the
+  // FP64 pipe); a negligible theta keeps the starting vector instead
+  if (tid < K) {
+    double tmx = 0.0;
+    for (int t = 0; t < K; ++t) tmx = fmax(tmx, fabs(th[t]));
+    const double v = th[tid];
+    thinv[tid] = (fabs(v) > 1e-30 * tmx && v != 0.0) ? 1.0 / v : 0.0;
+  }
+  __syncthreads();
   for (int i = tid; i < K * n; i += 256) {
-    const int t = i / n;
-    const double v = th[t];
-    if (fabs(v) > 1e-30 * tmx && v != 0.0) {
-      Qs[i] = P.Y[i] / v;
-    } else {
-      Qs[i] = (mode == 2) ? P.Qp[i] : (double)P.V0[i];
-    }
+    const int t = i / n, r = i - (i / n) * n;
+    const double w = thinv[t];
+    Qs[t * ld + r] = (w != 0.0) ? P.Y[i] * w : ((mode == 0) ? (double)P.V0[i] : P.Qp[i]);
   }
   __syncthreads();
-  if (chol_qr_pass(Qs, S, n, K)) {
-    if (!chol_qr_pass(Qs, S, n, K)) cgs2(Qs, n, K, dots, red);
-  } else {
-    cgs2(Qs, n, K, dots, red);
+  // CholeskyQR2: the second pass only where the first started from columns
+  // not already close to orthonormal
+  const int first = chol_qr_pass(Qs, ld, S, n, K);
+  if (first == 0) {
+    cgs2(Qs, ld, n, K, dots, red);
+  } else if (first == 1) {
+    if (chol_qr_pass(Qs, ld, S, n, K) == 0) cgs2(Qs, ld, n, K, dots, red);
   }
-  double* Q = P.Q;
-  for (int i = tid; i < K * n; i += 256) Q[i] = Qs[i];
+  for (int i = tid; i < K * n; i += 256) {
+    const int t = i / n, r = i - (i / n) * n;
+    P.Q[i] = Qs[t * ld + r];
+  }
   if (mode == 1) {
-    const double pn = proj_norm2<float>(P.V0, Qs, n, K, red);
-    for (int i = tid; i < K * n; i += 256) P.Qp[i] = Qs[i];
-    if (tid == 0) P.stat[0] = fmax(0.0, (double)K - pn);
+    const double gap = subspace_gap(P.Qp, Qs, ld, n, K, red);
+    __syncthreads();
+    for (int i = tid; i < K * n; i += 256) {
+      const int t = i / n, r = i - (i / n) * n;
+      P.Qp[i] = Qs[t * ld + r];
+    }
+    if (tid == 0) P.stat[0] = gap;
   } else if (mode == 2) {
-    const double pn = proj_norm2<double>(P.Qp, Qs, n, K, red);
+    const double d2 = subspace_gap(P.Qp, Qs, ld, n, K, red);
     if (tid == 0) {
-      const double d1 = P.stat[0], d2 = fmax(0.0, (double)K - pn);
+      const double d1 = P.stat[0];
       P.stat[1] = d2;
       const bool ok = (d2 == d2) && d2 <= tol && (d1 <= tol || d2 <= 0.25 * d1);
       need_cold(P) = ok ? 0 : 1;
+      if (!ok) cold[1 + atomicAdd(cold, 1)] = (int)m;
     }
   }
 }
 
 __global__ void __launch_bounds__(256) eig_orth_kernel(const EigBatch B, int mode, int gate,
                                                        double tol) {
-  for (unsigned m = blockIdx.x; m < (unsigned)B.batch; m += gridDim.x) {
+  const int cnt = visit_count(B, gate);
+  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const unsigned m = visit_index(B, gate, i);
     const EigDesc P = get_desc(B, m);
-    if (gated_off(P, gate)) continue;
     __syncthreads();
-    eig_orth_body(P, mode, tol);
+    eig_orth_body(P, mode, tol, m, B.cold);
   }
 }
 
@@ -780,19 +853,20 @@ __device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
   __shared__ int order[kMaxEigK];
   __shared__ int flip[kMaxEigK];
   __shared__ double dots[kMaxEigK];
-  for (int idx = warp; idx < K * K; idx += 8) {
+  // H = sym(Q^T Y), a thread per entry (no warp reductions on the FP64 pipe)
+  for (int idx = tid; idx < K * K; idx += 256) {
     const int a = idx / K, b = idx - (idx / K) * K;
     if (a > b) continue;
     const double* qa = P.Q + (int64_t)a * n;
     const double* yb = P.Y + (int64_t)b * n;
     const double* qb = P.Q + (int64_t)b * n;
     const double* ya = P.Y + (int64_t)a * n;
-    double s = 0.0;
-    for (int r = lane; r < n; r += 32) s += qa[r] * yb[r] + qb[r] * ya[r];
-    s = warp_sum(s);
-    if (lane == 0) {
-      Hf[a * K + b] = Hf[b * K + a] = (float)(0.5 * s);
+    double s0 = 0.0, s1 = 0.0;
+    for (int r = 0; r < n; ++r) {
+      s0 = fma(qa[r], yb[r], s0);
+      s1 = fma(qb[r], ya[r], s1);
     }
+    Hf[a * K + b] = Hf[b * K + a] = (float)(0.5 * (s0 + s1));
   }
   for (int idx = tid; idx < K * K; idx += 256) Uf[idx] = (idx / K == idx % K) ? 1.f : 0.f;
   __syncthreads();
@@ -920,9 +994,9 @@ __device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
 
 template <typename TOut>
 __global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B, int gate) {
-  for (unsigned m = blockIdx.x; m < (unsigned)B.batch; m += gridDim.x) {
-    const EigDesc P = get_desc(B, m);
-    if (gated_off(P, gate)) continue;
+  const int cnt = visit_count(B, gate);
+  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const EigDesc P = get_desc(B, visit_index(B, gate, i));
     __syncthreads();
     eig_finalize_body<TOut>(P);
   }
@@ -984,7 +1058,8 @@ int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, s
     EigBatch EB{};
     EB.batch = nb;
     EB.dev = nullptr;
-    char* p = static_cast<char*>(ws);
+    EB.cold = static_cast<int*>(ws);
+    char* p = static_cast<char*>(ws) + kAlign;
     int maxL = 1, maxK = 1;
     bool warm = (kernel_policy() & 2) == 0;
     for (int b = 0; b < nb; ++b) {
@@ -1006,7 +1081,7 @@ int launch_eig_topk(const EigProblem* probs, int batch, int f_dtype, void* ws, s
 }
 
 int launch_eig_batched(const EigDesc* dev, int count, int maxL, int maxK, int f_dtype,
-                       char* f_base, const char* f0_base, cudaStream_t s) {
+                       char* f_base, const char* f0_base, int* cold, cudaStream_t s) {
   if (count <= 0) return TUCKER_OK;
   if (maxL > kMaxEigL || maxK > kMaxEigK || maxK > maxL)
     return fail(TUCKER_ERR_UNSUPPORTED, "eig: need K <= min(L, 64) and L <= 200");
@@ -1016,6 +1091,7 @@ int launch_eig_batched(const EigDesc* dev, int count, int maxL, int maxK, int f_
   EB.dev = dev;
   EB.f_base = f_base;
   EB.f0_base = f0_base;
+  EB.cold = cold;
   const bool warm = f0_base != nullptr && (kernel_policy() & 2) == 0;
   return run_eig(EB, count, maxL, maxK, f_dtype, warm, s);
 }
@@ -1042,7 +1118,7 @@ int run_eig(const EigBatch& EB, int nb, int maxL, int maxK, int f_dtype, bool wa
     else
       TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_kernel<float>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    const size_t smo = ((size_t)maxK * maxL + (size_t)maxK * maxK) * 8;
+    const size_t smo = ((size_t)maxK * (maxL + 1) + (size_t)maxK * maxK) * 8;
     if (smo > (size_t)smax) return fail(TUCKER_ERR_UNSUPPORTED, "eig: L * K too large");
     TK_CUDA_TRY(cudaFuncSetAttribute(eig_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smo));
@@ -1060,6 +1136,7 @@ int run_eig(const EigBatch& EB, int nb, int maxL, int maxK, int f_dtype, bool wa
       // an a-posteriori check, then Rayleigh-Ritz; the full path below runs
       // only where the check failed (need-cold flag)
       const double tol = (f_dtype == TUCKER_F64) ? 1e-18 : 1e-12;
+      TK_CUDA_TRY(cudaMemsetAsync(EB.cold, 0, sizeof(int), s));
       if (f_dtype == TUCKER_F64)
         eig_seed_kernel<double><<<gb, 256, 0, s>>>(EB);
       else

@@ -24,9 +24,10 @@ namespace {
 constexpr int kNoallocMaxBatch = 8;
 constexpr int kNoallocMaxL = 200;
 constexpr int kNoallocMaxK = 64;
-// eig_ws_bytes() of kNoallocMaxBatch matrices with L = 200, K = 64 (~4 MiB)
+// eig_ws_bytes() of kNoallocMaxBatch matrices with L = 200, K = 64 (~4 MiB):
+// a 256-byte list head, then the per-matrix scratch
 constexpr size_t kPerMatrix = eig_bytes_per_matrix(kNoallocMaxL, kNoallocMaxK);
-constexpr size_t kNoallocScratchBytes = kNoallocMaxBatch * kPerMatrix;
+constexpr size_t kNoallocScratchBytes = kAlign + kNoallocMaxBatch * kPerMatrix;
 
 static __device__ __align__(256) unsigned char g_eig_scratch[kNoallocScratchBytes];
 

@@ -75,7 +75,8 @@ constexpr size_t eig_bytes_per_matrix(size_t l, size_t k) {
          kAlign;
 }
 
-// sizes of the eigensolver scratch for a batch of matrices
+// sizes of the eigensolver scratch for a batch of matrices (256 bytes for the
+// list of matrices sent to the full path, then eig_bytes_per_matrix each)
 size_t eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
 
 // releases the plan's profiling events (defined with the executor)

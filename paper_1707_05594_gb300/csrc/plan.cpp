@@ -254,7 +254,8 @@ void sthosvd_buffers(Plan& p) {
 }  // namespace
 
 size_t eig_ws_bytes(int batch, const int64_t* L, const int64_t* K) {
-  size_t total = 0;
+  size_t total = kAlign;  // list of the matrices sent to the full path
+  if (batch <= 0) return 0;
   for (int b = 0; b < batch; ++b) total += eig_bytes_per_matrix((size_t)L[b], (size_t)K[b]);
   return total;
 }
