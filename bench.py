@@ -413,7 +413,8 @@ def run_ours(args, ws_size, rank):
         "clocks": clocks,
     }
     if not args.no_precision:
-        out["precision_form"] = run_precision_form(args)
+        out["precision_form"] = run_precision_form(args, "precision5")
+        out["precision_form_6way"] = run_precision_form(args, "uneven6")
     if not args.no_batch:
         out["batched_form"] = run_batch_form(args)
     if rank == 0 and ws_size == 1 and not args.no_cpu_baseline:
@@ -429,21 +430,23 @@ def run_ours(args, ws_size, rank):
     return out
 
 
-def run_precision_form(args):
-    """BF16 vs FP32 form at equal fit error on the 64^5 workload (planted core
-    16^5 with geometric 0.8 mode scaling, rho 1e-2): both start from the same
-    STHOSVD; the FP32 form runs S sweeps on the FP32 tensor, the precision form
-    runs S-2 sweeps on the BF16 copy (tensor-core TTMs, BF16 intermediates) and
-    2 FP32 polish sweeps.  Times cover the sweeps (fused-core steps); the fit is
-    taken for the final factors against the FP32 tensor."""
+def run_precision_form(args, name="precision5"):
+    """BF16 vs FP32 form at equal fit error: on the 64^5 workload (planted core
+    16^5 with geometric 0.8 mode scaling, rho 1e-2, 10 sweeps) or the uneven
+    6-way workload (64x56x48x40x32x24, core 16x14x12x10x8x6, Student-t noise,
+    8 sweeps).  Both forms start from the same STHOSVD; the FP32 form runs S
+    sweeps on the FP32 tensor, the precision form runs S-2 sweeps on the BF16
+    copy (tensor-core TTMs, BF16 intermediates) and 2 FP32 polish sweeps.
+    Times cover the sweeps (fused-core steps); the fit is taken for the final
+    factors against the FP32 tensor."""
     import torch
 
     import paper_1707_05594_gb300 as tk
     import workloads
-    spec = workloads.WORKLOADS["precision5"]
+    spec = workloads.WORKLOADS[name]
     L, K = spec["L"], spec["K"]
     S = int(spec["sweeps"])
-    w = workloads.make_workload("precision5", device="cuda")
+    w = workloads.make_workload(name, device="cuda")
     T32 = w["T"]
     del w
     T16 = torch.empty(T32.shape, dtype=torch.bfloat16, device="cuda")
@@ -478,11 +481,15 @@ def run_precision_form(args):
         torch.cuda.synchronize()
         return ms, fo[0].item()
 
-    run([(p32, T32)] * 2)  # warm-up
+    run([(p32, T32)] * 2 + [(p16, T16)] * 2)  # warm-up of both plans
     ms32, fit32 = run([(p32, T32)] * S)
     ms16, fit16 = run([(p16, T16)] * (S - 2) + [(p32, T32)] * 2)
     rel = abs(fit16 - fit32) / fit32
-    return {"workload": "64^5 planted Tucker, ranks 16, geometric 0.8 core scaling, rho 1e-2, seed 3",
+    desc = {"precision5": "64^5 planted Tucker, ranks 16, geometric 0.8 core scaling, rho 1e-2, seed 3",
+            "uneven6": "64x56x48x40x32x24 planted Tucker, ranks 16x14x12x10x8x6, Student-t(3) "
+                       "noise at rho 1e-2, seed 5"}[name]
+    del T16, T32
+    return {"workload": desc, "elements": int(math.prod(L)),
             "sweeps": S,
             "fp32_form": {"ms_total": round(ms32, 3), "ms_per_sweep": round(ms32 / S, 4),
                           "fit": fit32},
