@@ -24,7 +24,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_liboracle.so")
-_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "planner_oracle.c")]
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "planner_oracle.c"),
+         os.path.join(_HERE, "fp8_oracle.c")]
 
 _lib = None
 
@@ -90,6 +91,14 @@ def _load():
     lib.orc_tree_cost.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.orc_tree_cost.restype = _u64
+    # FP8 E4M3 storage with per-64 scales
+    lib.orc_e4m3_decode.argtypes = [ctypes.c_int]
+    lib.orc_e4m3_decode.restype = ctypes.c_double
+    lib.orc_e4m3_encode.argtypes = [ctypes.c_float]
+    lib.orc_e4m3_encode.restype = ctypes.c_int
+    lib.orc_fp8_quantize.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]
+    lib.orc_fp8_dequantize.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, _dp]
     _lib = lib
     return lib
 
@@ -302,3 +311,38 @@ def tree_cost(L: Sequence[int], K: Sequence[int], labels: Sequence[int], parents
     pa = (ctypes.c_int * n)(*parents)
     r = int(_load().orc_tree_cost(len(L), _i64(L), _i64(K), n, la, pa))
     return None if r == ORC_INF else r
+
+
+# --------------------------------------------------------------------------
+# FP8 E4M3 storage with one FP32 scale per 64 consecutive elements
+# --------------------------------------------------------------------------
+def e4m3_decode(code: int) -> float:
+    """Value of an E4M3 code (format definition; NaN for 0x7F / 0xFF)."""
+    return _load().orc_e4m3_decode(int(code))
+
+
+def e4m3_encode(v: float) -> int:
+    """E4M3 code of v: round to nearest, ties to the even code, saturate at 448."""
+    return _load().orc_e4m3_encode(float(v))
+
+
+def fp8_quantize(x: np.ndarray):
+    """Codes (uint8, same length) and scales (float32, one per 64 elements) of
+    the flattened float32 array x: s = amax / 448 per slab, q = E4M3(x / s)."""
+    lib = _load()
+    xf = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    n = xf.size
+    q = np.empty(n, dtype=np.uint8)
+    s = np.empty((n + 63) // 64, dtype=np.float32)
+    lib.orc_fp8_quantize(n, xf.ctypes.data, q.ctypes.data, s.ctypes.data)
+    return q, s
+
+
+def fp8_dequantize(q: np.ndarray, s: np.ndarray) -> np.ndarray:
+    """s[i // 64] * decode(q[i]) in float64."""
+    lib = _load()
+    qc = np.ascontiguousarray(q, dtype=np.uint8).reshape(-1)
+    sc = np.ascontiguousarray(s, dtype=np.float32).reshape(-1)
+    out = np.empty(qc.size, dtype=np.float64)
+    lib.orc_fp8_dequantize(qc.size, qc.ctypes.data, sc.ctypes.data, out.ctypes.data_as(_dp))
+    return out

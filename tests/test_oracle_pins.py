@@ -253,3 +253,70 @@ def test_sthosvd_singular_values_of_unfolding(orc):
     F, G, evs = orc.sthosvd(X, (3, 3, 3), return_evals=True)
     s = np.linalg.svd(unfold(X, 0), compute_uv=False)
     np.testing.assert_allclose(evs[0], s ** 2, rtol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# FP8 E4M3 storage with per-64 scales (the precision form's FP8 variant)
+# --------------------------------------------------------------------------
+def test_e4m3_decode_follows_the_format(orc):
+    """Sign, 4-bit exponent (bias 7), 3-bit mantissa; subnormals below 2^-6;
+    largest finite 448; one NaN code per sign."""
+    assert orc.e4m3_decode(0x38) == 1.0
+    assert orc.e4m3_decode(0x7E) == 448.0
+    assert orc.e4m3_decode(0x01) == 2.0 ** -9
+    assert orc.e4m3_decode(0x08) == 2.0 ** -6
+    assert orc.e4m3_decode(0x07) == 7 * 2.0 ** -9
+    assert orc.e4m3_decode(0xB8) == -1.0
+    assert math.isnan(orc.e4m3_decode(0x7F)) and math.isnan(orc.e4m3_decode(0xFF))
+    vals = [orc.e4m3_decode(c) for c in range(0x7F)]
+    assert all(b > a for a, b in zip(vals, vals[1:]))
+
+
+def test_e4m3_encode_roundtrip_ties_and_saturation(orc):
+    for c in list(range(0x7F)) + list(range(0x80, 0xFF)):
+        assert orc.e4m3_encode(orc.e4m3_decode(c)) == c, hex(c)
+    # midpoints go to the even code
+    assert orc.e4m3_encode(1.0625) == 0x38      # between 1.0 (0x38) and 1.125 (0x39)
+    assert orc.e4m3_encode(1.1875) == 0x3A      # between 1.125 (0x39) and 1.25 (0x3A)
+    assert orc.e4m3_encode(-1.0625) == 0xB8
+    assert orc.e4m3_encode(2.0 ** -10) == 0x00  # half the smallest subnormal: tie to 0
+    assert orc.e4m3_encode(3 * 2.0 ** -10) == 0x02
+    # beyond 448 saturates
+    assert orc.e4m3_encode(449.0) == 0x7E and orc.e4m3_encode(1e30) == 0x7E
+    assert orc.e4m3_encode(-1e30) == 0xFE
+
+
+def test_e4m3_encode_matches_library_cast(orc):
+    """torch's float8_e4m3fn cast (an independent implementation) agrees on
+    random values inside the finite range."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8_e4m3fn")
+    rng = np.random.default_rng(0)
+    v = np.concatenate([rng.uniform(-448, 448, 20000), rng.standard_normal(20000) * 1e-2,
+                        rng.standard_normal(2000) * 1e-3]).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    got = np.array([orc.e4m3_encode(float(a)) for a in v], dtype=np.uint8)
+    assert np.array_equal(got, ref)
+
+
+def test_fp8_quantize_scales_and_error_bound(orc):
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal(64 * 37 + 11) * np.repeat(rng.uniform(0.01, 100, 38), 64)[:64 * 37 + 11]
+         ).astype(np.float32)
+    x[64 * 5:64 * 6] = 0.0  # an all-zero slab
+    q, s = orc.fp8_quantize(x)
+    assert q.size == x.size and s.size == 38
+    xh = orc.fp8_dequantize(q, s)
+    for j in range(38):
+        sl = slice(64 * j, min(x.size, 64 * j + 64))
+        if np.all(x[sl] == 0):
+            assert s[j] == 1.0 and np.all(xh[sl] == 0)
+            continue
+        # the slab's largest magnitude maps to the largest code
+        assert np.max(q[sl] & 0x7F) == 0x7E
+        # round to nearest: half a spacing, relative 2^-4 for normal codes,
+        # absolute 2^-10 s below 2^-6 s
+        err = np.abs(xh[sl] - x[sl].astype(np.float64))
+        bound = np.maximum(np.abs(x[sl]).astype(np.float64) * 2.0 ** -4, float(s[j]) * 2.0 ** -10)
+        assert np.all(err <= bound * (1 + 1e-6)), j
