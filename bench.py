@@ -451,9 +451,12 @@ def run_precision_form(args, name="precision5"):
     del w
     T16 = torch.empty(T32.shape, dtype=torch.bfloat16, device="cuda")
     tk.tucker_convert_bf16(T32, T16)
+    T8 = tk.tucker_convert_fp8(T32.reshape(-1))
+    T8.shape = tuple(L)
     p32 = tk.tucker_plan(L, K, tk.TUCKER_F32)
     p16 = tk.tucker_plan(L, K, tk.TUCKER_BF16)
-    ws = torch.empty(max(tk.tucker_plan_cost(p32)["ws_bytes"], tk.tucker_plan_cost(p16)["ws_bytes"]),
+    p8 = tk.tucker_plan(L, K, tk.TUCKER_FP8_E4M3)
+    ws = torch.empty(max(tk.tucker_plan_cost(p)["ws_bytes"] for p in (p32, p16, p8)),
                      dtype=torch.uint8, device="cuda")
     F0 = [torch.empty(L[n], K[n], device="cuda") for n in range(len(L))]
     G = torch.empty(*K, device="cuda")
@@ -481,14 +484,16 @@ def run_precision_form(args, name="precision5"):
         torch.cuda.synchronize()
         return ms, fo[0].item()
 
-    run([(p32, T32)] * 2 + [(p16, T16)] * 2)  # warm-up of both plans
+    run([(p32, T32)] * 2 + [(p16, T16)] * 2 + [(p8, T8)] * 2)  # warm-up of every plan
     ms32, fit32 = run([(p32, T32)] * S)
     ms16, fit16 = run([(p16, T16)] * (S - 2) + [(p32, T32)] * 2)
+    ms8, fit8 = run([(p8, T8)] * (S - 2) + [(p32, T32)] * 2)
     rel = abs(fit16 - fit32) / fit32
+    rel8 = abs(fit8 - fit32) / fit32
     desc = {"precision5": "64^5 planted Tucker, ranks 16, geometric 0.8 core scaling, rho 1e-2, seed 3",
             "uneven6": "64x56x48x40x32x24 planted Tucker, ranks 16x14x12x10x8x6, Student-t(3) "
                        "noise at rho 1e-2, seed 5"}[name]
-    del T16, T32
+    del T16, T32, T8
     return {"workload": desc, "elements": int(math.prod(L)),
             "sweeps": S,
             "fp32_form": {"ms_total": round(ms32, 3), "ms_per_sweep": round(ms32 / S, 4),
@@ -496,7 +501,11 @@ def run_precision_form(args, name="precision5"):
             "bf16_polish_form": {"schedule": f"{S - 2} BF16 + 2 FP32", "ms_total": round(ms16, 3),
                                  "ms_per_sweep": round(ms16 / S, 4), "fit": fit16},
             "rel_fit_diff": rel, "bar": 1e-3, "meets_bar": rel <= 1e-3,
-            "speedup_bf16_polish_vs_fp32": round(ms32 / ms16, 3)}
+            "speedup_bf16_polish_vs_fp32": round(ms32 / ms16, 3),
+            "fp8_polish_form": {"schedule": f"{S - 2} FP8 E4M3 (per-64 scales) + 2 FP32",
+                                "ms_total": round(ms8, 3), "ms_per_sweep": round(ms8 / S, 4),
+                                "fit": fit8, "rel_fit_diff": rel8, "meets_bar": rel8 <= 1e-3,
+                                "speedup_vs_fp32": round(ms32 / ms8, 3)}}
 
 
 def run_batch_form(args):

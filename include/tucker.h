@@ -49,7 +49,9 @@ extern "C" {
 typedef enum {
   TUCKER_F32 = 0,  /* float32; factors/core float32                        */
   TUCKER_F64 = 1,  /* float64; factors/core float64                        */
-  TUCKER_BF16 = 2  /* bfloat16 (raw uint16 bits); factors/core float32     */
+  TUCKER_BF16 = 2, /* bfloat16 (raw uint16 bits); factors/core float32     */
+  TUCKER_FP8_E4M3 = 3 /* FP8 E4M3 codes + one float32 scale per 64 elements  */
+                      /* (layout at tucker_fp8_bytes); factors/core float32  */
 } tucker_dtype_t;
 
 /* Which TTM-tree the plan executes (Sec. 3.2 / 3.3). */
@@ -220,6 +222,19 @@ uint64_t tucker_launch_count(void);
  * hi + lo holds x to ~16 significand bits.  n elements; all three device
  * buffers 16-byte aligned; BF16 values are raw uint16 bit patterns. */
 int tucker_convert_bf16(const float* x, uint16_t* hi, uint16_t* lo, int64_t n, void* stream);
+
+/* FP8 storage (the FP8 variant of the precision form).  An FP8 tensor of n
+ * elements occupies tucker_fp8_bytes(n) bytes: n E4M3 codes, then, from the
+ * next 256-byte boundary, ceil(n / 64) float scales; element i stands for
+ * scale[i / 64] * E4M3(code[i]).  tucker_convert_fp8 fills such a buffer from
+ * n floats: per slab of 64 consecutive elements, scale = amax / 448 (1 for an
+ * all-zero slab) and code = E4M3(x / scale), rounded to nearest even and
+ * saturated; out must be 256-byte aligned.  Plans of type TUCKER_FP8_E4M3 run
+ * sweeps, cores and norms on such a tensor (BF16 tree intermediates, FP32
+ * factors); their STHOSVD returns TUCKER_ERR_UNSUPPORTED (run it on the FP32
+ * tensor). */
+size_t tucker_fp8_bytes(int64_t n);
+int tucker_convert_fp8(const float* x, void* out, int64_t n, void* stream);
 
 /* Kernel selection, a bit mask (process-wide; 0 is the default):
  *   bit 0 (1): every TTM on the CUDA-core kernels (otherwise BF16 tensors use

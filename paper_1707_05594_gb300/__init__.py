@@ -19,7 +19,7 @@ from typing import List, Sequence
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtucker_gb300.so")
 
-TUCKER_F32, TUCKER_F64, TUCKER_BF16 = 0, 1, 2
+TUCKER_F32, TUCKER_F64, TUCKER_BF16, TUCKER_FP8_E4M3 = 0, 1, 2, 3
 TREE_OPTIMAL, TREE_CHAIN, TREE_CHAIN_K, TREE_CHAIN_H, TREE_BALANCED = 0, 1, 2, 3, 4
 COST_MACS, COST_ELEMS = 0, 1
 ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "WORKSPACE", -4: "CUDA", -5: "TIMEOUT",
@@ -89,6 +89,10 @@ def lib():
     L.tucker_convert_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_void_p]
     L.tucker_set_kernel_policy.argtypes = [ctypes.c_int]
+    L.tucker_fp8_bytes.argtypes = [ctypes.c_int64]
+    L.tucker_fp8_bytes.restype = ctypes.c_size_t
+    L.tucker_convert_fp8.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_void_p]
     L.tucker_device_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     L.tucker_eig_topk_noalloc.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
                                           ctypes.c_void_p]
@@ -130,7 +134,16 @@ def _i64(a: Sequence[int]):
 
 
 def _ptrs(ts):
+    for t in ts:
+        _req(t, "tensor")
     return (ctypes.c_void_p * len(ts))(*[ctypes.c_void_p(t.data_ptr()) for t in ts])
+
+
+def _dp(t, name):
+    """Device pointer of a contiguous CUDA tensor (the ABI takes dense row-major
+    buffers; a strided view would be read as if it were dense)."""
+    _req(t, name)
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _stream(stream):
@@ -142,6 +155,8 @@ def _stream(stream):
 
 def _dtype_code(t) -> int:
     import torch
+    if isinstance(t, Fp8Tensor):
+        return TUCKER_FP8_E4M3
     if t.dtype == torch.float32:
         return TUCKER_F32
     if t.dtype == torch.float64:
@@ -221,56 +236,56 @@ def workspace(plan: Plan, device=None):
 
 def tucker_sthosvd(plan: Plan, T, F: Sequence, G, ws, stream=None):
     _req(T, "T")
-    _check(lib().tucker_sthosvd(plan.handle, ctypes.c_void_p(T.data_ptr()), _ptrs(F),
-                                ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+    _check(lib().tucker_sthosvd(plan.handle, _dp(T, "T"), _ptrs(F),
+                                _dp(G, "G"), _dp(ws, "ws"),
                                 ws.numel(), _stream(stream)), "tucker_sthosvd")
 
 
 def tucker_hooi_sweep(plan: Plan, T, F_in: Sequence, F_out: Sequence, ws, stream=None):
     _req(T, "T")
-    _check(lib().tucker_hooi_sweep(plan.handle, ctypes.c_void_p(T.data_ptr()), _ptrs(F_in),
-                                   _ptrs(F_out), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+    _check(lib().tucker_hooi_sweep(plan.handle, _dp(T, "T"), _ptrs(F_in),
+                                   _ptrs(F_out), _dp(ws, "ws"), ws.numel(),
                                    _stream(stream)), "tucker_hooi_sweep")
 
 
 def tucker_hooi_sweep_core(plan: Plan, T, F_in: Sequence, F_out: Sequence, G_in, ws, stream=None):
     """HOOI sweep that also returns the core of its INPUT factors (from the tree)."""
     _req(T, "T")
-    _check(lib().tucker_hooi_sweep_core(plan.handle, ctypes.c_void_p(T.data_ptr()), _ptrs(F_in),
+    _check(lib().tucker_hooi_sweep_core(plan.handle, _dp(T, "T"), _ptrs(F_in),
                                         _ptrs(F_out),
-                                        ctypes.c_void_p(G_in.data_ptr()) if G_in is not None else None,
-                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
+                                        _dp(G_in, "G_in") if G_in is not None else None,
+                                        _dp(ws, "ws"), ws.numel(), _stream(stream)),
            "tucker_hooi_sweep_core")
 
 
 def tucker_core(plan: Plan, T, F: Sequence, G, ws, stream=None):
-    _check(lib().tucker_core(plan.handle, ctypes.c_void_p(T.data_ptr()), _ptrs(F),
-                             ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+    _check(lib().tucker_core(plan.handle, _dp(T, "T"), _ptrs(F),
+                             _dp(G, "G"), _dp(ws, "ws"),
                              ws.numel(), _stream(stream)), "tucker_core")
 
 
 def tucker_norm2(plan: Plan, T, out, stream=None):
-    _check(lib().tucker_norm2(plan.handle, ctypes.c_void_p(T.data_ptr()),
-                              ctypes.c_void_p(out.data_ptr()), _stream(stream)), "tucker_norm2")
+    _check(lib().tucker_norm2(plan.handle, _dp(T, "T"),
+                              _dp(out, "out"), _stream(stream)), "tucker_norm2")
 
 
 def tucker_fit(plan: Plan, G, normT2, out, stream=None):
-    _check(lib().tucker_fit(plan.handle, ctypes.c_void_p(G.data_ptr()),
-                            ctypes.c_void_p(normT2.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+    _check(lib().tucker_fit(plan.handle, _dp(G, "G"),
+                            _dp(normT2, "normT2"), _dp(out, "out"),
                             _stream(stream)), "tucker_fit")
 
 
 def tucker_ttm(X, n: int, F, Y, stream=None):
     _req(X, "X")
-    _check(lib().tucker_ttm(X.dim(), _i64(X.shape), ctypes.c_void_p(X.data_ptr()),
-                            _dtype_code(X), n, ctypes.c_void_p(F.data_ptr()), F.shape[1],
-                            ctypes.c_void_p(Y.data_ptr()), _stream(stream)), "tucker_ttm")
+    _check(lib().tucker_ttm(X.dim(), _i64(X.shape), _dp(X, "X"),
+                            _dtype_code(X), n, _dp(F, "F"), F.shape[1],
+                            _dp(Y, "Y"), _stream(stream)), "tucker_ttm")
 
 
 def tucker_gram(Z, n: int, W, stream=None):
     _req(Z, "Z")
-    _check(lib().tucker_gram(Z.dim(), _i64(Z.shape), ctypes.c_void_p(Z.data_ptr()),
-                             _dtype_code(Z), n, ctypes.c_void_p(W.data_ptr()), _stream(stream)),
+    _check(lib().tucker_gram(Z.dim(), _i64(Z.shape), _dp(Z, "Z"),
+                             _dtype_code(Z), n, _dp(W, "W"), _stream(stream)),
            "tucker_gram")
 
 
@@ -282,7 +297,7 @@ def tucker_eig_topk(Ws: Sequence, Fs: Sequence, ws, stream=None):
     Ls = [W.shape[0] for W in Ws]
     Ks = [F.shape[1] for F in Fs]
     _check(lib().tucker_eig_topk(len(Ws), _i64(Ls), _i64(Ks), _ptrs(Ws), _ptrs(Fs),
-                                 _dtype_code(Fs[0]), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                 _dtype_code(Fs[0]), _dp(ws, "ws"), ws.numel(),
                                  _stream(stream)), "tucker_eig_topk")
 
 
@@ -300,9 +315,61 @@ def tucker_eig_topk_noalloc(Ws: Sequence, Fs: Sequence, stream=None):
 def tucker_convert_bf16(x, hi, lo=None, stream=None):
     """hi = bf16(x) (round to nearest even), lo = bf16(x - hi) when given."""
     _req(x, "x")
-    _check(lib().tucker_convert_bf16(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(hi.data_ptr()),
-                                     ctypes.c_void_p(lo.data_ptr()) if lo is not None else None,
+    _check(lib().tucker_convert_bf16(ctypes.c_void_p(x.data_ptr()), _dp(hi, "hi"),
+                                     _dp(lo, "lo") if lo is not None else None,
                                      x.numel(), _stream(stream)), "tucker_convert_bf16")
+
+
+class Fp8Tensor:
+    """A tensor stored as FP8 E4M3 codes with one float scale per 64 elements
+    (the layout of tucker_fp8_bytes) in a uint8 CUDA buffer.  Passed wherever
+    a plan of type TUCKER_FP8_E4M3 takes T."""
+
+    def __init__(self, buf, shape):
+        self.buf = buf
+        self.shape = tuple(int(x) for x in shape)
+        self.is_cuda = buf.is_cuda
+        self.device = buf.device
+
+    def data_ptr(self):
+        return self.buf.data_ptr()
+
+    def is_contiguous(self):
+        return True
+
+    def dim(self):
+        return len(self.shape)
+
+    def numel(self):
+        n = 1
+        for x in self.shape:
+            n *= x
+        return n
+
+    def codes(self):
+        return self.buf[:self.numel()]
+
+    def scales(self):
+        import torch
+        n = self.numel()
+        off = (n + 255) // 256 * 256
+        return self.buf[off:off + 4 * ((n + 63) // 64)].view(torch.float32)
+
+
+def tucker_fp8_bytes(n: int) -> int:
+    return int(lib().tucker_fp8_bytes(int(n)))
+
+
+def tucker_convert_fp8(x, stream=None) -> Fp8Tensor:
+    """FP8 E4M3 copy of the float32 CUDA tensor x with per-64 scales."""
+    import torch
+    _req(x, "x")
+    if x.dtype != torch.float32:
+        raise TypeError("tucker_convert_fp8 takes a float32 tensor")
+    buf = torch.empty(max(256, tucker_fp8_bytes(x.numel())), dtype=torch.uint8, device=x.device)
+    _check(lib().tucker_convert_fp8(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(buf.data_ptr()),
+                                    x.numel(), _stream(stream)), "tucker_convert_fp8")
+    return Fp8Tensor(buf, x.shape)
 
 
 def tucker_set_kernel_policy(policy: int) -> None:
@@ -388,7 +455,7 @@ class Decomposition:
 
 # ---------------------------------------------------------- batched form ---
 def _vp(t):
-    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    return _dp(t, "tensor") if t is not None else None
 
 
 class BatchPlan:

@@ -163,6 +163,13 @@ bool ttm_tc_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X,
                       const void* X_lo);
 int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t C,
                   const float* F, int64_t K, void* Y, bool y_bf16, cudaStream_t s);
+// FP8 E4M3 tensors with per-64 scales (fp8.cu): Y = X x_n F^T with Y FP32 or
+// BF16, and ||X||^2; X is the whole tensor (R * L * C elements) in the layout
+// of tucker_fp8_bytes.
+size_t fp8_scale_offset(int64_t n);
+int launch_ttm_fp8(const void* X, int64_t R, int64_t L, int64_t C, const float* F, int64_t K,
+                   void* Y, int y_dtype, cudaStream_t s);
+int launch_norm2_fp8(const void* X, int64_t n, double* out, cudaStream_t s);
 // kernel-selection policy (tucker_set_kernel_policy): 0 = auto, 1 = CUDA cores only
 int kernel_policy();
 // W += Z_(n) Z_(n)^T for Z viewed as [R][L][C] (W must be zeroed first).

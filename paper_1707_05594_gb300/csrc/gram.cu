@@ -163,6 +163,9 @@ int launch_gram(int z_dtype, const void* Z, int64_t R, int64_t L, int64_t C, dou
       gram_kernel<bf16_t><<<grid, kGramThreads, 0, s>>>(static_cast<const bf16_t*>(Z), R, L, C,
                                                         W, tiles, mpb);
       break;
+    case TUCKER_FP8_E4M3:
+      return fail(TUCKER_ERR_UNSUPPORTED,
+                  "gram: FP8 tensors are read by TTMs only (run STHOSVD on the FP32 tensor)");
     default:
       return fail(TUCKER_ERR_INVALID_ARG, "gram: unknown dtype");
   }

@@ -49,14 +49,18 @@ struct Plan {
   std::vector<void*> prof_events;  // 2 * prof_cap events
   std::vector<int> prof_node, prof_label;
 
-  size_t elem_bytes() const { return dtype == TUCKER_F64 ? 8 : (dtype == TUCKER_BF16 ? 2 : 4); }
-  // tree intermediates: FP64 for FP64 tensors, BF16 for BF16 tensors (the
-  // precision form), FP32 otherwise
+  size_t elem_bytes() const {
+    return dtype == TUCKER_F64 ? 8 : (dtype == TUCKER_BF16 ? 2 : (dtype == TUCKER_FP8_E4M3 ? 1 : 4));
+  }
+  // tree intermediates: FP64 for FP64 tensors, BF16 for BF16 and FP8 tensors
+  // (the precision forms), FP32 otherwise
   int inter_dtype() const {
-    return dtype == TUCKER_F64 ? TUCKER_F64 : (dtype == TUCKER_BF16 ? TUCKER_BF16 : TUCKER_F32);
+    return dtype == TUCKER_F64 ? TUCKER_F64
+                               : ((dtype == TUCKER_BF16 || dtype == TUCKER_FP8_E4M3) ? TUCKER_BF16
+                                                                                     : TUCKER_F32);
   }
   size_t inter_bytes() const {
-    return dtype == TUCKER_F64 ? 8 : (dtype == TUCKER_BF16 ? 2 : 4);
+    return dtype == TUCKER_F64 ? 8 : ((dtype == TUCKER_BF16 || dtype == TUCKER_FP8_E4M3) ? 2 : 4);
   }
 };
 

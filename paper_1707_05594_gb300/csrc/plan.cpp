@@ -279,7 +279,8 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
   if (!L || !K) return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: L or K is NULL");
   tucker_plan_opts_t o{TUCKER_F32, TUCKER_TREE_OPTIMAL, TUCKER_COST_MACS, 0};
   if (opts) o = *opts;
-  if (o.dtype != TUCKER_F32 && o.dtype != TUCKER_F64 && o.dtype != TUCKER_BF16)
+  if (o.dtype != TUCKER_F32 && o.dtype != TUCKER_F64 && o.dtype != TUCKER_BF16 &&
+      o.dtype != TUCKER_FP8_E4M3)
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown dtype");
   if (o.tree < TUCKER_TREE_OPTIMAL || o.tree > TUCKER_TREE_BALANCED)
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown tree kind");

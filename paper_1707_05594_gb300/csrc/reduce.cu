@@ -75,6 +75,8 @@ int launch_norm2(int dtype, const void* X, int64_t n, double* out, cudaStream_t 
     case TUCKER_BF16:
       norm2_kernel<bf16_t><<<grid, kRedThreads, 0, s>>>(static_cast<const bf16_t*>(X), n, out);
       break;
+    case TUCKER_FP8_E4M3:
+      return launch_norm2_fp8(X, n, out, s);
     default:
       return fail(TUCKER_ERR_INVALID_ARG, "norm2: unknown dtype");
   }

@@ -409,6 +409,8 @@ int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, cons
       return ybf ? launch_typed<bf16_t, bf16_t>(X, R, L, C, F, K, Y, s)
                  : launch_typed<bf16_t, float>(X, R, L, C, F, K, Y, s);
     }
+    case TUCKER_FP8_E4M3:
+      return launch_ttm_fp8(X, R, L, C, static_cast<const float*>(F), K, Y, y_dtype, s);
     default: return fail(TUCKER_ERR_INVALID_ARG, "ttm: unknown dtype");
   }
 }

@@ -46,7 +46,8 @@ def orthonormal_factor(L: int, K: int, gen: torch.Generator, device, dtype=torch
     # make the factorisation unique: positive diagonal of R
     s = torch.sign(torch.diagonal(R))
     s[s == 0] = 1
-    return (Q * s).to(dtype)
+    # LAPACK returns Q column-major: make the factor a dense row-major matrix
+    return (Q * s).to(dtype).contiguous()
 
 
 def spectrum_scale(K: int, kind, device):
