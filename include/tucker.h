@@ -242,7 +242,13 @@ int tucker_convert_fp8(const float* x, void* out, int64_t n, void* stream);
  *   bit 1 (2): HOOI sweeps always run the full eigensolver (otherwise they start
  *              from the input factors: two FP64 subspace-iteration steps and an
  *              a-posteriori check, falling back to the full path on the GPU
- *              when the check fails).
+ *              when the check fails);
+ *   bit 2 (4): FP32 TTMs of the column case (mode not last, C >= 64) on the
+ *              tensor cores: tiles and factor split into three BF16 parts,
+ *              six products accumulated in TMEM (off by default: the
+ *              accumulation is not the CUDA cores' exactly rounded FMA, which
+ *              moves the fit identity ||T||^2 - ||G||^2 by ~1e-5 relative on
+ *              low-noise tensors).
  * Used to compare the paths. */
 int tucker_set_kernel_policy(int policy);
 

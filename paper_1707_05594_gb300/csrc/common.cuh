@@ -170,6 +170,11 @@ size_t fp8_scale_offset(int64_t n);
 int launch_ttm_fp8(const void* X, int64_t R, int64_t L, int64_t C, const float* F, int64_t K,
                    void* Y, int y_dtype, cudaStream_t s);
 int launch_norm2_fp8(const void* X, int64_t n, double* out, cudaStream_t s);
+// Tensor-core TTM for FP32 tensors (column case, ttm_tc.cu): FP32 tiles split
+// into BF16 hi + lo in shared memory, products within ~2^-16 of FP32.
+bool ttm_tc_f32_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X);
+int launch_ttm_tc_f32(const float* X, int64_t R, int64_t L, int64_t C, const float* F, int64_t K,
+                      float* Y, cudaStream_t s);
 // kernel-selection policy (tucker_set_kernel_policy): 0 = auto, 1 = CUDA cores only
 int kernel_policy();
 // W += Z_(n) Z_(n)^T for Z viewed as [R][L][C] (W must be zeroed first).

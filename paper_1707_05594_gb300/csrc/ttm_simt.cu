@@ -396,6 +396,9 @@ int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, cons
   switch (x_dtype) {
     case TUCKER_F32:
       if (y_dtype != TUCKER_F32) return fail(TUCKER_ERR_UNSUPPORTED, "ttm: FP32 input needs FP32 output");
+      if ((kernel_policy() & 5) == 4 && ttm_tc_f32_supported(R, L, C, K, X))
+        return launch_ttm_tc_f32(static_cast<const float*>(X), R, L, C, static_cast<const float*>(F), K,
+                                 static_cast<float*>(Y), s);
       return launch_typed<float, float>(X, R, L, C, F, K, Y, s);
     case TUCKER_F64:
       if (y_dtype != TUCKER_F64) return fail(TUCKER_ERR_UNSUPPORTED, "ttm: FP64 input needs FP64 output");

@@ -424,6 +424,252 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// FP32 tensors on the tensor cores (column case).  TMA brings 64 l x 128 c
+// FP32 tiles into a staging ring (no swizzle); a converter warpgroup splits
+// each value into three BF16 parts x1 = RNE(x), x2 = RNE(x - x1),
+// x3 = RNE(x - x1 - x2) (together 24 significant bits) and writes them in the
+// 128-byte-swizzled MN-major layout the MMA reads (the layout TMA produces for
+// BF16 boxes: 16-byte chunk j of row l stored at chunk j ^ (l & 7)).  F is
+// split the same way, B = [F1 | F2 | F3] along N.  Per k-step the MMA warp
+// issues A1 [F1|F2|F3] (N = 3 Np), A2 [F1|F2] (2 Np) and A3 F1 (Np) into one
+// accumulator, whose three column groups the epilogue adds: the six products
+// x_i f_j with i + j <= 4 leave out terms below 2^-24 |x f|, so the result is
+// as accurate as an FP32 contraction, read once at 4 bytes per element, with
+// the arithmetic off the CUDA cores.
+//
+// Warp roles (448 threads): warp 0 TMA producer, warp 1 TMEM + MMA issuer,
+// warps 2-5 converter, warps 6-13 two epilogue groups.
+// ---------------------------------------------------------------------------
+constexpr int kF32St = 2;                            // staging stages (FP32)
+constexpr int kF32Cv = 2;                            // converted stages (3 BF16 parts)
+constexpr int kF32StageBytes = kTileM * kBoxL * 4;   // 32 KB
+constexpr int kF32CvBytes = 3 * kStageBytes;         // 48 KB
+constexpr int kF32Threads = 64 + 128 + kEpiGroups * 128;
+
+__device__ __forceinline__ uint32_t bf_hi_bits(float x) { return f2bf(x); }
+__device__ __forceinline__ float bf_val(uint32_t b) { return __uint_as_float(b << 16); }
+
+template <typename TOut>
+__global__ void __launch_bounds__(kF32Threads, 1)
+    ttm_tc_f32_kernel(const __grid_constant__ CUtensorMap map_x, TOut* __restrict__ Y,
+                      const TcParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* stage = smem;                                        // kF32St x 32 KB
+  unsigned char* conv = stage + (size_t)kF32St * kF32StageBytes;      // kF32Cv x 48 KB
+  unsigned char* bsm = conv + (size_t)kF32Cv * kF32CvBytes;
+  const int N3 = 3 * P.Np;
+  const size_t b_bytes = (size_t)P.nk * N3 * 128;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + ((b_bytes + 15) & ~size_t(15)));
+  uint64_t* st_full = bars;                   // kF32St
+  uint64_t* st_empty = st_full + kF32St;      // kF32St
+  uint64_t* cv_full = st_empty + kF32St;      // kF32Cv
+  uint64_t* cv_empty = cv_full + kF32Cv;      // kF32Cv
+  uint64_t* tfull = cv_empty + kF32Cv;        // kAccBufs
+  uint64_t* tempty = tfull + kAccBufs;        // kAccBufs
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + kAccBufs);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(kAccBufs * N3)) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kF32St; ++s) {
+      mbar_init(&st_full[s], 1);
+      mbar_init(&st_empty[s], 4);
+    }
+    for (int s = 0; s < kF32Cv; ++s) {
+      mbar_init(&cv_full[s], 4);
+      mbar_init(&cv_empty[s], 1);
+    }
+    for (int b = 0; b < kAccBufs; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // B = [F1 | F2 | F3]^T as BF16, K-major without swizzle (as in ttm_tc_kernel)
+  for (int idx = threadIdx.x; idx < N3 * P.nk * kBoxL; idx += kF32Threads) {
+    const int row = idx / (P.nk * kBoxL);
+    const int l = idx - row * (P.nk * kBoxL);
+    const int part = row / P.Np, k = row - part * P.Np;
+    float f = 0.f;
+    if (k < P.K && l < P.L) f = P.F[(int64_t)l * P.K + k];
+    const uint32_t f1 = bf_hi_bits(f);
+    const float r1 = f - bf_val(f1);
+    const uint32_t f2 = bf_hi_bits(r1);
+    const uint32_t f3 = bf_hi_bits(r1 - bf_val(f2));
+    const uint16_t v = (uint16_t)(part == 0 ? f1 : (part == 1 ? f2 : f3));
+    const int chunk = l / kBoxL, lc = l - chunk * kBoxL;
+    const size_t off = (size_t)chunk * N3 * 128 + (size_t)(row >> 3) * 1024 + (size_t)(lc >> 3) * 128 +
+                       (size_t)(row & 7) * 16 + (size_t)(lc & 7) * 2;
+    *reinterpret_cast<uint16_t*>(bsm + off) = v;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+        const int64_t r = t / P.ctiles;
+        const int c0 = (int)((t - r * P.ctiles) * kTileM);
+        for (int kc = 0; kc < P.nk; ++kc, ++it) {
+          const uint32_t s = it % kF32St, ph = (it / kF32St) & 1u;
+          if (!mbar_wait(&st_empty[s], ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&st_full[s], (uint32_t)kF32StageBytes);
+          tma_load_3d(stage + (size_t)s * kF32StageBytes, &map_x, &st_full[s], c0, kc * kBoxL, (int)r);
+        }
+      }
+      const uint32_t issued = it;
+      for (uint32_t j = (issued > (uint32_t)kF32St ? issued - kF32St : 0); j < issued; ++j) {
+        const uint32_t s = j % kF32St, ph = (j / kF32St) & 1u;
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(&st_full[s], ph) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc3 = idesc_bf16(N3, 1);
+      const uint32_t idesc2 = idesc_bf16(2 * P.Np, 1);
+      const uint32_t idesc1 = idesc_bf16(P.Np, 1);
+      const uint32_t b_base = smem_u32(bsm);
+      uint32_t it = 0, tcount = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x, ++tcount) {
+        const uint32_t buf = tcount % kAccBufs, aph = (tcount / kAccBufs) & 1u;
+        if (!mbar_wait(&tempty[buf], aph ^ 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + buf * (uint32_t)N3;
+        for (int kc = 0; kc < P.nk; ++kc, ++it) {
+          const uint32_t s = it % kF32Cv, ph = (it / kF32Cv) & 1u;
+          if (!mbar_wait(&cv_full[s], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(conv + (size_t)s * kF32CvBytes);
+#pragma unroll
+          for (int ks = 0; ks < kBoxL / 16; ++ks) {
+            const uint64_t a1 = smem_desc(a_base + ks * 2048, 8192, 1024, kSwizzle128);
+            const uint64_t a2 = smem_desc(a_base + kStageBytes + ks * 2048, 8192, 1024, kSwizzle128);
+            const uint64_t a3 = smem_desc(a_base + 2 * kStageBytes + ks * 2048, 8192, 1024, kSwizzle128);
+            const uint32_t b_chunk = b_base + (uint32_t)(kc * N3 * 128);
+            const uint64_t bd = smem_desc(b_chunk + ks * 256, 128, 1024, kSwizzleNone);
+            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+            mma_bf16(d_tmem, a1, bd, idesc3, acc);
+            mma_bf16(d_tmem, a2, bd, idesc2, 1u);
+            mma_bf16(d_tmem, a3, bd, idesc1, 1u);
+          }
+          mma_commit(&cv_empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[buf]);
+      }
+    }
+  } else if (warp < 6) {
+    // ------------------------------------------------------------ converter
+    const int ct = threadIdx.x - 64;  // 0 .. 127
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+      for (int kc = 0; kc < P.nk; ++kc, ++it) {
+        const uint32_t ss = it % kF32St, sph = (it / kF32St) & 1u;
+        const uint32_t cs = it % kF32Cv, cph = (it / kF32Cv) & 1u;
+        if (!mbar_wait(&st_full[ss], sph, abort_flag) || !mbar_wait(&cv_empty[cs], cph ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const float* src = reinterpret_cast<const float*>(stage + (size_t)ss * kF32StageBytes);
+        unsigned char* d1 = conv + (size_t)cs * kF32CvBytes;
+#pragma unroll 4
+        for (int i = 0; i < (kTileM * kBoxL / 2) / 128; ++i) {
+          const int p = ct + 128 * i;  // pair index: l = p / 64, c = 2 (p % 64)
+          const int l = p >> 6, c = (p & 63) << 1;
+          const float2 x = *reinterpret_cast<const float2*>(src + l * kTileM + c);
+          const uint32_t a0 = bf_hi_bits(x.x), b0 = bf_hi_bits(x.y);
+          const float ra = x.x - bf_val(a0), rb = x.y - bf_val(b0);
+          const uint32_t a1 = bf_hi_bits(ra), b1 = bf_hi_bits(rb);
+          const uint32_t a2 = bf_hi_bits(ra - bf_val(a1)), b2 = bf_hi_bits(rb - bf_val(b1));
+          const int cc = c & 63;
+          const uint32_t off = (uint32_t)(c >> 6) * 8192u + (uint32_t)l * 128u +
+                               ((uint32_t)((cc >> 3) ^ (l & 7)) << 4) + (uint32_t)((cc & 7) << 1);
+          *reinterpret_cast<uint32_t*>(d1 + off) = a0 | (b0 << 16);
+          *reinterpret_cast<uint32_t*>(d1 + kStageBytes + off) = a1 | (b1 << 16);
+          *reinterpret_cast<uint32_t*>(d1 + 2 * kStageBytes + off) = a2 | (b2 << 16);
+        }
+        // the tensor core reads the converted tile through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&cv_full[cs]);
+          mbar_arrive(&st_empty[ss]);
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t group = (uint32_t)(warp - 6) / 4u;
+    uint32_t tcount = group;
+    for (int64_t t = blockIdx.x + (int64_t)group * gridDim.x; t < P.tiles;
+         t += (int64_t)kEpiGroups * gridDim.x, tcount += kEpiGroups) {
+      const uint32_t buf = tcount % kAccBufs, aph = (tcount / kAccBufs) & 1u;
+      if (!mbar_wait(&tfull[buf], aph, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + buf * (uint32_t)N3;
+      const int64_t r = t / P.ctiles;
+      const int64_t c = (t - r * P.ctiles) * kTileM + row;
+      float g1[16], g2[16], g3[16];
+      for (int k0 = 0; k0 < P.Np; k0 += 16) {
+        tmem_ld16(tbase + k0, g1);
+        tmem_ld16(tbase + P.Np + k0, g2);
+        tmem_ld16(tbase + 2 * P.Np + k0, g3);
+        tmem_wait_ld();
+        if (k0 + 16 >= P.Np) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+        if (c < P.C) {
+          TOut* yp = Y + (r * P.K) * P.C + c;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (k0 + j < P.K) yp[(int64_t)(k0 + j) * P.C] = to_out<TOut>((g3[j] + g2[j]) + g1[j]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(ncols));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -446,13 +692,14 @@ EncodeFn encoder() {
 }
 
 int make_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims,
-             const cuuint64_t* strides_bytes, const cuuint32_t* box) {
+             const cuuint64_t* strides_bytes, const cuuint32_t* box,
+             CUtensorMapDataType dtype = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+             CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   EncodeFn enc = encoder();
   if (!enc) return fail(TUCKER_ERR_CUDA, "ttm_tc: cuTensorMapEncodeTiled unavailable");
   const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank,
-                         const_cast<void*>(base), dims, strides_bytes, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  const CUresult r = enc(m, dtype, (cuuint32_t)rank, const_cast<void*>(base), dims, strides_bytes,
+                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TUCKER_ERR_CUDA, "ttm_tc: cuTensorMapEncodeTiled failed");
   return TUCKER_OK;
@@ -545,6 +792,52 @@ int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t
                 : launch_variant<false, false, float>(mh, ml, Y, P, smem, s);
 }
 
+size_t smem_bytes_f32(int Np, int nk) {
+  return 1024 + (size_t)kF32St * kF32StageBytes + (size_t)kF32Cv * kF32CvBytes +
+         (((size_t)nk * 3 * Np * 128 + 15) & ~size_t(15)) + (2 * kF32St + 2 * kF32Cv + 2 * kAccBufs) * 8 +
+         16;
+}
+
+// FP32 column-case TTM on the tensor cores: C % 4 == 0 (16-byte TMA strides),
+// C >= 64, K <= 32 (four accumulator buffers of 3 Np columns in TMEM), and B
+// plus the rings within shared memory.
+bool ttm_tc_f32_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X) {
+  if (K < 1 || K > 32 || L < 1 || L > 1024 || C < 64 || C % 4 != 0) return false;
+  if ((uintptr_t)X % 16 != 0 || R > INT32_MAX || C > INT32_MAX) return false;
+  const int Np = (int)((K + 15) / 16 * 16), nk = (int)((L + kBoxL - 1) / kBoxL);
+  return smem_bytes_f32(Np, nk) <= 227 * 1024;
+}
+
+int launch_ttm_tc_f32(const float* X, int64_t R, int64_t L, int64_t C, const float* F, int64_t K,
+                      float* Y, cudaStream_t s) {
+  if (!ttm_tc_f32_supported(R, L, C, K, X))
+    return fail(TUCKER_ERR_UNSUPPORTED, "ttm_tc_f32: shape or alignment not supported");
+  TcParams P{};
+  P.R = R;
+  P.C = C;
+  P.L = (int)L;
+  P.K = (int)K;
+  P.Np = (int)((K + 15) / 16 * 16);
+  P.nk = (int)((L + kBoxL - 1) / kBoxL);
+  P.F = F;
+  P.ctiles = (C + kTileM - 1) / kTileM;
+  P.tiles = R * P.ctiles;
+  CUtensorMap mx;
+  const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)L, (cuuint64_t)R};
+  const cuuint64_t str[2] = {(cuuint64_t)C * 4, (cuuint64_t)C * L * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)kTileM, (cuuint32_t)kBoxL, 1u};
+  int rc = make_map(&mx, X, 3, dims, str, box, CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (rc) return rc;
+  const size_t smem = smem_bytes_f32(P.Np, P.nk);
+  auto kern = ttm_tc_f32_kernel<float>;
+  TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t grid = std::min<int64_t>(P.tiles, sm_count());
+  kern<<<(unsigned)grid, kF32Threads, smem, s>>>(mx, Y, P);
+  TK_LAUNCH_CHECK("ttm_tc_f32");
+  return TUCKER_OK;
+}
+
 }  // namespace tk
 
 namespace tk {
@@ -555,8 +848,8 @@ int kernel_policy() { return g_policy.load(std::memory_order_relaxed); }
 }  // namespace tk
 
 extern "C" int tucker_set_kernel_policy(int policy) {
-  if (policy < 0 || policy > 3)
-    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 3]");
+  if (policy < 0 || policy > 7)
+    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 7]");
   tk::g_policy.store(policy, std::memory_order_relaxed);
   return TUCKER_OK;
 }

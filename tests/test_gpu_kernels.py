@@ -55,8 +55,13 @@ def test_ttm_matches_oracle(tk, orc, shape, n, K, dtype):
     out_shape = list(shape)
     out_shape[n] = K
     Y = torch.empty(out_shape, dtype=fdt, device="cuda")
-    tk.tucker_ttm(X.cuda(), n, F.cuda(), Y)
-    torch.cuda.synchronize()
+    # the CUDA-core kernels (policy 1): exact FMA accumulation bound
+    assert tk.lib().tucker_set_kernel_policy(1) == 0
+    try:
+        tk.tucker_ttm(X.cuda(), n, F.cuda(), Y)
+        torch.cuda.synchronize()
+    finally:
+        tk.lib().tucker_set_kernel_policy(0)
     Xd = X.double().numpy()
     Fd = F.double().numpy()
     ref = orc.ttm(Xd, n, Fd.T)
@@ -109,6 +114,47 @@ def test_ttm_bf16_tensor_cores(tk, orc, shape, n, K, policy):
     bound = orc.ttm(np.abs(Xd), n, np.abs(Fd).T)
     err = np.abs(Y.double().cpu().numpy() - ref)
     tol = (2.0 ** -15 + (shape[n] + 2) * 2.0 ** -23) * bound + 1e-30
+    assert np.all(err <= tol), (err / (bound + 1e-30)).max()
+
+
+F32_TC_CASES = [
+    # column case (C % 4 == 0, C >= 64): ragged tiles (C not a multiple of 128),
+    # l chunks (L > 64, L not a multiple of 64), K > 16 and K = 64
+    ((5, 200, 136), 1, 20), ((2, 64, 1000), 1, 16), ((130, 72), 0, 1), ((200, 4, 200), 0, 20),
+    ((4, 256, 128), 1, 32), ((96, 512), 0, 17), ((3, 37, 68), 1, 5), ((40, 40, 40, 40), 1, 20),
+]
+
+
+@pytest.mark.parametrize("shape,n,K", F32_TC_CASES)
+def test_ttm_f32_tensor_cores(tk, orc, shape, n, K):
+    """FP32 tensor, FP32 factor on tcgen05: tile and factor split into three
+    BF16 parts each (24 significant bits); the six products x_i f_j with
+    i + j <= 4 accumulate in FP32 in TMEM.  The parts reproduce x and f to
+    2^-24 relative and the omitted products are below 2^-24 |x f|, hence
+    the bound (2^-21 + (L + 2) * 2^-22) * sum |x f| (tensor-core FP32
+    accumulation counted at twice the FMA rounding)."""
+    X = workloads.random_tensor(shape, seed=sum(shape) * 5 + n, dtype=torch.float32)
+    F = workloads.random_factor(shape[n], K, seed=K + 3, dtype=torch.float32, orthonormal=False)
+    out_shape = list(shape)
+    out_shape[n] = K
+    Y = torch.full(out_shape, float("nan"), dtype=torch.float32, device="cuda")
+    assert tk.lib().tucker_set_kernel_policy(4) == 0
+    try:
+        tk.tucker_ttm(X.cuda(), n, F.cuda(), Y)
+        torch.cuda.synchronize()
+    finally:
+        tk.lib().tucker_set_kernel_policy(0)
+    assert status_ok(tk)
+    Xd = X.double().numpy()
+    Fd = F.double().numpy()
+    ref = orc.ttm(Xd, n, Fd.T)
+    bound = orc.ttm(np.abs(Xd), n, np.abs(Fd).T)
+    err = np.abs(Y.double().cpu().numpy() - ref)
+    # also the mean signed error relative to the bound: a bias of the
+    # accumulation shows here, a random rounding error averages out
+    bias = float(np.mean((Y.double().cpu().numpy() - ref) / (bound + 1e-30)))
+    print("f32 tensor-core TTM mean signed error / bound:", bias)
+    tol = (2.0 ** -21 + (shape[n] + 2) * 2.0 ** -22) * bound + 1e-30
     assert np.all(err <= tol), (err / (bound + 1e-30)).max()
 
 
