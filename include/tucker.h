@@ -318,6 +318,14 @@ int tucker_batch_graph_create(tucker_batch_t b, const float* T, const float* F_i
 int tucker_batch_graph_launch(tucker_batch_t b, void* graph_exec, void* stream);
 void tucker_batch_graph_destroy(void* graph_exec);
 
+/* Self-test of the failure path (no paper counterpart): one thread waits,
+ * through the same bounded wait the tensor-core pipelines use, on a barrier
+ * that nothing completes.  The wait gives up after its limit (2 s), records
+ * TUCKER_ERR_TIMEOUT in the device error word (read it with
+ * tucker_device_status) and the kernel returns; *outcome is 2 when the wait
+ * gave up, 1 if it completed.  Synchronous on `stream`. */
+int tucker_selftest_wait_timeout(int* outcome, void* stream);
+
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* tucker_last_error(void);
 

@@ -94,6 +94,7 @@ def lib():
     L.tucker_convert_fp8.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_void_p]
     L.tucker_device_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.tucker_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
     L.tucker_eig_topk_noalloc.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
                                           ctypes.c_void_p]
     L.tucker_eig_ws_bytes.argtypes = [ctypes.c_int, _i64p, _i64p]
@@ -380,6 +381,15 @@ def tucker_device_status(reset: bool = True) -> int:
     st = ctypes.c_int(0)
     _check(lib().tucker_device_status(ctypes.byref(st), 1 if reset else 0), "tucker_device_status")
     return st.value
+
+
+def tucker_selftest_wait_timeout(stream=None) -> int:
+    """Runs the bounded-wait self-test (a wait that nothing completes gives up
+    after its limit); returns 2 when the wait gave up, 1 if it completed."""
+    out = ctypes.c_int(0)
+    _check(lib().tucker_selftest_wait_timeout(ctypes.byref(out), _stream(stream)),
+           "tucker_selftest_wait_timeout")
+    return out.value
 
 
 def tucker_profile_enable(plan: Plan, capacity: int) -> None:

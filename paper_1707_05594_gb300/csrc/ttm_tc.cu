@@ -669,6 +669,22 @@ __global__ void __launch_bounds__(kF32Threads, 1)
   }
 }
 
+// One thread waits, through the kernels' bounded wait, on an mbarrier that no
+// thread or copy ever completes: the wait gives up after its time limit and
+// records TUCKER_ERR_TIMEOUT in the device error word, and the kernel returns
+// normally (the failure path of the pipelines, exercised without a fault).
+__global__ void wait_selftest_kernel(int* returned) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const bool ok = mbar_wait(&bar, 0u, &abort_flag);
+    *returned = ok ? 1 : 2;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -851,6 +867,25 @@ extern "C" int tucker_set_kernel_policy(int policy) {
   if (policy < 0 || policy > 7)
     return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 7]");
   tk::g_policy.store(policy, std::memory_order_relaxed);
+  return TUCKER_OK;
+}
+
+extern "C" int tucker_selftest_wait_timeout(int* outcome, void* stream) {
+  if (!outcome) return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_selftest_wait_timeout: NULL");
+  int* d = nullptr;
+  TK_CUDA_TRY(cudaMalloc(&d, sizeof(int)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    tk::wait_selftest_kernel<<<1, 32, 0, s>>>(d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(outcome, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess)
+    return tk::fail(TUCKER_ERR_CUDA, std::string("tucker_selftest_wait_timeout: ") + cudaGetErrorString(e));
+  tk::count_launches(1);
   return TUCKER_OK;
 }
 
