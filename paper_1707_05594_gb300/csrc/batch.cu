@@ -62,18 +62,6 @@ inline int64_t node_tiles(int64_t R, int64_t C) {
   return (R * C + kBThreads - 1) / kBThreads;
 }
 
-// Division by a small runtime divisor d (1 <= d < 2^16) for numerators below
-// 2^16: q = floor(x * ceil(2^32 / d) / 2^32) is exact there (the error of the
-// scaled reciprocal stays below 2^-16 <= 1/d).
-struct SmallDiv {
-  unsigned m;
-  int d;
-  __device__ __forceinline__ explicit SmallDiv(int d_) : m(0), d(d_) {
-    if (d_ > 1) m = (unsigned)((0x100000000ull + (unsigned)d_ - 1) / (unsigned)d_);
-  }
-  __device__ __forceinline__ int div(int x) const { return d == 1 ? x : (int)__umulhi((unsigned)x, m); }
-};
-
 // Out[r, k, c] = sum_l F[l, k] In[r, l, c] for one tile of one node, F in
 // chunks of 32 l through shared memory.  Each thread accumulates the K
 // outputs of one position (KB >= K registers).  Staged tiles (C < 32) copy

@@ -176,7 +176,15 @@ __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccO
       cp_async_wait<kDepth - 1>();
       A x[VEC];
       const unsigned char* slot = &ring[l % kDepth][tid][0];
-      if constexpr (sizeof(TIn) == 2) {
+      if constexpr (sizeof(TIn) == 2 && VEC == 8) {
+        const uint4 q = *reinterpret_cast<const uint4*>(slot);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          x[2 * j] = __uint_as_float(w[j] << 16);
+          x[2 * j + 1] = __uint_as_float(w[j] & 0xFFFF0000u);
+        }
+      } else if constexpr (sizeof(TIn) == 2) {
         const uint2 q = *reinterpret_cast<const uint2*>(slot);
         x[0] = __uint_as_float(q.x << 16);
         x[1] = __uint_as_float(q.x & 0xFFFF0000u);
@@ -335,11 +343,37 @@ int pick_kb(int64_t K) {
   return 32;
 }
 
+// Element loaders of the staged short-row kernel (common.cuh).
+struct LoadF32 {
+  const float* p;
+  __device__ __forceinline__ float operator()(int64_t e) const { return __ldg(p + e); }
+};
+struct LoadBF16 {
+  const unsigned short* p;
+  __device__ __forceinline__ float operator()(int64_t e) const { return bf16_to_float(__ldg(p + e)); }
+};
+
 template <typename TIn, typename TOut, int KB>
 int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccOf<TIn>::type* F,
               int64_t K, TOut* Y, cudaStream_t s) {
   const unsigned gy = (unsigned)((K + KB - 1) / KB);
   constexpr int V = sizeof(TIn) == 8 ? 2 : 4;
+  // (16-byte slots for BF16 columns measured slower than 8-byte ones)
+  constexpr int Vc = V;
+  if constexpr (sizeof(TIn) != 8) {
+    // short fibres of the last mode: whole rows staged through shared memory
+    if (C == 1) {
+      int rc = TUCKER_OK;
+      bool done;
+      if constexpr (sizeof(TIn) == 4)
+        done = try_launch_rows_staged(LoadF32{reinterpret_cast<const float*>(X)}, R, L,
+                                      reinterpret_cast<const float*>(F), K, Y, s, &rc);
+      else
+        done = try_launch_rows_staged(LoadBF16{reinterpret_cast<const unsigned short*>(X)}, R, L,
+                                      reinterpret_cast<const float*>(F), K, Y, s, &rc);
+      if (done) return rc;
+    }
+  }
   if (C == 1 && L % V == 0 && (uintptr_t)X % (V * sizeof(TIn)) == 0) {
     const int64_t gx = (R + kColsThreads - 1) / kColsThreads;
     ttm_rows_pipe_kernel<TIn, TOut, KB, V><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
@@ -354,9 +388,16 @@ int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccO
     TK_LAUNCH_CHECK("ttm_rows");
     return TUCKER_OK;
   }
+  const int64_t total = R * C;
+  if (Vc != V && C % Vc == 0 && (uintptr_t)X % (Vc * sizeof(TIn)) == 0) {
+    const int64_t gx = (total / Vc + kColsThreads - 1) / kColsThreads;
+    ttm_cols_pipe_kernel<TIn, TOut, KB, Vc><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
+        X, F, Y, R, (int)L, C, (int)K);
+    TK_LAUNCH_CHECK("ttm_cols");
+    return TUCKER_OK;
+  }
   const bool vec_ok = (C % V == 0) && ((uintptr_t)X % (V * sizeof(TIn)) == 0) &&
                       ((uintptr_t)Y % (V * sizeof(TOut)) == 0);
-  const int64_t total = R * C;
   if (vec_ok) {
     const int64_t gx = (total / V + kColsThreads - 1) / kColsThreads;
     ttm_cols_pipe_kernel<TIn, TOut, KB, V><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
@@ -407,7 +448,10 @@ int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, cons
       const bool ybf = y_dtype == TUCKER_BF16;
       if (!ybf && y_dtype != TUCKER_F32)
         return fail(TUCKER_ERR_UNSUPPORTED, "ttm: BF16 input needs FP32 or BF16 output");
-      if (kernel_policy() == 0 && ttm_tc_supported(R, L, C, K, X, nullptr))
+      // tensor cores, except for short last-mode fibres (a 128-row tile of
+      // rows of at most 32 elements is too little work per pipeline stage)
+      if ((kernel_policy() & 1) == 0 && !(C == 1 && L <= kStagedMaxL) &&
+          ttm_tc_supported(R, L, C, K, X, nullptr))
         return launch_ttm_tc(X, nullptr, R, L, C, static_cast<const float*>(F), K, Y, ybf, s);
       return ybf ? launch_typed<bf16_t, bf16_t>(X, R, L, C, F, K, Y, s)
                  : launch_typed<bf16_t, float>(X, R, L, C, F, K, Y, s);
