@@ -179,3 +179,29 @@ def test_batch_plan_validation(tk, dims, ranks, msg):
     with pytest.raises(tk.TuckerError) as e:
         tk.BatchPlan(dims, ranks)
     assert msg in str(e.value)
+
+
+def test_optimal_tree_never_above_prior_trees_on_benchmark_metadata(tk):
+    """Sec. 6 benchmark metadata (L_n in {20, 50, 100, 400}, K_n = L_n / c,
+    c in {1.25, 2, 5, 10}): the optimal tree's load is at most that of the
+    chain (K-order, h-order) and balanced trees of Sec. 3.2, on a seeded
+    sample of 5-D and 6-D inputs."""
+    import math
+    modes = [(L, int(round(L / c))) for L in (20, 50, 100, 400) for c in (1.25, 2, 5, 10)]
+    rng = random.Random(7)
+    checked = 0
+    while checked < 150:
+        N = rng.choice((5, 6))
+        pick = [rng.choice(modes) for _ in range(N)]
+        L = [p[0] for p in pick]
+        K = [p[1] for p in pick]
+        if math.prod(L) > 8e9:
+            continue
+        try:
+            opt = tk.tucker_plan_cost(tk.tucker_plan(L, K))["tree_macs"]
+        except tk.TuckerError:
+            continue
+        for tree in (tk.TREE_CHAIN_K, tk.TREE_CHAIN_H, tk.TREE_BALANCED, tk.TREE_CHAIN):
+            other = tk.tucker_plan_cost(tk.tucker_plan(L, K, tree=tree))["tree_macs"]
+            assert opt <= other, (L, K, tree)
+        checked += 1
