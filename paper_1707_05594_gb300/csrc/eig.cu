@@ -871,6 +871,13 @@ __device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
   for (int idx = tid; idx < K * K; idx += 256) Uf[idx] = (idx / K == idx % K) ? 1.f : 0.f;
   __syncthreads();
   if (warp == 0) {
+    // an off-diagonal entry at the FP32 rounding level of H (2e-7 max|h_ii|)
+    // counts as zero: otherwise rounding noise would keep every pair rotating
+    // and the sweep loop would always run to its cap; such entries only turn
+    // vectors inside the K-dimensional Ritz space
+    float hmax = 0.f;
+    for (int i = 0; i < K; ++i) hmax = fmaxf(hmax, fabsf(Hf[i * K + i]));
+    const float floor_abs = 2e-7f * hmax;
     for (int sweep = 0; sweep < 30; ++sweep) {
       int rotated = 0;
       for (int p = 0; p < K - 1; ++p) {
@@ -878,7 +885,7 @@ __device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
           const float apq = Hf[p * K + q];
           const float app = Hf[p * K + p], aqq = Hf[q * K + q];
           if (apq == 0.f) continue;
-          if (fabsf(apq) <= 1e-9f * sqrtf(fabsf(app) * fabsf(aqq))) {
+          if (fabsf(apq) <= floor_abs || fabsf(apq) <= 1e-9f * sqrtf(fabsf(app) * fabsf(aqq))) {
             __syncwarp();
             if (lane == 0) Hf[p * K + q] = Hf[q * K + p] = 0.f;
             __syncwarp();
