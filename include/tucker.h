@@ -149,6 +149,12 @@ int tucker_core(tucker_plan_t plan, const void* T, const void* const* F, void* G
 /* ||T||_F^2 accumulated in double, written to the device double *out. */
 int tucker_norm2(tucker_plan_t plan, const void* T, double* out, void* stream);
 
+/* Synchronous finiteness check of n elements of type dtype at X (a tensor,
+ * factor or core): returns TUCKER_ERR_NONFINITE when any is NaN or Inf (their
+ * sum of squares is not finite), TUCKER_OK otherwise.  Allocates nothing;
+ * waits for `stream`. */
+int tucker_check_finite(const void* X, int dtype, int64_t n, void* stream);
+
 /* Error metric of Sec. 2.2 ("normalized root mean square"), using
  * ||T - G x F||^2 = ||T||^2 - ||G||^2 for orthonormal factors:
  * out[0] = fit = 1 - sqrt(max(0, normT2 - ||G||^2)) / sqrt(normT2),

@@ -95,6 +95,7 @@ def lib():
                                      ctypes.c_void_p]
     L.tucker_device_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     L.tucker_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
+    L.tucker_check_finite.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
     L.tucker_eig_topk_noalloc.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
                                           ctypes.c_void_p]
     L.tucker_eig_ws_bytes.argtypes = [ctypes.c_int, _i64p, _i64p]
@@ -383,6 +384,12 @@ def tucker_device_status(reset: bool = True) -> int:
     return st.value
 
 
+def tucker_check_finite(X, stream=None) -> None:
+    """Raises TuckerError (NONFINITE) when X holds a NaN or an Inf."""
+    _check(lib().tucker_check_finite(_dp(X, "X"), _dtype_code(X), X.numel(), _stream(stream)),
+           "tucker_check_finite")
+
+
 def tucker_selftest_wait_timeout(stream=None) -> int:
     """Runs the bounded-wait self-test (a wait that nothing completes gives up
     after its limit); returns 2 when the wait gave up, 1 if it completed."""
@@ -461,6 +468,21 @@ class Decomposition:
 
     def fit(self) -> float:
         return float(self.fit_out[0].item())
+
+    def state_dict(self) -> dict:
+        """Checkpoint: the HOOI state is the factors (and the core of the last
+        step); copied to host memory."""
+        return {"L": tuple(self.T.shape), "K": tuple(self.G.shape),
+                "F": [f.detach().cpu().clone() for f in self.F],
+                "G": self.G.detach().cpu().clone()}
+
+    def load_state_dict(self, sd: dict) -> None:
+        """Resume from state_dict(): same lengths and ranks required."""
+        if tuple(sd["L"]) != tuple(self.T.shape) or tuple(sd["K"]) != tuple(self.G.shape):
+            raise ValueError("checkpoint of a different shape")
+        for f, s in zip(self.F, sd["F"]):
+            f.copy_(s)
+        self.G.copy_(sd["G"])
 
 
 # ---------------------------------------------------------- batched form ---

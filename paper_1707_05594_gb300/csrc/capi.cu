@@ -4,8 +4,12 @@
 // (Sec. 5), solves the N eigenproblems in one batched launch, and runs the
 // new-core chain, STHOSVD, norms and fit.
 #include <atomic>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
+
+#include "nvtx3/nvToolsExt.h"
 
 #include "common.cuh"
 
@@ -43,7 +47,15 @@ struct ProfScope {
   Plan& p;
   cudaStream_t s;
   int slot = -1;
+  bool nvtx = false;
   ProfScope(Plan& pp, cudaStream_t ss, int node, int label) : p(pp), s(ss) {
+    if (p.prof_cap > 0) {
+      // an NVTX range per node on the host timeline (for timeline tools)
+      char name[64];
+      snprintf(name, sizeof(name), "tucker node %d mode %d", node, label);
+      nvtxRangePushA(name);
+      nvtx = true;
+    }
     if (p.prof_cap > 0 && p.prof_n < p.prof_cap) {
       slot = p.prof_n++;
       p.prof_node[(size_t)slot] = node;
@@ -53,6 +65,7 @@ struct ProfScope {
   }
   ~ProfScope() {
     if (slot >= 0) cudaEventRecord(static_cast<cudaEvent_t>(p.prof_events[2 * (size_t)slot + 1]), s);
+    if (nvtx) nvtxRangePop();
   }
 };
 
@@ -319,6 +332,26 @@ int tucker_norm2(tucker_plan_t plan, const void* T, double* out, void* stream) {
   const Plan& p = plan->p;
   return launch_norm2(p.dtype, T, (int64_t)tensor_size(p, 0), out,
                       static_cast<cudaStream_t>(stream));
+}
+
+// ||X||^2 of the finiteness check: a device double of the library, so the
+// check allocates nothing.
+static __device__ double g_check_norm2;
+
+int tucker_check_finite(const void* X, int dtype, int64_t n, void* stream) {
+  if (!X || n < 0) return fail(TUCKER_ERR_INVALID_ARG, "tucker_check_finite: invalid argument");
+  if (n == 0) return TUCKER_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* d = nullptr;
+  TK_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void**>(&d), g_check_norm2));
+  const int rc = launch_norm2(dtype, X, n, d, s);
+  if (rc) return rc;
+  double h = 0.0;
+  TK_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TK_CUDA_TRY(cudaStreamSynchronize(s));
+  if (!std::isfinite(h))
+    return fail(TUCKER_ERR_NONFINITE, "tucker_check_finite: the tensor holds NaN or Inf values");
+  return TUCKER_OK;
 }
 
 int tucker_fit(tucker_plan_t plan, const void* G, const double* normT2, double* out,
