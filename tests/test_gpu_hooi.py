@@ -60,6 +60,11 @@ CASES = [
     ((20, 17, 15), (5, 4, 6), 0.6, 12, torch.float64, 0),
     ((33, 45), (7, 7), 0.4, 13, torch.float32, 0),               # N = 2
     ((12, 10, 8), (12, 10, 8), 0.1, 14, torch.float32, 0),       # full rank
+    ((7, 6, 5, 6, 4, 5), (3, 2, 2, 3, 2, 2), 0.3, 15, torch.float32, 0),        # N = 6
+    ((5, 4, 6, 4, 5, 3, 4), (2, 2, 3, 2, 2, 2, 2), 0.3, 16, torch.float32, 0),  # N = 7
+    ((4, 3, 4, 3, 4, 3, 4, 3), (2, 2, 2, 2, 2, 2, 2, 2), 0.3, 17, torch.float32, 0),  # N = 8, the maximum
+    ((6, 5, 4, 6, 5, 4, 3, 4), (2, 3, 2, 2, 2, 2, 2, 2), 0.2, 18, torch.float64, 0),  # N = 8, FP64
+    ((30, 25, 20), (1, 1, 1), 0.2, 19, torch.float32, 0),         # rank 1 in every mode
 ]
 
 
