@@ -321,8 +321,54 @@ int tucker_batch_fit(tucker_batch_t b, const float* T, const float* F, const flo
 int tucker_batch_graph_create(tucker_batch_t b, const float* T, const float* F_in, float* F_out,
                               float* G_in, const double* normT2, double* fit, void* ws,
                               size_t ws_bytes, void** graph_exec);
+/* Launches a recorded sweep.  Fails with TUCKER_ERR_INVALID_ARG for a graph
+ * not created from this batch, or recorded before a later
+ * tucker_batch_autotune changed the batch's launch configurations (create it
+ * again). */
 int tucker_batch_graph_launch(tucker_batch_t b, void* graph_exec, void* stream);
 void tucker_batch_graph_destroy(void* graph_exec);
+
+/* Autotuner of the batched form's launch configurations (no paper
+ * counterpart; the batched form runs many small tensors per launch).  Every
+ * launch site of a sweep -- each tree level, the core step, each
+ * reconstruction step of the fit -- is run with every candidate
+ * configuration on these buffers and timed with CUDA events (one untimed
+ * launch, then `reps` timed ones, 1 <= reps <= 1000); the fastest is kept
+ * (another candidate replaces the default only when at least 2 % faster).
+ * Candidates: positions per thread of the long-row TTM and reconstruction
+ * tiles (256, 512 or 1024 consecutive positions per 256-thread tile; 1024
+ * only when every rank <= 8), the row length below which a TTM tile stages
+ * whole rows through shared memory (0, 16, 32 or 64), the order of the
+ * site's nodes (tensor by tensor, or the nodes with the most tiles first),
+ * and for long-row TTM tiles of one position per thread whether each chunk
+ * of 32 input rows is copied into shared memory by cp.async first.
+ * None of them changes the order in which the terms of any output are
+ * summed: the tree's outputs, the factors and cores of a sweep are the same
+ * bits tuned or not (the fit's per-tensor sums are added atomically and may
+ * differ in the last bits).  STHOSVD keeps the default configuration.
+ * The call runs the sites on the batch's data: it overwrites G with the core
+ * of F (as tucker_batch_sweep with G_in) and the workspace's intermediates;
+ * T and F are read only.  Synchronous.  Graphs recorded before it must be
+ * created again.  F and G as in tucker_batch_sweep; needs a prepared `ws`. */
+int tucker_batch_autotune(tucker_batch_t b, const float* T, const float* F, float* G, void* ws,
+                          size_t ws_bytes, int reps, void* stream);
+/* The batch's launch configuration per site (host only).  *n_sites = the
+ * number of sites; for the first min(cap, *n_sites) sites, cfg[6i..6i+5] =
+ * (kind: 0 tree level, 1 core step, 2 fit step; index within the kind;
+ * positions per thread; staging row length; order 0/1; cp.async rows 0/1)
+ * and ms[2i], ms[2i+1] = the default's and the chosen configuration's time
+ * per launch in the last tucker_batch_autotune (-1 before one).  cfg and ms
+ * may be NULL. */
+int tucker_batch_tuning(tucker_batch_t b, int cap, int* n_sites, int* cfg, float* ms);
+/* Sets every site's launch configuration from records in tucker_batch_tuning's
+ * cfg format and order (to reuse an earlier tuning without timing again).
+ * TUCKER_ERR_INVALID_ARG for a wrong site count or order, positions per
+ * thread other than 1, 2 (or 4 when every rank <= 8), a staging length
+ * outside 0..64, an order or cp.async flag other than 0/1, or the cp.async
+ * flag with more than one position per thread or on a fit step (fit steps
+ * ignore the staging length).  Host only; the batch must be prepared again
+ * (tucker_batch_prepare) and its graphs created again. */
+int tucker_batch_set_tuning(tucker_batch_t b, int n_sites, const int* cfg);
 
 /* Self-test of the failure path (no paper counterpart): one thread waits,
  * through the same bounded wait the tensor-core pipelines use, on a barrier

@@ -119,6 +119,10 @@ def lib():
     L.tucker_batch_graph_launch.argtypes = [vp, vp, vp]
     L.tucker_batch_graph_destroy.argtypes = [vp]
     L.tucker_batch_graph_destroy.restype = None
+    L.tucker_batch_autotune.argtypes = [vp, vp, vp, vp, vp, sz, ctypes.c_int, vp]
+    L.tucker_batch_tuning.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+    L.tucker_batch_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.tucker_last_error.restype = ctypes.c_char_p
     L.tucker_version.restype = ctypes.c_int
     _lib = L
@@ -571,6 +575,47 @@ def tucker_batch_fit(b: BatchPlan, T, F, G, normT2, fit, ws, stream=None):
            "tucker_batch_fit")
 
 
+def tucker_batch_autotune(b: BatchPlan, T, F, G, ws, reps: int = 5, stream=None):
+    """Times every candidate launch configuration of each sweep site on these
+    buffers and keeps the fastest (synchronous; overwrites G with the core of
+    F).  Graphs recorded earlier must be created again."""
+    _check(lib().tucker_batch_autotune(b.handle, _vp(T), _vp(F), _vp(G), _vp(ws),
+                                       ws.numel() * ws.element_size(), int(reps), _stream(stream)),
+           "tucker_batch_autotune")
+
+
+_SITE_KIND = {0: "level", 1: "core", 2: "fit"}
+
+
+def tucker_batch_tuning(b: BatchPlan):
+    """The launch configuration of every sweep site: a list of dicts with the
+    site (kind, index), its positions per thread, staging row length and node
+    order, and the default's and the chosen configuration's ms per launch from
+    the last autotune (-1 before one)."""
+    n = ctypes.c_int()
+    _check(lib().tucker_batch_tuning(b.handle, 0, ctypes.byref(n), None, None), "tucker_batch_tuning")
+    cfg = (ctypes.c_int * (6 * n.value))()
+    ms = (ctypes.c_float * (2 * n.value))()
+    _check(lib().tucker_batch_tuning(b.handle, n.value, ctypes.byref(n), cfg, ms), "tucker_batch_tuning")
+    out = []
+    for i in range(n.value):
+        c = cfg[6 * i:6 * i + 6]
+        out.append({"site": _SITE_KIND[c[0]], "index": c[1], "ppt": c[2], "stage_c": c[3],
+                    "order": c[4], "async": c[5], "ms_default": ms[2 * i], "ms_tuned": ms[2 * i + 1]})
+    return out
+
+
+def tucker_batch_set_tuning(b: BatchPlan, sites):
+    """Sets every site's configuration from tucker_batch_tuning's list (the
+    dicts' site, index, ppt, stage_c, order, async); prepare the batch again after."""
+    kind = {v: k for k, v in _SITE_KIND.items()}
+    flat = []
+    for s in sites:
+        flat += [kind[s["site"]], s["index"], s["ppt"], s["stage_c"], s["order"], s.get("async", 0)]
+    arr = (ctypes.c_int * len(flat))(*flat)
+    _check(lib().tucker_batch_set_tuning(b.handle, len(sites), arr), "tucker_batch_set_tuning")
+
+
 class BatchGraph:
     """An executable CUDA graph of one batched sweep (tucker_batch_graph_*)."""
 
@@ -620,6 +665,15 @@ class BatchDecomposition:
         tucker_batch_sthosvd(self.b, self.T, self.Fbuf[self.cur], self.G, self.ws)
         tucker_batch_fit(self.b, self.T, self.Fbuf[self.cur], self.G, self.normT2, self.fit_out,
                          self.ws)
+
+    def autotune(self, reps: int = 5):
+        """Tunes the batch's launch configurations on the current factors
+        (tucker_batch_autotune); the recorded graphs are dropped and recorded
+        again at the next graph sweep.  G is overwritten with the core of the
+        current factors."""
+        self._graphs = None
+        tucker_batch_autotune(self.b, self.T, self.Fbuf[self.cur], self.G, self.ws, reps)
+        return tucker_batch_tuning(self.b)
 
     def sweep(self, graph: bool = True):
         src, dst = self.Fbuf[self.cur], self.Fbuf[1 - self.cur]

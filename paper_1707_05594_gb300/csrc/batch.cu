@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -38,8 +39,10 @@ struct BNode {
   int64_t f_off;     // into F (L x K factor, applied transposed)
   int64_t R, C;      // view [R][L][C] of the input
   int32_t L, K;
-  int64_t tile0;     // first tile (256 positions) of this node
-  int32_t in_src, out_dst;
+  int64_t tile0;     // first tile of this node
+  int8_t in_src, out_dst;
+  int8_t staged;     // rows staged through shared memory (set with the tile map)
+  int8_t pad[5];
 };
 
 // One 32 x 32 tile of a leaf Gram W = Z_(n) Z_(n)^T (lower triangle, ti >= tj).
@@ -50,51 +53,49 @@ struct BGram {
   int32_t L, ti, tj, z_src;
 };
 
-// Tiles of a node: nodes whose rows are at least 32 elements long (C >= 32)
-// take 256 consecutive (r, c) positions per tile and read along c; shorter
-// rows take 256 / C whole rows per tile, staged through shared memory.
-constexpr int kStageC = 32;
-inline int64_t node_tiles(int64_t R, int64_t C) {
-  if (C < kStageC) {
+// Launch configuration of one batched launch site (a tree level, the core
+// step, an STHOSVD step or a fit step), picked by tucker_batch_autotune.
+// None of the knobs changes the order in which any output's terms are summed.
+//   ppt:     positions per thread of the direct (long-row) tiles: a tile is
+//            256 * ppt consecutive (r, c) positions
+//   stage_c: nodes with rows shorter than stage_c (C < stage_c) take whole
+//            rows per tile, staged through shared memory (0: never)
+//   order:   0 = nodes in plan order (tensor by tensor), 1 = nodes with the
+//            most tiles first (longest-processing-time order)
+//   async:   direct tiles copy each chunk of 32 input rows into shared memory
+//            with cp.async before the multiply-adds (one position per thread)
+struct BCfg {
+  int ppt = 1, stage_c = 32, order = 0, async = 0;
+};
+
+// Tiles of a node under a configuration.  Staged tiles take 256 / C whole
+// rows; direct tiles take 256 * ppt consecutive positions and read along c.
+inline bool node_staged(int64_t C, const BCfg& cfg) { return C < cfg.stage_c; }
+inline int64_t node_tiles(int64_t R, int64_t C, const BCfg& cfg) {
+  if (node_staged(C, cfg)) {
     const int64_t rt = kBThreads / C;
     return (R + rt - 1) / rt;
   }
-  return (R * C + kBThreads - 1) / kBThreads;
+  const int64_t tp = (int64_t)kBThreads * cfg.ppt;
+  return (R * C + tp - 1) / tp;
 }
 
 // Out[r, k, c] = sum_l F[l, k] In[r, l, c] for one tile of one node, F in
 // chunks of 32 l through shared memory.  Each thread accumulates the K
-// outputs of one position (KB >= K registers).  Staged tiles (C < 32) copy
-// the rows of the chunk into shared memory transposed, Ts[l][position], with
-// coalesced loads, and write their outputs back the same way.
+// outputs of each of its positions (KB >= K registers per position), l in
+// increasing order.  Staged tiles (short rows) copy the rows of the chunk
+// into shared memory transposed, Ts[l][position], with coalesced loads, and
+// write their outputs back the same way; they take one position per thread.
 template <int KB>
-__device__ __forceinline__ void bttm_tile(const BNode& nd, int64_t t, const float* __restrict__ T,
-                                          const float* __restrict__ F, float* __restrict__ inter,
-                                          float* __restrict__ G, float* Fs /* [32][KB] */,
-                                          float (*Ts)[kBThreads + 1]) {
+__device__ __forceinline__ void bttm_staged(const BNode& nd, int64_t t, const float* __restrict__ src,
+                                            float* __restrict__ dst, const float* __restrict__ f,
+                                            float* Fs /* [32][KB] */, float (*Ts)[kBThreads + 1]) {
   const int tid = threadIdx.x;
-  const bool staged = nd.C < kStageC;
-  const float* src = (nd.in_src ? inter : T) + nd.in_off;
-  float* dst = (nd.out_dst ? G : inter) + nd.out_off;
-  const float* f = F + nd.f_off;
-  // staged: rows r0 .. r0 + nrows - 1, position tid = (r - r0) * C + c
-  // direct: position p = t * 256 + tid
-  int64_t r0 = 0, r = 0, c = 0;
-  int nrows = 0, C = (int)(staged ? nd.C : 0);
-  bool active;
-  if (staged) {
-    const int rt = kBThreads / C;
-    r0 = t * rt;
-    nrows = (int)min((int64_t)rt, nd.R - r0);
-    active = tid < nrows * C;
-  } else {
-    const int64_t p = t * kBThreads + tid;
-    active = p < nd.R * nd.C;
-    if (active) {
-      r = p / nd.C;
-      c = p - r * nd.C;
-    }
-  }
+  const int C = (int)nd.C;
+  const int rt = kBThreads / C;
+  const int64_t r0 = t * rt;
+  const int nrows = (int)min((int64_t)rt, nd.R - r0);
+  const bool active = tid < nrows * C;
   float acc[KB];
 #pragma unroll
   for (int k = 0; k < KB; ++k) acc[k] = 0.f;
@@ -105,90 +106,187 @@ __device__ __forceinline__ void bttm_tile(const BNode& nd, int64_t t, const floa
       const int l = i / KB, k = i - (i / KB) * KB;
       Fs[i] = (l < lc && k < nd.K) ? f[(int64_t)(l0 + l) * nd.K + k] : 0.f;
     }
-    if (staged) {
-      // row rr of the chunk: lc * C contiguous elements
-      const int seg = lc * C;
-      const SmallDiv dseg(seg), dc(C);
-      for (int i = tid; i < nrows * seg; i += kBThreads) {
-        const int rr = dseg.div(i), o = i - rr * seg;
-        const int l = dc.div(o), cc = o - l * C;
-        Ts[l][rr * C + cc] = src[((r0 + rr) * nd.L + l0) * C + o];
-      }
-      __syncthreads();
-      if (active) {
-        for (int l = 0; l < lc; ++l) {
-          const float x = Ts[l][tid];
-#pragma unroll
-          for (int k = 0; k < KB; ++k) acc[k] = fmaf(Fs[l * KB + k], x, acc[k]);
-        }
-      }
-    } else {
-      __syncthreads();
-      if (active) {
-        const float* in = src + (r * nd.L + l0) * nd.C + c;
-#pragma unroll 4
-        for (int l = 0; l < lc; ++l) {
-          const float x = __ldg(in + (int64_t)l * nd.C);
-#pragma unroll
-          for (int k = 0; k < KB; ++k) acc[k] = fmaf(Fs[l * KB + k], x, acc[k]);
-        }
-      }
-    }
-  }
-  if (staged) {
-    // outputs through shared memory: row rr owns K * C contiguous elements
-    __syncthreads();
-    if (active) {
-#pragma unroll
-      for (int k = 0; k < KB; ++k)
-        if (k < nd.K) Ts[k][tid] = acc[k];
-    }
-    __syncthreads();
-    const int seg = nd.K * C;
+    // row rr of the chunk: lc * C contiguous elements
+    const int seg = lc * C;
     const SmallDiv dseg(seg), dc(C);
     for (int i = tid; i < nrows * seg; i += kBThreads) {
       const int rr = dseg.div(i), o = i - rr * seg;
-      const int k = dc.div(o), cc = o - k * C;
-      dst[(r0 + rr) * seg + o] = Ts[k][rr * C + cc];
+      const int l = dc.div(o), cc = o - l * C;
+      Ts[l][rr * C + cc] = src[((r0 + rr) * nd.L + l0) * C + o];
     }
-    return;
+    __syncthreads();
+    if (active) {
+      for (int l = 0; l < lc; ++l) {
+        const float x = Ts[l][tid];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) acc[k] = fmaf(Fs[l * KB + k], x, acc[k]);
+      }
+    }
   }
-  if (!active) return;
+  // outputs through shared memory: row rr owns K * C contiguous elements
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < KB; ++k)
+      if (k < nd.K) Ts[k][tid] = acc[k];
+  }
+  __syncthreads();
+  const int seg = nd.K * C;
+  const SmallDiv dseg(seg), dc(C);
+  for (int i = tid; i < nrows * seg; i += kBThreads) {
+    const int rr = dseg.div(i), o = i - rr * seg;
+    const int k = dc.div(o), cc = o - k * C;
+    dst[(r0 + rr) * seg + o] = Ts[k][rr * C + cc];
+  }
+}
+
+constexpr int kDepth = 8;  // rows of a chunk loaded ahead by the direct TTM tiles
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Direct tile, one position per thread, each chunk of up to 32 input rows
+// copied into Ts[l][thread] by cp.async (32 copies per thread in flight, no
+// registers held while they travel), then multiplied from shared memory.
+template <int KB>
+__device__ __forceinline__ void bttm_async(const BNode& nd, int64_t t, const float* __restrict__ src,
+                                           float* __restrict__ dst, const float* __restrict__ f,
+                                           float* Fs /* [32][KB] */, float (*Ts)[kBThreads + 1]) {
+  const int tid = threadIdx.x;
+  const int64_t p = t * kBThreads + tid;
+  const bool act = p < nd.R * nd.C;
+  const int64_t r = act ? p / nd.C : 0, c = act ? p - r * nd.C : 0;
+  const float* in = src + (r * nd.L) * nd.C + c;
+  float acc[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) acc[k] = 0.f;
+  for (int l0 = 0; l0 < nd.L; l0 += 32) {
+    const int lc = min(32, nd.L - l0);
+    __syncthreads();  // the previous chunk's reads of Ts and Fs are done
+    if (act)
+      for (int l = 0; l < lc; ++l) cp_async4(&Ts[l][tid], in + (int64_t)(l0 + l) * nd.C);
+    for (int i = tid; i < 32 * KB; i += kBThreads) {
+      const int l = i / KB, k = i - (i / KB) * KB;
+      Fs[i] = (l < lc && k < nd.K) ? f[(int64_t)(l0 + l) * nd.K + k] : 0.f;
+    }
+    cp_async_commit_wait_all();
+    __syncthreads();
+    if (act) {
+      for (int l = 0; l < lc; ++l) {
+        const float x = Ts[l][tid];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) acc[k] = fmaf(Fs[l * KB + k], x, acc[k]);
+      }
+    }
+  }
+  if (!act) return;
   float* out = dst + (r * nd.K) * nd.C + c;
 #pragma unroll
   for (int k = 0; k < KB; ++k)
     if (k < nd.K) out[(int64_t)k * nd.C] = acc[k];
 }
 
+template <int KB, int PPT>
+__device__ __forceinline__ void bttm_direct(const BNode& nd, int64_t t, const float* __restrict__ src,
+                                            float* __restrict__ dst, const float* __restrict__ f,
+                                            float* Fs /* [32][KB] */) {
+  const int tid = threadIdx.x;
+  const int64_t M = nd.R * nd.C;
+  const float* in[PPT];
+  int64_t ob[PPT];
+  bool act[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    const int64_t p = (t * PPT + j) * kBThreads + tid;
+    act[j] = p < M;
+    const int64_t r = act[j] ? p / nd.C : 0, c = act[j] ? p - r * nd.C : 0;
+    in[j] = src + (r * nd.L) * nd.C + c;
+    ob[j] = (r * nd.K) * nd.C + c;
+  }
+  float acc[PPT][KB];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j)
+#pragma unroll
+    for (int k = 0; k < KB; ++k) acc[j][k] = 0.f;
+  for (int l0 = 0; l0 < nd.L; l0 += 32) {
+    const int lc = min(32, nd.L - l0);
+    __syncthreads();
+    for (int i = tid; i < 32 * KB; i += kBThreads) {
+      const int l = i / KB, k = i - (i / KB) * KB;
+      Fs[i] = (l < lc && k < nd.K) ? f[(int64_t)(l0 + l) * nd.K + k] : 0.f;
+    }
+    __syncthreads();
+    if (act[0]) {
+      // kDepth rows of the chunk are loaded before their multiply-adds, so
+      // that each thread has kDepth * PPT loads in flight
+      for (int lb = 0; lb < lc; lb += kDepth) {
+        float x[kDepth][PPT];
+#pragma unroll
+        for (int u = 0; u < kDepth; ++u)
+#pragma unroll
+          for (int j = 0; j < PPT; ++j)
+            x[u][j] = (lb + u < lc && act[j]) ? __ldg(in[j] + (int64_t)(l0 + lb + u) * nd.C) : 0.f;
+#pragma unroll
+        for (int u = 0; u < kDepth; ++u) {
+          if (lb + u < lc) {
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+              const float fk = Fs[(lb + u) * KB + k];
+#pragma unroll
+              for (int j = 0; j < PPT; ++j) acc[j][k] = fmaf(fk, x[u][j], acc[j][k]);
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    if (!act[j]) continue;
+    float* out = dst + ob[j];
+#pragma unroll
+    for (int k = 0; k < KB; ++k)
+      if (k < nd.K) out[(int64_t)k * nd.C] = acc[j][k];
+  }
+}
+
+template <int KB, int PPT, bool ASYNC>
+__device__ __forceinline__ void bttm_tile(const BNode& nd, int64_t t, const float* __restrict__ T,
+                                          const float* __restrict__ F, float* __restrict__ inter,
+                                          float* __restrict__ G, float* Fs,
+                                          float (*Ts)[kBThreads + 1]) {
+  const float* src = (nd.in_src ? inter : T) + nd.in_off;
+  float* dst = (nd.out_dst ? G : inter) + nd.out_off;
+  const float* f = F + nd.f_off;
+  if (nd.staged) bttm_staged<KB>(nd, t, src, dst, f, Fs, Ts);
+  else if (ASYNC) bttm_async<KB>(nd, t, src, dst, f, Fs, Ts);
+  else bttm_direct<KB, PPT>(nd, t, src, dst, f, Fs);
+}
+
 // One block per tile; the block runs the variant whose KB is the smallest of
 // 4, 8, 12, 16, 24, 32 that holds its node's K (KMAX bounds the variants so
 // that the kernel's register count follows the batch's largest rank).
-template <int KMAX>
+template <int KMAX, int PPT, bool ASYNC>
 __global__ void __launch_bounds__(kBThreads)
-    bttm_kernel(const BNode* __restrict__ nodes, int nnodes, const float* __restrict__ T,
-                const float* __restrict__ F, float* __restrict__ inter, float* __restrict__ G) {
+    bttm_kernel(const BNode* __restrict__ nodes, const int* __restrict__ tile_node,
+                const float* __restrict__ T, const float* __restrict__ F, float* __restrict__ inter,
+                float* __restrict__ G) {
   __shared__ __align__(16) float Fs[32 * KMAX];
   __shared__ float Ts[32][kBThreads + 1];
-  __shared__ int node_idx;
   const int64_t tile = blockIdx.x;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = nnodes - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (nodes[mid].tile0 <= tile) lo = mid;
-      else hi = mid - 1;
-    }
-    node_idx = lo;
-  }
-  __syncthreads();
-  const BNode nd = nodes[node_idx];
+  const BNode nd = nodes[tile_node[tile]];
   const int64_t t = tile - nd.tile0;
-  if (nd.K <= 4) bttm_tile<4>(nd, t, T, F, inter, G, Fs, Ts);
-  else if (nd.K <= 8 || KMAX <= 8) bttm_tile<(KMAX < 8 ? KMAX : 8)>(nd, t, T, F, inter, G, Fs, Ts);
-  else if (nd.K <= 12 || KMAX <= 12) bttm_tile<(KMAX < 12 ? KMAX : 12)>(nd, t, T, F, inter, G, Fs, Ts);
-  else if (nd.K <= 16 || KMAX <= 16) bttm_tile<(KMAX < 16 ? KMAX : 16)>(nd, t, T, F, inter, G, Fs, Ts);
-  else if (nd.K <= 24 || KMAX <= 24) bttm_tile<(KMAX < 24 ? KMAX : 24)>(nd, t, T, F, inter, G, Fs, Ts);
-  else bttm_tile<KMAX>(nd, t, T, F, inter, G, Fs, Ts);
+  if (nd.K <= 4) bttm_tile<4, PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
+  else if (nd.K <= 8 || KMAX <= 8) bttm_tile<(KMAX < 8 ? KMAX : 8), PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
+  else if (nd.K <= 12 || KMAX <= 12) bttm_tile<(KMAX < 12 ? KMAX : 12), PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
+  else if (nd.K <= 16 || KMAX <= 16) bttm_tile<(KMAX < 16 ? KMAX : 16), PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
+  else if (nd.K <= 24 || KMAX <= 24) bttm_tile<(KMAX < 24 ? KMAX : 24), PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
+  else bttm_tile<KMAX, PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
 }
 
 // 32 x 32 Gram tile over all M = R*C columns: FP32 products summed in runs of
@@ -286,67 +384,87 @@ struct BExp {
 
 constexpr int kExpMaxL = 200;
 
-// Each thread owns one (r, c) position: it keeps the K inputs In[r, :, c] in
-// registers and produces the L outputs one after another (F from shared
-// memory, broadcast).  In the last step the FP32 differences T - Out are
-// squared and summed in FP32 per thread, then reduced in FP64 per block and
-// added to res2[tensor].
-template <int KB>
+// Each thread owns PPT (r, c) positions, 256 apart: it keeps the K inputs
+// In[r, :, c] of each in registers and produces the L outputs one after
+// another (F from shared memory, broadcast).  In the last step the FP32
+// differences T - Out are squared and summed in FP32 per position, then
+// reduced in FP64 per block and added to res2[tensor].
+template <int KB, int PPT>
 __global__ void __launch_bounds__(kBThreads)
-    bexpand_kernel(const BExp* __restrict__ steps, int nsteps, const float* __restrict__ T,
+    bexpand_kernel(const BExp* __restrict__ steps, const int* __restrict__ tile_step,
+                   const float* __restrict__ T,
                    const float* __restrict__ F, const float* __restrict__ G,
                    float* __restrict__ inter, double* __restrict__ res2) {
   __shared__ __align__(16) float Fs[kExpMaxL][KB];
-  __shared__ int step_idx;
   __shared__ double red[kBThreads / 32];
   const int64_t tile = blockIdx.x;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = nsteps - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (steps[mid].tile0 <= tile) lo = mid;
-      else hi = mid - 1;
-    }
-    step_idx = lo;
-  }
-  __syncthreads();
-  const BExp st = steps[step_idx];
+  const BExp st = steps[tile_step[tile]];
   const float* f = F + st.f_off;
   for (int i = threadIdx.x; i < st.L * KB; i += kBThreads) {
     const int l = i / KB, k = i - (i / KB) * KB;
     Fs[l][k] = k < st.K ? f[(int64_t)l * st.K + k] : 0.f;
   }
   __syncthreads();
-  const int64_t p = (tile - st.tile0) * kBThreads + threadIdx.x;
-  float part = 0.f;
-  if (p < st.R * st.C) {
-    const int64_t r = p / st.C, c = p - (p / st.C) * st.C;
+  const int64_t M = st.R * st.C;
+  float y[PPT][KB];
+  int64_t ob[PPT];
+  bool act[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    const int64_t p = ((tile - st.tile0) * PPT + j) * kBThreads + threadIdx.x;
+    act[j] = p < M;
+    const int64_t r = act[j] ? p / st.C : 0, c = act[j] ? p - r * st.C : 0;
     const float* in = (st.in_src ? inter : G) + st.in_off + (r * st.K) * st.C + c;
-    float y[KB];
 #pragma unroll
-    for (int k = 0; k < KB; ++k) y[k] = k < st.K ? in[(int64_t)k * st.C] : 0.f;
-    const int64_t ob = (r * st.L) * st.C + c;
+    for (int k = 0; k < KB; ++k) y[j][k] = (act[j] && k < st.K) ? in[(int64_t)k * st.C] : 0.f;
+    ob[j] = (r * st.L) * st.C + c;
+  }
+  float part[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) part[j] = 0.f;
+  if (act[0]) {
     if (st.last) {
-      const float* t = T + st.out_off + ob;
-      for (int l = 0; l < st.L; ++l) {
-        float v = 0.f;
+      // kDepth rows of T are loaded ahead of their comparisons
+      const float* t = T + st.out_off;
+      for (int lb = 0; lb < st.L; lb += kDepth) {
+        float tv[kDepth][PPT];
 #pragma unroll
-        for (int k = 0; k < KB; ++k) v = fmaf(Fs[l][k], y[k], v);
-        const float d = __ldg(t + (int64_t)l * st.C) - v;
-        part = fmaf(d, d, part);
+        for (int u = 0; u < kDepth; ++u)
+#pragma unroll
+          for (int j = 0; j < PPT; ++j)
+            tv[u][j] = (lb + u < st.L && act[j]) ? __ldg(t + ob[j] + (int64_t)(lb + u) * st.C) : 0.f;
+#pragma unroll
+        for (int u = 0; u < kDepth; ++u) {
+          if (lb + u >= st.L) break;
+#pragma unroll
+          for (int j = 0; j < PPT; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < KB; ++k) v = fmaf(Fs[lb + u][k], y[j][k], v);
+            if (act[j]) {
+              const float d = tv[u][j] - v;
+              part[j] = fmaf(d, d, part[j]);
+            }
+          }
+        }
       }
     } else {
-      float* o = inter + st.out_off + ob;
+      float* o = inter + st.out_off;
       for (int l = 0; l < st.L; ++l) {
-        float v = 0.f;
 #pragma unroll
-        for (int k = 0; k < KB; ++k) v = fmaf(Fs[l][k], y[k], v);
-        o[(int64_t)l * st.C] = v;
+        for (int j = 0; j < PPT; ++j) {
+          float v = 0.f;
+#pragma unroll
+          for (int k = 0; k < KB; ++k) v = fmaf(Fs[l][k], y[j][k], v);
+          if (act[j]) o[ob[j] + (int64_t)l * st.C] = v;
+        }
       }
     }
   }
   if (!st.last) return;
-  double s = (double)part;
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) s += (double)part[j];
 #pragma unroll
   for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -371,6 +489,17 @@ int64_t prod64(const int64_t* d, int a, int b) {
   return p;
 }
 
+// Device side of one launch site: its work table, the tile -> item map (one
+// int per tile, so that a block finds its item with one load), the tile
+// count of the current configuration and the map's capacity (the most tiles
+// any configuration gives).
+template <class Item>
+struct DevSite {
+  Item* items = nullptr;
+  int* map = nullptr;
+  int64_t tiles = 0, cap = 0;
+};
+
 }  // namespace
 }  // namespace tk
 
@@ -389,7 +518,6 @@ struct tucker_batch_s {
   std::vector<std::vector<BGram>> sth_gram;   // STHOSVD Gram of step n
   std::vector<EigDesc> eig;                   // [mode][tensor]
   std::vector<std::vector<BExp>> fit_steps;   // reconstruction step s of every tensor
-  int64_t level_tiles_max = 0;
   // workspace layout (bytes)
   size_t off_inter = 0, bytes_inter = 0;      // floats
   size_t off_gram = 0, bytes_gram = 0;        // doubles
@@ -400,41 +528,92 @@ struct tucker_batch_s {
   size_t ws_total = 0;
   // device table addresses (valid after prepare)
   void* prepared_ws = nullptr;
-  std::vector<const BNode*> d_levels;
-  std::vector<int64_t> level_tiles;
-  const BNode* d_core = nullptr;
-  int64_t core_tiles = 0;
+  std::vector<DevSite<BNode>> d_levels;       // per tree level
+  DevSite<BNode> d_core;
   const BGram* d_gram = nullptr;
-  std::vector<const BNode*> d_sth_ttm;
-  std::vector<int64_t> sth_tiles;
+  std::vector<DevSite<BNode>> d_sth;          // STHOSVD step n
   std::vector<const BGram*> d_sth_gram;
   const EigDesc* d_eig = nullptr;
-  std::vector<const BExp*> d_fit;
-  std::vector<int64_t> fit_tiles;
+  std::vector<DevSite<BExp>> d_fit;           // reconstruction step s
   const int64_t* d_t_off = nullptr;
   const int64_t* d_t_size = nullptr;
+  // launch configurations per site (defaults until tucker_batch_autotune)
+  std::vector<BCfg> lvl_cfg;                  // per tree level
+  BCfg core_cfg;
+  std::vector<BCfg> fit_cfg;                  // per reconstruction step
+  std::vector<float> tune_ms_default, tune_ms_best;  // per site, from the last autotune
+  uint64_t epoch = 0;                         // bumped when the tile maps change
 
-  std::unordered_map<void*, uint64_t> graph_launches;  // kernels recorded per graph
+  struct GraphRec {
+    uint64_t launches;                        // kernels recorded in the graph
+    uint64_t epoch;                           // tile maps the graph was recorded with
+  };
+  std::unordered_map<void*, GraphRec> graph_launches;
 };
 
 namespace {
 
-void add_tiles(std::vector<BNode>& v, int64_t* total) {
+// The table of one launch site under a configuration: the nodes in the
+// configuration's order, each with its first tile and its staging flag, and
+// the tile -> node map.
+std::vector<BNode> site_table(const std::vector<BNode>& v, const BCfg& cfg, int64_t* total,
+                              std::vector<int>* map) {
+  std::vector<BNode> out(v);
+  if (cfg.order == 1)
+    std::stable_sort(out.begin(), out.end(), [&](const BNode& a, const BNode& c) {
+      return node_tiles(a.R, a.C, cfg) > node_tiles(c.R, c.C, cfg);
+    });
   int64_t t = 0;
-  for (BNode& nd : v) {
+  map->clear();
+  for (size_t i = 0; i < out.size(); ++i) {
+    BNode& nd = out[i];
     nd.tile0 = t;
-    t += node_tiles(nd.R, nd.C);
+    nd.staged = node_staged(nd.C, cfg) ? 1 : 0;
+    const int64_t n = node_tiles(nd.R, nd.C, cfg);
+    map->insert(map->end(), (size_t)n, (int)i);
+    t += n;
   }
   *total = t;
+  return out;
 }
 
-void add_tiles(std::vector<BExp>& v, int64_t* total) {
+inline int64_t exp_tiles(const BExp& e, const BCfg& cfg) {
+  const int64_t tp = (int64_t)kBThreads * cfg.ppt;
+  return (e.R * e.C + tp - 1) / tp;
+}
+
+std::vector<BExp> site_table(const std::vector<BExp>& v, const BCfg& cfg, int64_t* total,
+                             std::vector<int>* map) {
+  std::vector<BExp> out(v);
+  if (cfg.order == 1)
+    std::stable_sort(out.begin(), out.end(), [&](const BExp& a, const BExp& c) {
+      return exp_tiles(a, cfg) > exp_tiles(c, cfg);
+    });
   int64_t t = 0;
-  for (BExp& e : v) {
+  map->clear();
+  for (size_t i = 0; i < out.size(); ++i) {
+    BExp& e = out[i];
     e.tile0 = t;
-    t += (e.R * e.C + kBThreads - 1) / kBThreads;
+    const int64_t n = exp_tiles(e, cfg);
+    map->insert(map->end(), (size_t)n, (int)i);
+    t += n;
   }
   *total = t;
+  return out;
+}
+
+// The most tiles a site can have under any configuration (one position per
+// thread; rows staged up to the largest staging length, or not at all).
+int64_t site_cap(const std::vector<BNode>& v) {
+  int64_t c = 0;
+  for (const BNode& nd : v)
+    c += std::max(node_tiles(nd.R, nd.C, BCfg{1, 64, 0}), node_tiles(nd.R, nd.C, BCfg{1, 0, 0}));
+  return c;
+}
+int64_t site_cap(const std::vector<BExp>& v) {
+  int64_t c = 0;
+  for (const BExp& e : v) c += exp_tiles(e, BCfg{1, 32, 0});
+  return c;
 }
 
 void gram_tiles_for(std::vector<BGram>& v, int64_t z_off, int z_src, int64_t w_off, int64_t R,
@@ -455,16 +634,55 @@ void gram_tiles_for(std::vector<BGram>& v, int64_t z_off, int z_src, int64_t w_o
     }
 }
 
-int launch_bttm(const tucker_batch_s& b, const BNode* d_nodes, int64_t nnodes, int64_t tiles,
+// positions per thread allowed with the batch's largest rank class (4 only
+// up to KB = 8: at KB = 16 its 64 accumulators per position set spill)
+inline bool ppt_allowed(int KB, int ppt) { return ppt == 1 || ppt == 2 || (ppt == 4 && KB <= 8); }
+
+template <int KMAX>
+void bttm_launch(const BCfg& c, unsigned grid, cudaStream_t s, const BNode* d, const int* map,
+                 const float* T, const float* F, float* inter, float* G) {
+  if (c.async) bttm_kernel<KMAX, 1, true><<<grid, kBThreads, 0, s>>>(d, map, T, F, inter, G);
+  else if (c.ppt == 4 && KMAX <= 8)
+    bttm_kernel<KMAX, (KMAX <= 8 ? 4 : 2), false><<<grid, kBThreads, 0, s>>>(d, map, T, F, inter, G);
+  else if (c.ppt == 2) bttm_kernel<KMAX, 2, false><<<grid, kBThreads, 0, s>>>(d, map, T, F, inter, G);
+  else bttm_kernel<KMAX, 1, false><<<grid, kBThreads, 0, s>>>(d, map, T, F, inter, G);
+}
+
+int launch_bttm(const tucker_batch_s& b, const BCfg& cfg, const DevSite<BNode>& site, int64_t tiles,
                 const float* T, const float* F, float* inter, float* G, cudaStream_t s) {
-  if (nnodes == 0 || tiles == 0) return TUCKER_OK;
-  if (tiles > INT32_MAX) return fail(TUCKER_ERR_UNSUPPORTED, "batch: too many tiles");
+  if (tiles == 0) return TUCKER_OK;
+  if (tiles > INT32_MAX || tiles > site.cap) return fail(TUCKER_ERR_UNSUPPORTED, "batch: tile map overflow");
+  if (!ppt_allowed(b.KB, cfg.ppt) || (cfg.async && cfg.ppt != 1))
+    return fail(TUCKER_ERR_INVALID_ARG, "batch: positions per thread");
   switch (b.KB) {
-    case 8: bttm_kernel<8><<<(unsigned)tiles, kBThreads, 0, s>>>(d_nodes, (int)nnodes, T, F, inter, G); break;
-    case 16: bttm_kernel<16><<<(unsigned)tiles, kBThreads, 0, s>>>(d_nodes, (int)nnodes, T, F, inter, G); break;
-    default: bttm_kernel<32><<<(unsigned)tiles, kBThreads, 0, s>>>(d_nodes, (int)nnodes, T, F, inter, G); break;
+    case 8: bttm_launch<8>(cfg, (unsigned)tiles, s, site.items, site.map, T, F, inter, G); break;
+    case 16: bttm_launch<16>(cfg, (unsigned)tiles, s, site.items, site.map, T, F, inter, G); break;
+    default: bttm_launch<32>(cfg, (unsigned)tiles, s, site.items, site.map, T, F, inter, G); break;
   }
   TK_LAUNCH_CHECK("batch_ttm");
+  return TUCKER_OK;
+}
+
+template <int KB>
+void bexpand_launch(int ppt, unsigned grid, cudaStream_t s, const BExp* d, const int* map, const float* T,
+                    const float* F, const float* G, float* inter, double* res2) {
+  if (ppt == 4 && KB <= 8) bexpand_kernel<KB, (KB <= 8 ? 4 : 2)><<<grid, kBThreads, 0, s>>>(d, map, T, F, G, inter, res2);
+  else if (ppt == 2) bexpand_kernel<KB, 2><<<grid, kBThreads, 0, s>>>(d, map, T, F, G, inter, res2);
+  else bexpand_kernel<KB, 1><<<grid, kBThreads, 0, s>>>(d, map, T, F, G, inter, res2);
+}
+
+int launch_bexpand(const tucker_batch_s& b, const BCfg& cfg, const DevSite<BExp>& site, int64_t tiles,
+                   const float* T, const float* F, const float* G, float* inter, double* res2,
+                   cudaStream_t s) {
+  if (tiles == 0) return TUCKER_OK;
+  if (tiles > INT32_MAX || tiles > site.cap) return fail(TUCKER_ERR_UNSUPPORTED, "batch: tile map overflow");
+  if (!ppt_allowed(b.KB, cfg.ppt)) return fail(TUCKER_ERR_INVALID_ARG, "batch: positions per thread");
+  switch (b.KB) {
+    case 8: bexpand_launch<8>(cfg.ppt, (unsigned)tiles, s, site.items, site.map, T, F, G, inter, res2); break;
+    case 16: bexpand_launch<16>(cfg.ppt, (unsigned)tiles, s, site.items, site.map, T, F, G, inter, res2); break;
+    default: bexpand_launch<32>(cfg.ppt, (unsigned)tiles, s, site.items, site.map, T, F, G, inter, res2); break;
+  }
+  TK_LAUNCH_CHECK("batch_fit_expand");
   return TUCKER_OK;
 }
 
@@ -679,6 +897,8 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
   }
   inter = std::max(inter, fit_inter);
   while (!b->levels.empty() && b->levels.back().empty()) b->levels.pop_back();
+  b->lvl_cfg.assign(b->levels.size(), BCfg());
+  b->fit_cfg.assign(b->fit_steps.size(), BCfg());
   b->KB = b->maxK <= 8 ? 8 : (b->maxK <= 16 ? 16 : 32);
   // workspace layout
   size_t off = 0;
@@ -696,12 +916,21 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
   b->off_cold = off;
   off += align_up((size_t)(1 + (size_t)count * N) * sizeof(int));
   b->off_tables = off;
+  // work tables: each TTM / reconstruction site holds its items and a tile
+  // map sized for the configuration with the most tiles
   size_t tb = 0;
-  for (auto& v : b->fit_steps) tb += align_up(v.size() * sizeof(BExp));
-  for (auto& v : b->levels) tb += align_up(v.size() * sizeof(BNode));
-  tb += align_up(b->core_nodes.size() * sizeof(BNode));
+  b->d_levels.assign(b->levels.size(), {});
+  b->d_sth.assign(b->sth_ttm.size(), {});
+  b->d_fit.assign(b->fit_steps.size(), {});
+  auto site_bytes = [&](auto& site, const auto& items) {
+    site.cap = site_cap(items);
+    tb += align_up(items.size() * sizeof(items[0])) + align_up((size_t)site.cap * sizeof(int));
+  };
+  for (size_t st = 0; st < b->fit_steps.size(); ++st) site_bytes(b->d_fit[st], b->fit_steps[st]);
+  for (size_t lv = 0; lv < b->levels.size(); ++lv) site_bytes(b->d_levels[lv], b->levels[lv]);
+  site_bytes(b->d_core, b->core_nodes);
   tb += align_up(b->gram_tiles.size() * sizeof(BGram));
-  for (auto& v : b->sth_ttm) tb += align_up(v.size() * sizeof(BNode));
+  for (size_t n = 0; n < b->sth_ttm.size(); ++n) site_bytes(b->d_sth[n], b->sth_ttm[n]);
   for (auto& v : b->sth_gram) tb += align_up(v.size() * sizeof(BGram));
   tb += align_up(b->eig.size() * sizeof(EigDesc));
   tb += 2 * align_up((size_t)count * sizeof(int64_t));
@@ -747,33 +976,26 @@ int tucker_batch_prepare(tucker_batch_t b, void* ws, size_t ws_bytes, void* stre
     tp += align_up(bytes);
     return dst;
   };
-  b->d_levels.clear();
-  b->level_tiles.clear();
-  for (auto& v : b->levels) {
-    int64_t tiles = 0;
-    add_tiles(v, &tiles);
-    b->level_tiles.push_back(tiles);
-    b->d_levels.push_back(reinterpret_cast<const BNode*>(upload(v.data(), v.size() * sizeof(BNode))));
-  }
-  add_tiles(b->core_nodes, &b->core_tiles);
-  b->d_core = reinterpret_cast<const BNode*>(upload(b->core_nodes.data(), b->core_nodes.size() * sizeof(BNode)));
+  // a site's items, then its tile map in a slot of `cap` ints
+  bool ok = true;
+  auto upload_site = [&](auto& site, const auto& items, const BCfg& cfg) {
+    using Item = typename std::decay_t<decltype(items)>::value_type;
+    std::vector<int> map;
+    const std::vector<Item> t = site_table(items, cfg, &site.tiles, &map);
+    site.items = reinterpret_cast<Item*>(upload(t.data(), t.size() * sizeof(Item)));
+    site.map = reinterpret_cast<int*>(tp);
+    if (!map.empty() && cudaMemcpyAsync(tp, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                        s) != cudaSuccess)
+      ok = false;
+    tp += align_up((size_t)site.cap * sizeof(int));
+    if (!site.items || (int64_t)map.size() > site.cap || cudaStreamSynchronize(s) != cudaSuccess) ok = false;
+  };
+  for (size_t st = 0; st < b->fit_steps.size(); ++st) upload_site(b->d_fit[st], b->fit_steps[st], b->fit_cfg[st]);
+  for (size_t lv = 0; lv < b->levels.size(); ++lv) upload_site(b->d_levels[lv], b->levels[lv], b->lvl_cfg[lv]);
+  upload_site(b->d_core, b->core_nodes, b->core_cfg);
   b->d_gram = reinterpret_cast<const BGram*>(upload(b->gram_tiles.data(), b->gram_tiles.size() * sizeof(BGram)));
-  b->d_sth_ttm.clear();
-  b->sth_tiles.clear();
-  for (auto& v : b->sth_ttm) {
-    int64_t tiles = 0;
-    add_tiles(v, &tiles);
-    b->sth_tiles.push_back(tiles);
-    b->d_sth_ttm.push_back(reinterpret_cast<const BNode*>(upload(v.data(), v.size() * sizeof(BNode))));
-  }
-  b->d_fit.clear();
-  b->fit_tiles.clear();
-  for (auto& v : b->fit_steps) {
-    int64_t tiles = 0;
-    add_tiles(v, &tiles);
-    b->fit_tiles.push_back(tiles);
-    b->d_fit.push_back(reinterpret_cast<const BExp*>(upload(v.data(), v.size() * sizeof(BExp))));
-  }
+  for (size_t n = 0; n < b->sth_ttm.size(); ++n) upload_site(b->d_sth[n], b->sth_ttm[n], BCfg());
+  if (!ok) return fail(TUCKER_ERR_CUDA, "tucker_batch_prepare: table upload failed");
   b->d_sth_gram.clear();
   for (auto& v : b->sth_gram)
     b->d_sth_gram.push_back(reinterpret_cast<const BGram*>(upload(v.data(), v.size() * sizeof(BGram))));
@@ -792,7 +1014,7 @@ int tucker_batch_prepare(tucker_batch_t b, void* ws, size_t ws_bytes, void* stre
   b->d_eig = reinterpret_cast<const EigDesc*>(upload(ed.data(), ed.size() * sizeof(EigDesc)));
   b->d_t_off = reinterpret_cast<const int64_t*>(upload(b->t_off.data(), b->t_off.size() * sizeof(int64_t)));
   b->d_t_size = reinterpret_cast<const int64_t*>(upload(b->t_size.data(), b->t_size.size() * sizeof(int64_t)));
-  if (!b->d_core || !b->d_gram || !b->d_eig || !b->d_t_size)
+  if (!b->d_core.items || !b->d_gram || !b->d_eig || !b->d_t_size)
     return fail(TUCKER_ERR_CUDA, "tucker_batch_prepare: table upload failed");
   TK_CUDA_TRY(cudaStreamSynchronize(s));  // the host tables above go out of scope
   b->prepared_ws = ws;
@@ -810,8 +1032,7 @@ int tucker_batch_sweep(tucker_batch_t b, const float* T, const float* F_in, floa
   float* inter = reinterpret_cast<float*>(base + b->off_inter);
   double* gram = reinterpret_cast<double*>(base + b->off_gram);
   for (size_t lv = 0; lv < b->levels.size(); ++lv) {
-    rc = launch_bttm(*b, b->d_levels[lv], (int64_t)b->levels[lv].size(), b->level_tiles[lv], T,
-                     F_in, inter, nullptr, s);
+    rc = launch_bttm(*b, b->lvl_cfg[lv], b->d_levels[lv], b->d_levels[lv].tiles, T, F_in, inter, nullptr, s);
     if (rc) return rc;
   }
   if (!b->gram_tiles.empty()) {
@@ -819,7 +1040,7 @@ int tucker_batch_sweep(tucker_batch_t b, const float* T, const float* F_in, floa
     TK_LAUNCH_CHECK("batch_gram");
   }
   if (G_in) {
-    rc = launch_bttm(*b, b->d_core, (int64_t)b->core_nodes.size(), b->core_tiles, T, F_in, inter, G_in, s);
+    rc = launch_bttm(*b, b->core_cfg, b->d_core, b->d_core.tiles, T, F_in, inter, G_in, s);
     if (rc) return rc;
   }
   return launch_eig_batched(b->d_eig, b->count * b->N, b->maxL, b->maxK, TUCKER_F32,
@@ -844,8 +1065,7 @@ int tucker_batch_sthosvd(tucker_batch_t b, const float* T, float* F, float* G, v
                             reinterpret_cast<char*>(F), nullptr,
                             reinterpret_cast<int*>(base + b->off_cold), s);
     if (rc) return rc;
-    rc = launch_bttm(*b, b->d_sth_ttm[(size_t)n], (int64_t)b->sth_ttm[(size_t)n].size(),
-                     b->sth_tiles[(size_t)n], T, F, inter, G, s);
+    rc = launch_bttm(*b, BCfg(), b->d_sth[(size_t)n], b->d_sth[(size_t)n].tiles, T, F, inter, G, s);
     if (rc) return rc;
   }
   return TUCKER_OK;
@@ -874,15 +1094,8 @@ int tucker_batch_fit(tucker_batch_t b, const float* T, const float* F, const flo
   double* res2 = reinterpret_cast<double*>(base + b->off_res);
   TK_CUDA_TRY(cudaMemsetAsync(res2, 0, sizeof(double) * (size_t)b->count, s));
   for (size_t st = 0; st < b->fit_steps.size(); ++st) {
-    const int64_t tiles = b->fit_tiles[st];
-    const int n = (int)b->fit_steps[st].size();
-    if (tiles > INT32_MAX) return fail(TUCKER_ERR_UNSUPPORTED, "batch: too many tiles");
-    switch (b->KB) {
-      case 8: bexpand_kernel<8><<<(unsigned)tiles, kBThreads, 0, s>>>(b->d_fit[st], n, T, F, G, inter, res2); break;
-      case 16: bexpand_kernel<16><<<(unsigned)tiles, kBThreads, 0, s>>>(b->d_fit[st], n, T, F, G, inter, res2); break;
-      default: bexpand_kernel<32><<<(unsigned)tiles, kBThreads, 0, s>>>(b->d_fit[st], n, T, F, G, inter, res2); break;
-    }
-    TK_LAUNCH_CHECK("batch_fit_expand");
+    rc = launch_bexpand(*b, b->fit_cfg[st], b->d_fit[st], b->d_fit[st].tiles, T, F, G, inter, res2, s);
+    if (rc) return rc;
   }
   bfit_finish_kernel<<<(b->count + 255) / 256, 256, 0, s>>>(b->count, res2, normT2, fit);
   TK_LAUNCH_CHECK("batch_fit_finish");
@@ -921,22 +1134,199 @@ int tucker_batch_graph_create(tucker_batch_t b, const float* T, const float* F_i
   // count them at every replay instead
   const uint64_t recorded = tucker_launch_count() - launches0;
   count_launches((uint64_t)0 - recorded);
-  b->graph_launches[ex] = recorded;
+  b->graph_launches[ex] = tucker_batch_s::GraphRec{recorded, b->epoch};
   *graph_exec = ex;
   return TUCKER_OK;
 }
 
 int tucker_batch_graph_launch(tucker_batch_t b, void* graph_exec, void* stream) {
   if (!b || !graph_exec) return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_graph_launch: NULL argument");
+  const auto it = b->graph_launches.find(graph_exec);
+  if (it == b->graph_launches.end())
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_graph_launch: graph not created from this batch");
+  if (it->second.epoch != b->epoch)
+    return fail(TUCKER_ERR_INVALID_ARG,
+                "tucker_batch_graph_launch: graph recorded before tucker_batch_autotune changed the tile "
+                "maps; create it again");
   TK_CUDA_TRY(cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec),
                               static_cast<cudaStream_t>(stream)));
-  const auto it = b->graph_launches.find(graph_exec);
-  if (it != b->graph_launches.end()) count_launches(it->second);
+  count_launches(it->second.launches);
   return TUCKER_OK;
 }
 
 void tucker_batch_graph_destroy(void* graph_exec) {
   if (graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph_exec));
+}
+
+int tucker_batch_autotune(tucker_batch_t b, const float* T, const float* F, float* G, void* ws,
+                          size_t ws_bytes, int reps, void* stream) {
+  if (!b || !T || !F || !G) return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_autotune: NULL argument");
+  if (reps < 1 || reps > 1000) return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_autotune: reps in 1..1000");
+  int rc = check_batch_ws(b, ws, ws_bytes, "tucker_batch_autotune");
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  float* inter = reinterpret_cast<float*>(base + b->off_inter);
+  double* res2 = reinterpret_cast<double*>(base + b->off_res);
+  cudaEvent_t e0, e1;
+  TK_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(TUCKER_ERR_CUDA, "tucker_batch_autotune: cudaEventCreate");
+  }
+  // candidates: the default first; another replaces the best only when at
+  // least 2 % faster, so that timing noise does not pick a variant
+  std::vector<BCfg> ttm_cands, exp_cands;
+  const int ppts[3] = {1, 2, 4};
+  const int stages[4] = {32, 0, 16, 64};  // staged rows need C <= 256
+  for (int o = 0; o < 2; ++o) {
+    for (int ppt : ppts) {
+      if (!ppt_allowed(b->KB, ppt)) continue;
+      for (int sc : stages) ttm_cands.push_back(BCfg{ppt, sc, o, 0});
+      exp_cands.push_back(BCfg{ppt, 32, o, 0});
+    }
+    for (int sc : stages) ttm_cands.push_back(BCfg{1, sc, o, 1});
+  }
+  b->tune_ms_default.clear();
+  b->tune_ms_best.clear();
+  // time one site: upload each candidate's table to the site's slot, launch
+  // once untimed, then `reps` times between events; keep the fastest
+  auto tune_site = [&](const auto& items, auto& site, BCfg* cfg, const std::vector<BCfg>& cands,
+                       auto&& launch) -> int {
+    using Item = typename std::decay_t<decltype(items)>::value_type;
+    // upload a candidate's table and tile map into the site's slots
+    auto put = [&](const BCfg& c, int64_t* tiles) -> int {
+      std::vector<int> map;
+      const std::vector<Item> t = site_table(items, c, tiles, &map);
+      if ((int64_t)map.size() > site.cap) return fail(TUCKER_ERR_UNSUPPORTED, "batch: tile map overflow");
+      TK_CUDA_TRY(cudaMemcpyAsync(site.items, t.data(), t.size() * sizeof(Item), cudaMemcpyHostToDevice, s));
+      if (!map.empty())
+        TK_CUDA_TRY(cudaMemcpyAsync(site.map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      TK_CUDA_TRY(cudaStreamSynchronize(s));  // t and map go out of scope
+      return TUCKER_OK;
+    };
+    float best_ms = 0.f, def_ms = 0.f;
+    BCfg best = cands[0];
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+      int64_t tiles = 0;
+      int r = put(cands[ci], &tiles);
+      if (r) return r;
+      r = launch(cands[ci], tiles);
+      if (r) return r;
+      TK_CUDA_TRY(cudaEventRecord(e0, s));
+      for (int i = 0; i < reps && !r; ++i) r = launch(cands[ci], tiles);
+      if (r) return r;
+      TK_CUDA_TRY(cudaEventRecord(e1, s));
+      TK_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      TK_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= (float)reps;
+      if (ci == 0) {
+        def_ms = best_ms = ms;
+      } else if (ms < 0.98f * best_ms) {
+        best_ms = ms;
+        best = cands[ci];
+      }
+    }
+    const int r = put(best, &site.tiles);
+    if (r) return r;
+    *cfg = best;
+    b->tune_ms_default.push_back(def_ms);
+    b->tune_ms_best.push_back(best_ms);
+    return TUCKER_OK;
+  };
+  // tree levels in order (each reads the previous level's outputs), then the
+  // core step (reads the tree's intermediates), then the reconstruction steps
+  // of the fit (which reuse the intermediate region)
+  for (size_t lv = 0; lv < b->levels.size() && !rc; ++lv) {
+    const DevSite<BNode>& site = b->d_levels[lv];
+    rc = tune_site(b->levels[lv], b->d_levels[lv], &b->lvl_cfg[lv], ttm_cands,
+                   [&](const BCfg& c, int64_t tiles) {
+                     return launch_bttm(*b, c, site, tiles, T, F, inter, nullptr, s);
+                   });
+  }
+  if (!rc)
+    rc = tune_site(b->core_nodes, b->d_core, &b->core_cfg, ttm_cands, [&](const BCfg& c, int64_t tiles) {
+      return launch_bttm(*b, c, b->d_core, tiles, T, F, inter, G, s);
+    });
+  for (size_t st = 0; st < b->fit_steps.size() && !rc; ++st) {
+    const DevSite<BExp>& site = b->d_fit[st];
+    rc = tune_site(b->fit_steps[st], b->d_fit[st], &b->fit_cfg[st], exp_cands,
+                   [&](const BCfg& c, int64_t tiles) {
+                     return launch_bexpand(*b, c, site, tiles, T, F, G, inter, res2, s);
+                   });
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ++b->epoch;  // graphs recorded before now hold the old tile counts
+  return rc;
+}
+
+int tucker_batch_set_tuning(tucker_batch_t b, int n_sites, const int* cfg) {
+  if (!b || !cfg) return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_set_tuning: NULL argument");
+  const int want = (int)b->levels.size() + 1 + (int)b->fit_steps.size();
+  if (n_sites != want)
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_set_tuning: expected " + std::to_string(want) + " sites");
+  std::vector<BCfg> lv(b->levels.size()), ft(b->fit_steps.size());
+  BCfg core;
+  for (int i = 0; i < n_sites; ++i) {
+    const int* c = cfg + 6 * i;
+    const int kind = i < (int)lv.size() ? 0 : (i == (int)lv.size() ? 1 : 2);
+    const int index = kind == 0 ? i : (kind == 1 ? 0 : i - (int)lv.size() - 1);
+    if (c[0] != kind || c[1] != index)
+      return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_set_tuning: site " + std::to_string(i) +
+                                              " out of order (as tucker_batch_tuning lists them)");
+    if (!ppt_allowed(b->KB, c[2]) || c[3] < 0 || c[3] > 64 || (c[4] != 0 && c[4] != 1) ||
+        (c[5] != 0 && c[5] != 1) || (c[5] == 1 && (kind == 2 || c[2] != 1)))
+      return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_set_tuning: site " + std::to_string(i) +
+                                              ": configuration out of range");
+    const BCfg v{c[2], kind == 2 ? 32 : c[3], c[4], c[5]};
+    if (kind == 0) lv[(size_t)index] = v;
+    else if (kind == 1) core = v;
+    else ft[(size_t)index] = v;
+  }
+  b->lvl_cfg = lv;
+  b->core_cfg = core;
+  b->fit_cfg = ft;
+  b->tune_ms_default.clear();
+  b->tune_ms_best.clear();
+  b->prepared_ws = nullptr;  // the tables must be uploaded again
+  ++b->epoch;
+  return TUCKER_OK;
+}
+
+int tucker_batch_tuning(tucker_batch_t b, int cap, int* n_sites, int* cfg, float* ms) {
+  if (!b || !n_sites) return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_tuning: NULL argument");
+  std::vector<std::pair<int, int>> sites;  // (kind, index)
+  std::vector<BCfg> cfgs;
+  for (size_t lv = 0; lv < b->levels.size(); ++lv) {
+    sites.push_back({0, (int)lv});
+    cfgs.push_back(b->lvl_cfg[lv]);
+  }
+  sites.push_back({1, 0});
+  cfgs.push_back(b->core_cfg);
+  for (size_t st = 0; st < b->fit_steps.size(); ++st) {
+    sites.push_back({2, (int)st});
+    cfgs.push_back(b->fit_cfg[st]);
+  }
+  *n_sites = (int)sites.size();
+  const bool timed = b->tune_ms_best.size() == sites.size();
+  for (int i = 0; i < std::min(cap, (int)sites.size()); ++i) {
+    if (cfg) {
+      int* c = cfg + 6 * i;
+      c[0] = sites[(size_t)i].first;
+      c[1] = sites[(size_t)i].second;
+      c[2] = cfgs[(size_t)i].ppt;
+      c[3] = cfgs[(size_t)i].stage_c;
+      c[4] = cfgs[(size_t)i].order;
+      c[5] = cfgs[(size_t)i].async;
+    }
+    if (ms) {
+      ms[2 * i] = timed ? b->tune_ms_default[(size_t)i] : -1.f;
+      ms[2 * i + 1] = timed ? b->tune_ms_best[(size_t)i] : -1.f;
+    }
+  }
+  return TUCKER_OK;
 }
 
 }  // extern "C"

@@ -170,6 +170,61 @@ def test_batch_plan_layout(tk):
     assert b.ws_bytes > 4 * b.t_elems // 10
 
 
+def test_batch_tuning_defaults_before_autotune(tk):
+    """Before tucker_batch_autotune every sweep site holds the default launch
+    configuration (one position per thread, rows shorter than 32 staged, plan
+    order) and no timings; the sites are the tree levels, the core step and
+    the N reconstruction steps of the fit (host only)."""
+    import workloads
+    dims, ranks = workloads.batch_shapes(19, 4)
+    b = tk.BatchPlan(dims, ranks)
+    sites = tk.tucker_batch_tuning(b)
+    kinds = [s["site"] for s in sites]
+    assert kinds.count("core") == 1 and kinds.count("fit") == 3
+    assert kinds == ["level"] * kinds.count("level") + ["core"] + ["fit"] * 3
+    assert 1 <= kinds.count("level") <= 2  # 3-way trees: depth 2 at most below the root
+    for s in sites:
+        assert (s["ppt"], s["stage_c"], s["order"], s["async"]) == (1, 32, 0, 0)
+        assert s["ms_default"] == -1.0 and s["ms_tuned"] == -1.0
+
+
+def test_batch_set_tuning_round_trip_and_validation(tk):
+    """Configurations set through tucker_batch_set_tuning read back the same;
+    out-of-order sites and out-of-range values are refused (host only)."""
+    import copy
+
+    import workloads
+    dims, ranks = workloads.batch_shapes(11, 5)
+    b = tk.BatchPlan(dims, ranks)
+    sites = tk.tucker_batch_tuning(b)
+    new = copy.deepcopy(sites)
+    for i, s in enumerate(new):
+        s["ppt"] = 2
+        s["order"] = i % 2
+        if s["site"] != "fit":
+            s["stage_c"] = (0, 16, 64)[i % 3]
+            if i % 2:
+                s["ppt"], s["async"] = 1, 1
+    tk.tucker_batch_set_tuning(b, new)
+    got = tk.tucker_batch_tuning(b)
+    for s, g in zip(new, got):
+        assert (g["ppt"], g["order"], g["async"]) == (s["ppt"], s["order"], s["async"])
+        assert g["stage_c"] == (s["stage_c"] if s["site"] != "fit" else 32)
+    for bad in ({"ppt": 3}, {"ppt": 4}, {"stage_c": 65}, {"order": 2}, {"index": 7},
+                {"async": 2}, {"async": 1, "ppt": 2}):
+        wrong = copy.deepcopy(sites)
+        wrong[0].update(bad)
+        with pytest.raises(tk.TuckerError) as e:
+            tk.tucker_batch_set_tuning(b, wrong)
+        assert e.value.code == -1
+    with pytest.raises(tk.TuckerError):
+        tk.tucker_batch_set_tuning(b, sites[:-1])
+    fit = copy.deepcopy(sites)
+    fit[-1]["async"] = 1  # reconstruction steps have no cp.async variant
+    with pytest.raises(tk.TuckerError):
+        tk.tucker_batch_set_tuning(b, fit)
+
+
 @pytest.mark.parametrize("dims,ranks,msg", [
     ([(20, 20, 201)], [(4, 4, 4)], "L_n <= 200"),
     ([(40, 40, 40)], [(33, 33, 33)], "K_n <= 32"),
