@@ -47,6 +47,8 @@ def parse():
                     help="skip the BF16-vs-FP32 comparison on the 64^5 workload")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched form (4096 small tensors) against per-tensor calls")
+    ap.add_argument("--precision-only", default=None, choices=["precision5", "uneven6"],
+                    help="run only one precision form (kernel studies)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched form (kernel studies and ncu captures)")
     ap.add_argument("--batch-count", type=int, default=None,
@@ -796,6 +798,13 @@ def main():
         return 0
     if args.batch_only:
         print(json.dumps({"batched_form": run_batch_form(args)}), flush=True)
+        return 0
+    if args.precision_only:
+        import paper_1707_05594_gb300 as tk
+        from paper_1707_05594_gb300 import build as tkbuild
+        tkbuild.build()
+        tk.lib().tucker_set_kernel_policy(args.kernel_policy)
+        print(json.dumps({args.precision_only: run_precision_form(args, args.precision_only)}), flush=True)
         return 0
     out = run_ours(args, ws_size, rank)
     if rank == 0:

@@ -254,8 +254,12 @@ int tucker_convert_fp8(const float* x, void* out, int64_t n, void* stream);
  *              six products accumulated in TMEM (off by default: the
  *              accumulation is not the CUDA cores' exactly rounded FMA, which
  *              moves the fit identity ||T||^2 - ||G||^2 by ~1e-5 relative on
- *              low-noise tensors).
- * Used to compare the paths. */
+ *              low-noise tensors);
+ *   bit 3 (8): no short-row kernels (otherwise FP32 and BF16 TTMs with short
+ *              rows after mode n -- C == 1 with 256 rows in 32 KB, or
+ *              1 < C < 64 -- and no tensor-core tile copy runs of whole slabs
+ *              into shared memory by cp.async and multiply from there).
+ * Used to compare the paths.  TUCKER_ERR_INVALID_ARG outside 0..15. */
 int tucker_set_kernel_policy(int policy);
 
 /* Device error word of the tensor-core kernels: 0, or TUCKER_ERR_TIMEOUT if a

@@ -288,6 +288,14 @@ bool ttm_tc_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X,
                       const void* X_lo);
 int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t C,
                   const float* F, int64_t K, void* Y, bool y_bf16, cudaStream_t s);
+// Short-row TTMs (ttm_slab.cu): C == 1 with 256 * L elements in 32 KB, or
+// 1 < C < 64 with a slab of L * C elements in 8 KB; FP32 or BF16 input, F
+// FP32, K <= 32; Y FP32 (or BF16 for BF16 input).
+bool ttm_slab_supported(int x_dtype, int64_t R, int64_t L, int64_t C, int64_t K);
+// the shapes launch_ttm sends to the short-row kernels (measured faster there)
+bool ttm_slab_preferred(int x_dtype, int64_t R, int64_t L, int64_t C, int64_t K);
+int launch_ttm_slab(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, const float* F,
+                    int64_t K, void* Y, int y_dtype, cudaStream_t s);
 // FP8 E4M3 tensors with per-64 scales (fp8.cu): Y = X x_n F^T with Y FP32 or
 // BF16, and ||X||^2; X is the whole tensor (R * L * C elements) in the layout
 // of tucker_fp8_bytes.

@@ -440,6 +440,8 @@ int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, cons
       if ((kernel_policy() & 5) == 4 && ttm_tc_f32_supported(R, L, C, K, X))
         return launch_ttm_tc_f32(static_cast<const float*>(X), R, L, C, static_cast<const float*>(F), K,
                                  static_cast<float*>(Y), s);
+      if ((kernel_policy() & 8) == 0 && ttm_slab_preferred(TUCKER_F32, R, L, C, K))
+        return launch_ttm_slab(TUCKER_F32, X, R, L, C, static_cast<const float*>(F), K, Y, y_dtype, s);
       return launch_typed<float, float>(X, R, L, C, F, K, Y, s);
     case TUCKER_F64:
       if (y_dtype != TUCKER_F64) return fail(TUCKER_ERR_UNSUPPORTED, "ttm: FP64 input needs FP64 output");
@@ -453,6 +455,9 @@ int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, cons
       if ((kernel_policy() & 1) == 0 && !(C == 1 && L <= kStagedMaxL) &&
           ttm_tc_supported(R, L, C, K, X, nullptr))
         return launch_ttm_tc(X, nullptr, R, L, C, static_cast<const float*>(F), K, Y, ybf, s);
+      // short rows (no tensor-core tile): runs of whole slabs through shared memory
+      if ((kernel_policy() & 8) == 0 && ttm_slab_preferred(TUCKER_BF16, R, L, C, K))
+        return launch_ttm_slab(TUCKER_BF16, X, R, L, C, static_cast<const float*>(F), K, Y, y_dtype, s);
       return ybf ? launch_typed<bf16_t, bf16_t>(X, R, L, C, F, K, Y, s)
                  : launch_typed<bf16_t, float>(X, R, L, C, F, K, Y, s);
     }

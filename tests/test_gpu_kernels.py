@@ -71,6 +71,47 @@ def test_ttm_matches_oracle(tk, orc, shape, n, K, dtype):
     assert np.all(err <= (shape[n] + 2) * u * bound + 1e-300), err.max()
 
 
+SLAB_CASES = [
+    # C == 1 rows: L a multiple of 8 (vector reads for both types), of 4 only
+    # (vector FP32, scalar BF16), odd L; R ragged against the 256-row block;
+    # K over every rank class (2 .. 32)
+    ((300, 24), 1, 6), ((1000, 24), 1, 8), ((257, 20), 1, 5), ((513, 7), 1, 3), ((64, 3, 32), 2, 32),
+    ((91, 17), 1, 1), ((40, 33), 1, 13), ((5, 7, 9, 63), 3, 17), ((2, 300, 16), 2, 24),
+    # 1 < C < 64: slabs of L x C per block, positions 256 apart
+    ((77, 32, 24), 1, 8), ((50, 40, 2), 1, 4), ((33, 9, 63), 1, 16), ((5, 17, 3), 1, 2),
+    ((64, 56, 48, 40, 3), 3, 10), ((129, 31, 5), 1, 32), ((7, 24, 33), 1, 20),
+]
+
+
+@pytest.mark.parametrize("shape,n,K", SLAB_CASES)
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_ttm_short_rows_match_oracle(tk, orc, shape, n, K, dtype, offset):
+    """Short rows after mode n (C < 64): runs of whole slabs staged in shared
+    memory by 16-byte cp.async (offset 0), or by element copies when the
+    tensor does not start on a 16-byte boundary (offset 1: the tensor is a
+    view one element into a larger buffer).  FP32 FMA accumulation of exact
+    inputs: bound (L + 2) 2^-24 sum |x f|, as for the other CUDA-core TTMs."""
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    X = workloads.random_tensor(shape, seed=sum(shape) * 7 + n, dtype=tdt)
+    m = X.numel()
+    buf = torch.zeros(m + 8, dtype=tdt, device="cuda")
+    buf[offset:offset + m] = X.reshape(-1).cuda()
+    Xg = buf[offset:offset + m].view(shape)
+    F = workloads.random_factor(shape[n], K, seed=K + 11, dtype=torch.float32, orthonormal=False)
+    out_shape = list(shape)
+    out_shape[n] = K
+    Y = torch.full(out_shape, float("nan"), dtype=torch.float32, device="cuda")
+    tk.tucker_ttm(Xg, n, F.cuda(), Y)
+    torch.cuda.synchronize()
+    Xd = X.double().numpy()
+    Fd = F.double().numpy()
+    ref = orc.ttm(Xd, n, Fd.T)
+    bound = orc.ttm(np.abs(Xd), n, np.abs(Fd).T)
+    err = np.abs(Y.double().cpu().numpy() - ref)
+    assert np.all(err <= (shape[n] + 2) * U32 * bound + 1e-300), (err / (bound + 1e-300)).max()
+
+
 TC_CASES = [
     # column case (mode not last; C % 8 == 0, C >= 64): ragged tiles, l chunks
     ((5, 200, 136), 1, 20), ((3, 37, 64), 1, 5), ((2, 64, 1000), 1, 16), ((130, 72), 0, 1),
