@@ -73,8 +73,18 @@ typedef struct {
   int32_t dtype;      /* tucker_dtype_t, storage type of T               */
   int32_t tree;       /* tucker_tree_t                                   */
   int32_t cost_model; /* tucker_cost_t (only for TUCKER_TREE_OPTIMAL)    */
-  int32_t reserved;   /* must be 0                                       */
+  int32_t flags;      /* TUCKER_PLAN_* bits, 0 by default                */
 } tucker_plan_opts_t;
+
+/* Plan flag: never fuse the root.  By default, when the first two root
+ * children of the tree (modes a < b) are both TTM nodes, T is FP32 or BF16,
+ * the trailing block of T from mode a on (L_a * ... * L_{N-1} elements) fits
+ * in 8 KB and K_a, K_b <= 32, a sweep computes both children from one read of
+ * T (one kernel that stages each block in shared memory and contracts it
+ * along a and along b); the second child's buffer then sits after the first
+ * child's subtree (see ws_offset), which can enlarge the workspace.
+ * Results are those of the two separate TTMs (same order of summation). */
+#define TUCKER_PLAN_NO_FUSED_ROOT 1
 
 typedef struct tucker_plan_s* tucker_plan_t;
 
@@ -112,6 +122,11 @@ int tucker_plan_cost(tucker_plan_t plan, uint64_t* tree_macs, uint64_t* tree_ele
 /* Copies at most `capacity` nodes of the plan's tree (see tucker_node_t) and
  * sets *n_nodes to the total count.  nodes may be NULL to query the count. */
 int tucker_plan_nodes(tucker_plan_t plan, tucker_node_t* nodes, int capacity, int* n_nodes);
+
+/* The fused root of a plan: *first and *second = the node indices of the two
+ * root children computed together (first in depth-first order), or -1 and -1
+ * when the root is not fused.  Host only. */
+int tucker_plan_fused_root(tucker_plan_t plan, int* first, int* second);
 
 void tucker_plan_destroy(tucker_plan_t plan);
 
@@ -168,6 +183,19 @@ int tucker_fit(tucker_plan_t plan, const void* G, const double* normT2, double* 
  * TUCKER_F64, else float.  Exposed for testing the TTM kernels. */
 int tucker_ttm(int N, const int64_t* dims, const void* X, int x_dtype, int n, const void* F,
                int64_t K, void* Y, void* stream);
+
+/* Two TTMs of one tensor from a single read of it (the fused root of a
+ * sweep): Ya = X x_a Fa^T and Yb = X x_b Fb^T for modes a < b, with Fa
+ * dims[a] x Ka and Fb dims[b] x Kb row-major float, Ya and Yb laid out as
+ * X with dims[a] (dims[b]) replaced by Ka (Kb).  x_dtype TUCKER_F32 (y_dtype
+ * TUCKER_F32) or TUCKER_BF16 (y_dtype TUCKER_BF16 or TUCKER_F32).  Each
+ * output is summed over its contracted mode in increasing order with FP32
+ * fused multiply-adds.  TUCKER_ERR_UNSUPPORTED unless the trailing block
+ * dims[a] * ... * dims[N-1] fits in 8 KB, Ka, Kb <= 32 and the factors fit in
+ * shared memory (the conditions of the plan's fused root). */
+int tucker_ttm_pair(int N, const int64_t* dims, const void* X, int x_dtype, int a, const float* Fa,
+                    int64_t Ka, int b, const float* Fb, int64_t Kb, void* Ya, void* Yb, int y_dtype,
+                    void* stream);
 
 /* Gram W = Z_(n) Z_(n)^T (Sec. 5) of a tensor Z of lengths dims[0..N-1] and
  * type z_dtype; W is a dims[n] x dims[n] device double matrix (overwritten). */
@@ -258,8 +286,12 @@ int tucker_convert_fp8(const float* x, void* out, int64_t n, void* stream);
  *   bit 3 (8): no short-row kernels (otherwise FP32 and BF16 TTMs with short
  *              rows after mode n -- C == 1 with 256 rows in 32 KB, or
  *              1 < C < 64 -- and no tensor-core tile copy runs of whole slabs
- *              into shared memory by cp.async and multiply from there).
- * Used to compare the paths.  TUCKER_ERR_INVALID_ARG outside 0..15. */
+ *              into shared memory by cp.async and multiply from there);
+ *   bit 4 (16): BF16 TTMs on the tensor cores wherever the shape allows
+ *              (otherwise column shapes whose tensor-core tiles would be less
+ *              than 60 % useful -- l in stages of 64, 128 positions per tile
+ *              -- run on the CUDA cores, which are faster there).
+ * Used to compare the paths.  TUCKER_ERR_INVALID_ARG outside 0..31. */
 int tucker_set_kernel_policy(int policy);
 
 /* Device error word of the tensor-core kernels: 0, or TUCKER_ERR_TIMEOUT if a

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libtucker_gb300.so")
 TUCKER_F32, TUCKER_F64, TUCKER_BF16, TUCKER_FP8_E4M3 = 0, 1, 2, 3
 TREE_OPTIMAL, TREE_CHAIN, TREE_CHAIN_K, TREE_CHAIN_H, TREE_BALANCED = 0, 1, 2, 3, 4
 COST_MACS, COST_ELEMS = 0, 1
+PLAN_NO_FUSED_ROOT = 1
 ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "WORKSPACE", -4: "CUDA", -5: "TIMEOUT",
           -6: "NONFINITE"}
 
@@ -39,7 +40,7 @@ class TuckerError(RuntimeError):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("tree", ctypes.c_int32),
-                ("cost_model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cost_model", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class Node(ctypes.Structure):
@@ -64,6 +65,8 @@ def lib():
                               ctypes.POINTER(ctypes.c_void_p)]
     L.tucker_plan_cost.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p,
                                    ctypes.POINTER(ctypes.c_size_t)]
+    L.tucker_plan_fused_root.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]
     L.tucker_plan_nodes.argtypes = [ctypes.c_void_p, ctypes.POINTER(Node), ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int)]
     L.tucker_plan_destroy.argtypes = [ctypes.c_void_p]
@@ -82,6 +85,10 @@ def lib():
                              ctypes.c_void_p]
     L.tucker_ttm.argtypes = [ctypes.c_int, _i64p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                              ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    L.tucker_ttm_pair.argtypes = [ctypes.c_int, _i64p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                  ctypes.c_void_p]
     L.tucker_gram.argtypes = [ctypes.c_int, _i64p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                               ctypes.c_void_p, ctypes.c_void_p]
     L.tucker_eig_topk.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
@@ -206,12 +213,21 @@ class Plan:
 
 
 def tucker_plan(L: Sequence[int], K: Sequence[int], dtype: int = TUCKER_F32,
-                tree: int = TREE_OPTIMAL, cost_model: int = COST_MACS) -> Plan:
+                tree: int = TREE_OPTIMAL, cost_model: int = COST_MACS,
+                fuse_root: bool = True) -> Plan:
     h = ctypes.c_void_p()
-    opts = PlanOpts(dtype, tree, cost_model, 0)
+    opts = PlanOpts(dtype, tree, cost_model, 0 if fuse_root else PLAN_NO_FUSED_ROOT)
     _check(lib().tucker_plan(len(L), _i64(L), _i64(K), ctypes.byref(opts), ctypes.byref(h)),
            "tucker_plan")
     return Plan(h, tuple(int(x) for x in L), tuple(int(x) for x in K), dtype, tree)
+
+
+def tucker_plan_fused_root(plan: Plan):
+    """(first, second) node indices of the fused root children, or None."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().tucker_plan_fused_root(plan.handle, ctypes.byref(a), ctypes.byref(b)),
+           "tucker_plan_fused_root")
+    return None if a.value < 0 else (a.value, b.value)
 
 
 def tucker_plan_cost(plan: Plan):
@@ -286,6 +302,16 @@ def tucker_ttm(X, n: int, F, Y, stream=None):
     _check(lib().tucker_ttm(X.dim(), _i64(X.shape), _dp(X, "X"),
                             _dtype_code(X), n, _dp(F, "F"), F.shape[1],
                             _dp(Y, "Y"), _stream(stream)), "tucker_ttm")
+
+
+def tucker_ttm_pair(X, a: int, Fa, Ya, b: int, Fb, Yb, stream=None):
+    """Ya = X x_a Fa^T and Yb = X x_b Fb^T (a < b) from one read of X (the
+    fused root kernel); Ya / Yb FP32, or BF16 for a BF16 X."""
+    _req(X, "X")
+    _check(lib().tucker_ttm_pair(X.dim(), _i64(X.shape), _dp(X, "X"), _dtype_code(X), a,
+                                 _dp(Fa, "Fa"), Fa.shape[1], b, _dp(Fb, "Fb"), Fb.shape[1],
+                                 _dp(Ya, "Ya"), _dp(Yb, "Yb"), _dtype_code(Ya), _stream(stream)),
+           "tucker_ttm_pair")
 
 
 def tucker_gram(Z, n: int, W, stream=None):

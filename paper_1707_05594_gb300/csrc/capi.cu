@@ -11,6 +11,8 @@
 
 #include "nvtx3/nvToolsExt.h"
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tk {
@@ -102,6 +104,24 @@ int tucker_ttm(int N, const int64_t* dims, const void* X, int x_dtype, int n, co
                     static_cast<cudaStream_t>(stream));
 }
 
+int tucker_ttm_pair(int N, const int64_t* dims, const void* X, int x_dtype, int a, const float* Fa,
+                    int64_t Ka, int b, const float* Fb, int64_t Kb, void* Ya, void* Yb, int y_dtype,
+                    void* stream) {
+  if (N < 2 || N > kMaxModes || !dims || !X || !Fa || !Fb || !Ya || !Yb || a < 0 || b <= a || b >= N ||
+      Ka < 1 || Kb < 1 || Ka > dims[a] || Kb > dims[b])
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_ttm_pair: invalid argument");
+  for (int i = 0; i < N; ++i)
+    if (dims[i] < 1) return fail(TUCKER_ERR_INVALID_ARG, "tucker_ttm_pair: lengths must be >= 1");
+  int64_t K[kMaxModes] = {};
+  for (int i = 0; i < N; ++i) K[i] = 1;
+  K[a] = Ka;
+  K[b] = Kb;
+  if (!fused_root_fits(x_dtype, N, dims, K, a, b))
+    return fail(TUCKER_ERR_UNSUPPORTED, "tucker_ttm_pair: shape or type not supported");
+  return launch_ttm_fused_root(x_dtype, X, dims, N, a, b, Fa, Ka, Fb, Kb, Ya, Yb, y_dtype,
+                               static_cast<cudaStream_t>(stream));
+}
+
 int tucker_gram(int N, const int64_t* dims, const void* Z, int z_dtype, int n, double* W,
                 void* stream) {
   if (N < 1 || N > kMaxModes || !dims || n < 0 || n >= N || !Z || !W)
@@ -170,7 +190,19 @@ int tucker_hooi_sweep_core(tucker_plan_t plan, const void* T, const void* const*
     const void* in = from_root ? T : (const void*)(wsb + p.off_scratch + par.ws_off);
     const int in_dt = from_root ? p.dtype : idt;
     ProfScope prof(plan->p, s, (int)i, nd.label);
-    if (nd.label >= 0) {
+    if (nd.label >= 0 && (int)i == p.fused_u2) {
+      // written together with the first root child
+    } else if (nd.label >= 0 && (int)i == p.fused_u1) {
+      // fused root: both root children from one read of T
+      const PlanNode& n2 = p.nodes[(size_t)p.fused_u2];
+      const int a = std::min(nd.label, n2.label), b = std::max(nd.label, n2.label);
+      void* y1 = wsb + p.off_scratch + nd.ws_off;
+      void* y2 = wsb + p.off_scratch + n2.ws_off;
+      rc = launch_ttm_fused_root(p.dtype, T, p.L, p.N, a, b, static_cast<const float*>(F_in[a]), p.K[a],
+                                 static_cast<const float*>(F_in[b]), p.K[b], nd.label == a ? y1 : y2,
+                                 nd.label == a ? y2 : y1, idt, s);
+      if (rc) return rc;
+    } else if (nd.label >= 0) {
       int64_t R, L, C;
       view3(par.out_dims, p.N, nd.label, &R, &L, &C);
       rc = launch_ttm(in_dt, in, R, L, C, F_in[nd.label], p.K[nd.label],

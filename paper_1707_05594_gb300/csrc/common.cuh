@@ -288,6 +288,8 @@ bool ttm_tc_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X,
                       const void* X_lo);
 int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t C,
                   const float* F, int64_t K, void* Y, bool y_bf16, cudaStream_t s);
+// useful share of the tensor-core tiles for a shape (l stages of 64, 128-position tiles)
+double ttm_tc_efficiency(int64_t L, int64_t C);
 // Short-row TTMs (ttm_slab.cu): C == 1 with 256 * L elements in 32 KB, or
 // 1 < C < 64 with a slab of L * C elements in 8 KB; FP32 or BF16 input, F
 // FP32, K <= 32; Y FP32 (or BF16 for BF16 input).
@@ -296,6 +298,12 @@ bool ttm_slab_supported(int x_dtype, int64_t R, int64_t L, int64_t C, int64_t K)
 bool ttm_slab_preferred(int x_dtype, int64_t R, int64_t L, int64_t C, int64_t K);
 int launch_ttm_slab(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, const float* F,
                     int64_t K, void* Y, int y_dtype, cudaStream_t s);
+// Fused root (ttm_slab.cu): T x_a Fa^T and T x_b Fb^T (a < b) from one read
+// of T (FP32 -> FP32, BF16 -> BF16 or FP32), Ya as [A][Ka][M Lb B], Yb as
+// [A La M][Kb][B]; the shape must pass fused_root_fits.
+int launch_ttm_fused_root(int dtype, const void* X, const int64_t* L, int N, int a, int b,
+                          const float* Fa, int64_t Ka, const float* Fb, int64_t Kb, void* Ya, void* Yb,
+                          int y_dtype, cudaStream_t s);
 // FP8 E4M3 tensors with per-64 scales (fp8.cu): Y = X x_n F^T with Y FP32 or
 // BF16, and ||X||^2; X is the whole tensor (R * L * C elements) in the layout
 // of tucker_fp8_bytes.

@@ -33,6 +33,10 @@ struct Plan {
   int tree = TUCKER_TREE_OPTIMAL;
   int cost_model = TUCKER_COST_MACS;
   std::vector<PlanNode> nodes;  // depth-first pre-order, nodes[0] is the root
+  // fused root: the first two root children (node indices, DFS order) are
+  // computed together from one read of T when the first one is reached; the
+  // second one's buffer is placed after the first one's whole subtree
+  int fused_u1 = -1, fused_u2 = -1;
   uint64_t tree_macs = 0, tree_elems = 0;
   std::vector<int> core_order;  // mode order of the new-core chain
   uint64_t core_macs = 0;
@@ -63,6 +67,10 @@ struct Plan {
     return dtype == TUCKER_F64 ? 8 : ((dtype == TUCKER_BF16 || dtype == TUCKER_FP8_E4M3) ? 2 : 4);
   }
 };
+
+// whether the fused root TTM (ttm_slab.cu) takes the two root children of
+// modes a < b of a tensor of this type and these lengths
+bool fused_root_fits(int dtype, int N, const int64_t* L, const int64_t* K, int a, int b);
 
 // thread-local error text
 void set_error(const std::string& msg);

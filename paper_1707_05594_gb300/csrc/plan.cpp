@@ -185,20 +185,40 @@ struct Builder {
 };
 
 // Stack memory plan: a node's output stays live while its subtree runs, so
-// the buffer of a node sits right after its parent's buffer.
+// the buffer of a node sits right after its parent's buffer.  With a fused
+// root the second root child's output is written together with the first
+// one's and stays live through the first one's subtree: it goes after the
+// peak of the plain stack plan, and its own subtree after it.
 void memory_plan(Plan& p) {
   size_t peak = 0;
   std::vector<size_t> end(p.nodes.size(), 0);
-  for (size_t i = 0; i < p.nodes.size(); ++i) {
-    PlanNode& nd = p.nodes[i];
-    if (nd.label < 0) continue;  // root (T is the input) and leaves own no buffer
-    const int par = nd.parent;
-    const size_t base = (par <= 0) ? 0 : end[(size_t)par];
-    nd.ws_off = base;
-    end[i] = base + align_up((size_t)nd.out_elems * p.inter_bytes());
-    peak = std::max(peak, end[i]);
+  for (int pass = 0; pass < (p.fused_u2 > 0 ? 2 : 1); ++pass) {
+    const size_t plain_peak = peak;
+    for (size_t i = 0; i < p.nodes.size(); ++i) {
+      PlanNode& nd = p.nodes[i];
+      if (nd.label < 0) continue;  // root (T is the input) and leaves own no buffer
+      const int par = nd.parent;
+      size_t base = (par <= 0) ? 0 : end[(size_t)par];
+      if (pass == 1 && (int)i == p.fused_u2) base = plain_peak;
+      nd.ws_off = base;
+      end[i] = base + align_up((size_t)nd.out_elems * p.inter_bytes());
+      peak = std::max(peak, end[i]);
+    }
   }
   p.bytes_scratch = std::max(p.bytes_scratch, peak);
+}
+
+// Fused root: the first two root children in depth-first order, when both
+// are TTM nodes whose pair of modes the fused kernel takes.
+void choose_fused_root(Plan& p) {
+  int u[2] = {-1, -1}, found = 0;
+  for (size_t i = 1; i < p.nodes.size() && found < 2; ++i)
+    if (p.nodes[i].parent == 0 && p.nodes[i].label >= 0) u[found++] = (int)i;
+  if (found < 2) return;
+  const int m1 = p.nodes[(size_t)u[0]].label, m2 = p.nodes[(size_t)u[1]].label;
+  if (!fused_root_fits(p.dtype, p.N, p.L, p.K, std::min(m1, m2), std::max(m1, m2))) return;
+  p.fused_u1 = u[0];
+  p.fused_u2 = u[1];
 }
 
 // Mode order of the new-core chain minimising multiply-adds: DP over the set
@@ -286,6 +306,8 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown tree kind");
   if (o.cost_model != TUCKER_COST_MACS && o.cost_model != TUCKER_COST_ELEMS)
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown cost model");
+  if (o.flags & ~TUCKER_PLAN_NO_FUSED_ROOT)
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown flags");
   long double total = 1;
   for (int n = 0; n < N; ++n) {
     if (L[n] < 1 || K[n] < 1 || K[n] > L[n])
@@ -343,6 +365,7 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
       p.tree_elems += nd.in_elems + nd.out_elems;
     }
   }
+  if (!(o.flags & TUCKER_PLAN_NO_FUSED_ROOT)) choose_fused_root(p);
   memory_plan(p);
   core_chain(p);
   sthosvd_buffers(p);
@@ -391,6 +414,13 @@ int tucker_plan_nodes(tucker_plan_t plan, tucker_node_t* nodes, int capacity, in
       nodes[i].ws_offset = nd.ws_off;
     }
   }
+  return TUCKER_OK;
+}
+
+int tucker_plan_fused_root(tucker_plan_t plan, int* first, int* second) {
+  if (!plan || !first || !second) return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan_fused_root: NULL argument");
+  *first = plan->p.fused_u1;
+  *second = plan->p.fused_u2;
   return TUCKER_OK;
 }
 

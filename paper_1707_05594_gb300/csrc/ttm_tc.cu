@@ -752,6 +752,15 @@ bool ttm_tc_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X,
   return C % 8 == 0 && C >= 64;
 }
 
+// Share of a tensor-core tile's work that is the TTM's own: l runs in stages
+// of 64 (the last one zero-filled past L) and the column case tiles each
+// r-slab's C positions by 128 (by 64, two slabs per tile, at C = 64).
+double ttm_tc_efficiency(int64_t L, int64_t C) {
+  const double el = (double)L / (double)(kBoxL * ((L + kBoxL - 1) / kBoxL));
+  if (C <= 64) return el;
+  return el * (double)C / (double)(kTileM * ((C + kTileM - 1) / kTileM));
+}
+
 // Y (K outputs, FP32 or BF16) = X x_n F^T with X (and optionally X_lo) BF16.
 int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t C,
                   const float* F, int64_t K, void* Y, bool y_bf16, cudaStream_t s) {
@@ -864,8 +873,8 @@ int kernel_policy() { return g_policy.load(std::memory_order_relaxed); }
 }  // namespace tk
 
 extern "C" int tucker_set_kernel_policy(int policy) {
-  if (policy < 0 || policy > 15)
-    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 15]");
+  if (policy < 0 || policy > 31)
+    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 31]");
   tk::g_policy.store(policy, std::memory_order_relaxed);
   return TUCKER_OK;
 }

@@ -80,6 +80,8 @@ SLAB_CASES = [
     # 1 < C < 64: slabs of L x C per block, positions 256 apart
     ((77, 32, 24), 1, 8), ((50, 40, 2), 1, 4), ((33, 9, 63), 1, 16), ((5, 17, 3), 1, 2),
     ((64, 56, 48, 40, 3), 3, 10), ((129, 31, 5), 1, 32), ((7, 24, 33), 1, 20),
+    # C % 4 == 0 and K <= 16
+    ((300, 12, 8), 1, 3), ((40, 20, 60), 1, 13), ((9, 33, 4), 1, 16), ((1001, 7, 28), 1, 5),
 ]
 
 
@@ -131,12 +133,13 @@ def status_ok(tk):
 
 
 @pytest.mark.parametrize("shape,n,K", TC_CASES)
-@pytest.mark.parametrize("policy", [0, 1])
+@pytest.mark.parametrize("policy", [16, 1])
 def test_ttm_bf16_tensor_cores(tk, orc, shape, n, K, policy):
-    """BF16 tensor, FP32 factor: the tcgen05 path (policy 0) splits F into two
-    BF16 parts (error <= 2^-16 |f| per product) and accumulates in FP32 in
-    TMEM; the CUDA-core path (policy 1) converts exactly and accumulates with
-    FMAs.  Bound: (2^-15 + (L + 2) * 2^-23) * sum |x f|."""
+    """BF16 tensor, FP32 factor: the tcgen05 path (policy 16: tensor cores
+    wherever the shape allows) splits F into two BF16 parts (error <= 2^-16
+    |f| per product) and accumulates in FP32 in TMEM; the CUDA-core path
+    (policy 1) converts exactly and accumulates with FMAs.  Bound:
+    (2^-15 + (L + 2) * 2^-23) * sum |x f|."""
     X = workloads.random_tensor(shape, seed=sum(shape) * 3 + n, dtype=torch.bfloat16)
     F = workloads.random_factor(shape[n], K, seed=K + 1, dtype=torch.float32, orthonormal=False)
     out_shape = list(shape)

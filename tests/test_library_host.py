@@ -138,6 +138,69 @@ def test_memory_plan_is_a_stack(tk):
                 p = q["parent"]
 
 
+FUSED_SHAPES = [
+    # (L, K): shapes whose first two root children fuse, covering every layout
+    # of T as [A][La][M][Lb][B] (A, M, B each 1 or more) and both orders of
+    # the two children in the tree
+    ((64, 56, 48, 40, 32, 24), (16, 14, 12, 10, 8, 6)),
+    ((8, 4, 4), (3, 2, 2)), ((11, 9, 20), (10, 9, 10)), ((22, 7, 5, 2), (3, 4, 2, 2)),
+    ((21, 13, 7, 11, 21), (8, 3, 6, 1, 2)), ((13, 32, 14, 37, 4), (7, 8, 6, 7, 1)),
+    ((26, 39, 2, 30, 4), (12, 3, 1, 2, 2)), ((4, 31, 5, 13, 5, 16), (4, 9, 5, 3, 2, 6)),
+    ((5, 18, 3, 24), (4, 1, 3, 7)), ((13, 4, 32, 16), (3, 1, 3, 2)),
+    ((26, 3, 2, 16, 21), (5, 1, 2, 3, 12)), ((3, 13, 4, 3, 2), (2, 3, 3, 1, 2)),
+]
+
+
+@pytest.mark.parametrize("L,K", FUSED_SHAPES)
+def test_fused_root_plan(tk, L, K):
+    """A fused root names the first two root children (depth-first order);
+    the second one's buffer overlaps no buffer of the first one's subtree
+    (it is written with the first one and read after that subtree); without
+    fusion (plan flag) the plan is the plain stack plan.  The trailing block
+    from the smaller of the two modes fits in 8 KB (host only)."""
+    import math
+    for dtype, es in ((tk.TUCKER_F32, 4), (tk.TUCKER_BF16, 2)):
+        p = tk.tucker_plan(L, K, dtype)
+        nodes = tk.tucker_plan_nodes(p)
+        roots = [i for i, nd in enumerate(nodes) if nd["parent"] == 0 and nd["label"] >= 0]
+        f = tk.tucker_plan_fused_root(p)
+        a = min(nodes[roots[0]]["label"], nodes[roots[1]]["label"])
+        fits = math.prod(L[a:]) * es <= 8192
+        if dtype == tk.TUCKER_F32:
+            assert f is not None or not fits
+        if f is None:
+            continue
+        assert f == (roots[0], roots[1])
+        u1, u2 = f
+        sub = {u1}
+        for i, nd in enumerate(nodes):
+            if nd["parent"] in sub:
+                sub.add(i)
+        b0 = nodes[u2]["ws_offset"]
+        b1 = b0 + es * nodes[u2]["out_elems"]
+        for i in sub:
+            if nodes[i]["label"] < 0:
+                continue
+            a0 = nodes[i]["ws_offset"]
+            a1 = a0 + es * nodes[i]["out_elems"]
+            assert a1 <= b0 or b1 <= a0, (L, i)
+        assert b1 <= tk.tucker_plan_cost(p)["ws_bytes"]
+        q = tk.tucker_plan(L, K, dtype, fuse_root=False)
+        assert tk.tucker_plan_fused_root(q) is None
+        assert tk.tucker_plan_cost(q)["tree_macs"] == tk.tucker_plan_cost(p)["tree_macs"]
+
+
+def test_plan_flags_validated(tk):
+    import ctypes
+    h = ctypes.c_void_p()
+    L = (tk._i64((8, 4, 4)))
+    K = (tk._i64((3, 2, 2)))
+    opts = tk.PlanOpts(tk.TUCKER_F32, tk.TREE_OPTIMAL, tk.COST_MACS, 2)
+    assert tk.lib().tucker_plan(3, L, K, ctypes.byref(opts), ctypes.byref(h)) == -1
+    # no fused root where the trailing block is too large (200^4: 64 MB)
+    assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (20,) * 4)) is None
+
+
 def test_elems_cost_model(tk, orc):
     # the elements-moved objective never moves more elements than the MAC tree
     for L, K in [((672, 672, 627, 16), (279, 279, 153, 14)),
