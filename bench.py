@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--planner", action="store_true",
                     help="host only: TTM-tree loads of the optimal tree vs the prior trees over the "
                          "paper's metadata benchmark (5-D and 6-D) and its real-tensor metadata")
+    ap.add_argument("--ttm-pair", default=None,
+                    help="time the fused root kernel (tucker_ttm_pair) alone: "
+                         "'L0,L1,...:a:Ka:b:Kb[:f32|bf16]' (kernel studies and small ncu captures)")
     ap.add_argument("--ttm", default=None,
                     help="time one TTM kernel alone: 'L0,L1,...:mode:K[:f32|bf16|f64]' "
                          "(kernel studies and small ncu captures)")
@@ -103,6 +106,45 @@ def run_ttm_only(args):
     pk = peaks()
     return {"kernel": "tucker_ttm", "policy": args.kernel_policy, "shape": list(dims), "mode": n,
             "K": K,
+            "dtype": str(dt).replace("torch.", ""), "ms": round(ms, 5),
+            "gbs": round(byts / ms / 1e6, 1), "frac_of_hbm": round(byts / ms / 1e6 / pk["hbm_gbs"], 4),
+            "steps": args.steps, "warmup": args.warmup}
+
+
+def run_ttm_pair_only(args):
+    """Times tucker_ttm_pair (both root children from one read of X) on one
+    shape; outputs in the tensor's type, as inside a sweep."""
+    import torch
+
+    import paper_1707_05594_gb300 as tk
+    import workloads
+    from paper_1707_05594_gb300 import build as tkbuild
+    tkbuild.build()
+    parts = args.ttm_pair.split(":")
+    dims = tuple(int(x) for x in parts[0].split(","))
+    a, Ka, b, Kb = (int(x) for x in parts[1:5])
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16}[parts[5] if len(parts) > 5 else "f32"]
+    X = workloads.random_tensor(dims, seed=1, dtype=dt, device="cuda")
+    Fa = workloads.random_factor(dims[a], Ka, seed=2, device="cuda")
+    Fb = workloads.random_factor(dims[b], Kb, seed=3, device="cuda")
+    sa, sb = list(dims), list(dims)
+    sa[a], sb[b] = Ka, Kb
+    Ya = torch.empty(sa, dtype=dt, device="cuda")
+    Yb = torch.empty(sb, dtype=dt, device="cuda")
+    for _ in range(args.warmup):
+        tk.tucker_ttm_pair(X, a, Fa, Ya, b, Fb, Yb)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        tk.tucker_ttm_pair(X, a, Fa, Ya, b, Fb, Yb)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    byts = sum(t.numel() * t.element_size() for t in (X, Ya, Yb))
+    pk = peaks()
+    return {"kernel": "tucker_ttm_pair", "shape": list(dims), "modes": [a, b], "K": [Ka, Kb],
             "dtype": str(dt).replace("torch.", ""), "ms": round(ms, 5),
             "gbs": round(byts / ms / 1e6, 1), "frac_of_hbm": round(byts / ms / 1e6 / pk["hbm_gbs"], 4),
             "steps": args.steps, "warmup": args.warmup}
@@ -795,6 +837,9 @@ def main():
     ws_size, rank, local = dist_setup()
     if args.ttm:
         print(json.dumps(run_ttm_only(args)), flush=True)
+        return 0
+    if args.ttm_pair:
+        print(json.dumps(run_ttm_pair_only(args)), flush=True)
         return 0
     if args.batch_only:
         print(json.dumps({"batched_form": run_batch_form(args)}), flush=True)
