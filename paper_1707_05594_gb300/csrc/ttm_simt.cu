@@ -455,9 +455,9 @@ int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, cons
       // and for column shapes whose tiles are mostly padding (measured: at
       // L = 40, C = 192, 47 % useful, the CUDA cores are 1.3x faster; at
       // L = 48, C = 7680, 75 %, the tensor cores 1.2x)
-      if ((kernel_policy() & 1) == 0 && !(C == 1 && L <= kStagedMaxL) &&
-          (C == 1 || (kernel_policy() & 16) || ttm_tc_efficiency(L, C) >= 0.6) &&
-          ttm_tc_supported(R, L, C, K, X, nullptr))
+      const bool tc_any = (kernel_policy() & 16) != 0;
+      if ((kernel_policy() & 1) == 0 && (tc_any || !(C == 1 && L <= kStagedMaxL)) &&
+          (C == 1 || tc_any || ttm_tc_efficiency(L, C) >= 0.6) && ttm_tc_supported(R, L, C, K, X, nullptr))
         return launch_ttm_tc(X, nullptr, R, L, C, static_cast<const float*>(F), K, Y, ybf, s);
       // short rows (no tensor-core tile): runs of whole slabs through shared memory
       if ((kernel_policy() & 8) == 0 && ttm_slab_preferred(TUCKER_BF16, R, L, C, K))
