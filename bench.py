@@ -66,7 +66,7 @@ def parse():
                     help="time the fused root kernel (tucker_ttm_pair) alone: "
                          "'L0,L1,...:a:Ka:b:Kb[:f32|bf16]' (kernel studies and small ncu captures)")
     ap.add_argument("--ttm", default=None,
-                    help="time one TTM kernel alone: 'L0,L1,...:mode:K[:f32|bf16|f64]' "
+                    help="time one TTM kernel alone: 'L0,L1,...:mode:K[:f32|bf16|f64|fp8]' "
                          "(kernel studies and small ncu captures)")
     return ap.parse_args()
 
@@ -83,9 +83,13 @@ def run_ttm_only(args):
     parts = args.ttm.split(":")
     dims = tuple(int(x) for x in parts[0].split(","))
     n, K = int(parts[1]), int(parts[2])
-    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[
-        parts[3] if len(parts) > 3 else "f32"]
+    name = parts[3] if len(parts) > 3 else "f32"
+    fp8 = name == "fp8"
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64, "fp8": torch.float32}[name]
     X = workloads.random_tensor(dims, seed=1, dtype=dt, device="cuda")
+    if fp8:
+        X = tk.tucker_convert_fp8(X.reshape(-1))
+        X.shape = tuple(dims)
     fdt = torch.float64 if dt == torch.float64 else torch.float32
     F = workloads.random_factor(dims[n], K, seed=2, dtype=fdt, device="cuda")
     out = list(dims)
@@ -102,11 +106,12 @@ def run_ttm_only(args):
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    byts = X.numel() * X.element_size() + Y.numel() * Y.element_size()
+    xbytes = X.numel() * (1 + 4 / 64) if fp8 else X.numel() * X.element_size()
+    byts = xbytes + Y.numel() * Y.element_size()
     pk = peaks()
     return {"kernel": "tucker_ttm", "policy": args.kernel_policy, "shape": list(dims), "mode": n,
             "K": K,
-            "dtype": str(dt).replace("torch.", ""), "ms": round(ms, 5),
+            "dtype": "fp8_e4m3" if fp8 else str(dt).replace("torch.", ""), "ms": round(ms, 5),
             "gbs": round(byts / ms / 1e6, 1), "frac_of_hbm": round(byts / ms / 1e6 / pk["hbm_gbs"], 4),
             "steps": args.steps, "warmup": args.warmup}
 

@@ -308,6 +308,11 @@ int launch_ttm_fused_root(int dtype, const void* X, const int64_t* L, int N, int
 // BF16, and ||X||^2; X is the whole tensor (R * L * C elements) in the layout
 // of tucker_fp8_bytes.
 size_t fp8_scale_offset(int64_t n);
+// FP8 column-case TTM on the tensor cores (ttm_tc.cu): Xq the codes, scales
+// one FP32 per 64 elements of the row-major tensor, Y FP32 or BF16.
+bool ttm_tc_fp8_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* Xq);
+int launch_ttm_tc_fp8(const void* Xq, const float* scales, int64_t R, int64_t L, int64_t C,
+                      const float* F, int64_t K, void* Y, bool y_bf16, cudaStream_t s);
 int launch_ttm_fp8(const void* X, int64_t R, int64_t L, int64_t C, const float* F, int64_t K,
                    void* Y, int y_dtype, cudaStream_t s);
 int launch_norm2_fp8(const void* X, int64_t n, double* out, cudaStream_t s);

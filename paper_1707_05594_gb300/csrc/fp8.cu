@@ -267,6 +267,11 @@ int launch_ttm_fp8(const void* X, int64_t R, int64_t L, int64_t C, const float* 
   const int64_t n = R * L * C;
   const uint8_t* q = static_cast<const uint8_t*>(X);
   const float* sc = reinterpret_cast<const float*>(q + fp8_scale_offset(n));
+  // tensor cores (codes decoded to a BF16 hi + lo pair in shared memory) where
+  // the column shape allows, unless the policy keeps TTMs on the CUDA cores
+  if ((kernel_policy() & 1) == 0 && (y_dtype == TUCKER_F32 || y_dtype == TUCKER_BF16) &&
+      ttm_tc_fp8_supported(R, L, C, K, q))
+    return launch_ttm_tc_fp8(q, sc, R, L, C, F, K, Y, y_dtype == TUCKER_BF16, s);
   if ((R * C + kF8Threads - 1) / kF8Threads >= (int64_t)INT32_MAX || L > INT32_MAX)
     return fail(TUCKER_ERR_UNSUPPORTED, "ttm: tensor too large for the grid");
   if (y_dtype == TUCKER_BF16)

@@ -26,6 +26,9 @@
 // %globaltimer deadline; on expiry the kernel records an error word, drains
 // its own copies (bounded), frees TMEM and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <atomic>
 #include <mutex>
@@ -669,6 +672,282 @@ __global__ void __launch_bounds__(kF32Threads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP8 E4M3 tensors (one FP32 scale per 64 consecutive elements) on the tensor
+// cores (column case, C % 64 == 0).  TMA brings 128 c x 64 l tiles of codes
+// (8 KB) into a staging ring (no swizzle); a converter of eight warps decodes
+// eight codes at a time, multiplies them by their block's scale (exact in
+// FP32: a 4-bit significand times a 24-bit one) and writes the value rounded
+// to BF16 (relative 2^-9, a 32nd of the E4M3 step) in the 128-byte-swizzled
+// MN-major layout; per k-step the MMA warp issues A [F_hi | F_lo], so F keeps
+// ~16 bits.  Warp roles: warp 0 TMA producer, warp 1 TMEM + MMA issuer,
+// warps 2-9 converter, warps 10-17 two epilogue groups.
+// ---------------------------------------------------------------------------
+constexpr int kF8St = 12;                         // staging stages (codes): 96 KB in flight
+constexpr int kF8Cv = 3;                          // converted stages (BF16)
+constexpr int kF8Warps = 8;                       // converter warps
+constexpr int kF8StageBytes = kTileM * kBoxL;     // 8 KB
+constexpr int kF8CvBytes = kStageBytes;           // 16 KB
+constexpr int kF8Threads = 64 + kF8Warps * 32 + kEpiGroups * 128;
+
+template <typename TOut>
+__global__ void __launch_bounds__(kF8Threads, 1)
+    ttm_tc_fp8_kernel(const __grid_constant__ CUtensorMap map_q, const float* __restrict__ scales,
+                      TOut* __restrict__ Y, const TcParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* stage = smem;                                        // kF8St x 8 KB
+  unsigned char* conv = stage + (size_t)kF8St * kF8StageBytes;        // kF8Cv x 16 KB
+  unsigned char* bsm = conv + (size_t)kF8Cv * kF8CvBytes;
+  const int N2 = 2 * P.Np;
+  const size_t b_bytes = (size_t)P.nk * N2 * 128;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + ((b_bytes + 15) & ~size_t(15)));
+  uint64_t* st_full = bars;                   // kF8St
+  uint64_t* st_empty = st_full + kF8St;       // kF8St
+  uint64_t* cv_full = st_empty + kF8St;       // kF8Cv
+  uint64_t* cv_empty = cv_full + kF8Cv;       // kF8Cv
+  uint64_t* tfull = cv_empty + kF8Cv;         // kAccBufs
+  uint64_t* tempty = tfull + kAccBufs;        // kAccBufs
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + kAccBufs);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(kAccBufs * N2)) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kF8St; ++st) {
+      mbar_init(&st_full[st], 1);
+      mbar_init(&st_empty[st], kF8Warps);
+    }
+    for (int st = 0; st < kF8Cv; ++st) {
+      mbar_init(&cv_full[st], kF8Warps);
+      mbar_init(&cv_empty[st], 1);
+    }
+    for (int b = 0; b < kAccBufs; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // B = [F_hi | F_lo]^T as BF16, K-major without swizzle (as in ttm_tc_kernel)
+  for (int idx = threadIdx.x; idx < N2 * P.nk * kBoxL; idx += kF8Threads) {
+    const int row = idx / (P.nk * kBoxL);
+    const int l = idx - row * (P.nk * kBoxL);
+    const int k = row < P.Np ? row : row - P.Np;
+    float f = 0.f;
+    if (k < P.K && l < P.L) f = P.F[(int64_t)l * P.K + k];
+    const uint16_t hi = f2bf(f);
+    const float rem = f - __uint_as_float((uint32_t)hi << 16);
+    const uint16_t v = row < P.Np ? hi : f2bf(rem);
+    const int chunk = l / kBoxL, lc = l - chunk * kBoxL;
+    const size_t off = (size_t)chunk * N2 * 128 + (size_t)(row >> 3) * 1024 + (size_t)(lc >> 3) * 128 +
+                       (size_t)(row & 7) * 16 + (size_t)(lc & 7) * 2;
+    *reinterpret_cast<uint16_t*>(bsm + off) = v;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+        const int64_t r = t / P.ctiles;
+        const int c0 = (int)((t - r * P.ctiles) * kTileM);
+        for (int kc = 0; kc < P.nk; ++kc, ++it) {
+          const uint32_t st = it % kF8St, ph = (it / kF8St) & 1u;
+          if (!mbar_wait(&st_empty[st], ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&st_full[st], (uint32_t)kF8StageBytes);
+          tma_load_3d(stage + (size_t)st * kF8StageBytes, &map_q, &st_full[st], c0, kc * kBoxL, (int)r);
+        }
+      }
+      const uint32_t issued = it;
+      for (uint32_t j = (issued > (uint32_t)kF8St ? issued - kF8St : 0); j < issued; ++j) {
+        const uint32_t st = j % kF8St, ph = (j / kF8St) & 1u;
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(&st_full[st], ph) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc_full = idesc_bf16(N2, 1);
+      const uint32_t b_base = smem_u32(bsm);
+      uint32_t it = 0, tcount = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x, ++tcount) {
+        const uint32_t buf = tcount % kAccBufs, aph = (tcount / kAccBufs) & 1u;
+        if (!mbar_wait(&tempty[buf], aph ^ 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + buf * (uint32_t)N2;
+        for (int kc = 0; kc < P.nk; ++kc, ++it) {
+          const uint32_t cs = it % kF8Cv, ph = (it / kF8Cv) & 1u;
+          if (!mbar_wait(&cv_full[cs], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(conv + (size_t)cs * kF8CvBytes);
+#pragma unroll
+          for (int ks = 0; ks < kBoxL / 16; ++ks) {
+            const uint64_t ad = smem_desc(a_base + ks * 2048, 8192, 1024, kSwizzle128);
+            const uint32_t b_chunk = b_base + (uint32_t)(kc * N2 * 128);
+            const uint64_t bd = smem_desc(b_chunk + ks * 256, 128, 1024, kSwizzleNone);
+            mma_bf16(d_tmem, ad, bd, idesc_full, (kc > 0 || ks > 0) ? 1u : 0u);
+          }
+          mma_commit(&cv_empty[cs]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[buf]);
+      }
+    }
+  } else if (warp < 2 + kF8Warps) {
+    // ------------------------------------------------------------ converter
+    // Thread ct converts groups g = ct + 256 i (i < 4) of a stage: row
+    // l = 2 wq + (lane >> 4) + 16 i, columns c = 8 (lane & 15) .. + 7.  The 16
+    // (row, 64-column half) scales a warp needs per stage are loaded six
+    // stages ahead, one per lane (slot j = lane & 15: row 2 wq + ((j >> 1) & 1)
+    // + 16 (j >> 2), half j & 1), and handed to the groups by warp shuffles.
+    const int ct = threadIdx.x - 64;  // 0 .. 255
+    const int wq = ct >> 5;
+    const int js = lane & 15;
+    auto scale_slot = [&](int64_t t, int kc) -> float {
+      if (t >= P.tiles) return 0.f;
+      const int64_t r = t / P.ctiles;
+      const int64_t lg = (int64_t)kc * kBoxL + 2 * wq + ((js >> 1) & 1) + 16 * (js >> 2);
+      const int64_t cg = (t - r * P.ctiles) * kTileM + 64 * (js & 1);
+      return (lg < P.L && cg < P.C) ? __ldg(scales + (((r * P.L + lg) * P.C + cg) >> 6)) : 0.f;
+    };
+    // (tile, chunk) of the stage after (t, kc)
+    auto advance = [&](int64_t& t, int& kc) {
+      if (++kc == P.nk) {
+        kc = 0;
+        t += gridDim.x;
+      }
+    };
+    // scale slots of the next kAhead stages: slot a holds stage it's scale for
+    // it % kAhead == a; the stage loop is unrolled by kAhead so that a slot is
+    // read and refilled in place (moving a register whose load is still in
+    // flight would wait for that load)
+    constexpr int kAhead = 6;
+    float ahead[kAhead];
+    int64_t tp = blockIdx.x;
+    int kcp = 0;
+#pragma unroll
+    for (int a = 0; a < kAhead; ++a) {
+      ahead[a] = scale_slot(tp, kcp);
+      advance(tp, kcp);
+    }
+    uint32_t it = 0;
+    bool ok = true;
+    int64_t t = blockIdx.x;
+    int kc = 0;
+    while (ok && t < P.tiles) {
+#pragma unroll
+      for (int a = 0; a < kAhead; ++a) {
+        if (!ok || t >= P.tiles) break;
+        const float cur = ahead[a];
+        ahead[a] = scale_slot(tp, kcp);
+        advance(tp, kcp);
+        const uint32_t ss = it % kF8St, sph = (it / kF8St) & 1u;
+        const uint32_t cs = it % kF8Cv, cph = (it / kF8Cv) & 1u;
+        if (!mbar_wait(&st_full[ss], sph, abort_flag) || !mbar_wait(&cv_empty[cs], cph ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* src = stage + (size_t)ss * kF8StageBytes;
+        unsigned char* dst = conv + (size_t)cs * kF8CvBytes;
+#pragma unroll
+        for (int i = 0; i < (kTileM * kBoxL / 8) / (kF8Warps * 32); ++i) {
+          const int g = ct + kF8Warps * 32 * i;   // eight consecutive c of one l
+          const int l = g >> 4, c = (g & 15) << 3;
+          // with C % 64 == 0 the 64-column half of row l is one scale block;
+          // rows and columns past the tensor were zero-filled by TMA (scale 0)
+          const float sc = __shfl_sync(0xffffffffu, cur, (i << 2) | ((lane >> 4) << 1) | ((lane & 15) >> 3));
+          const uint2 w = *reinterpret_cast<const uint2*>(src + l * kTileM + c);
+          const uint32_t words[2] = {w.x, w.y};
+          uint32_t hw[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const __nv_fp8x2_storage_t pr = (__nv_fp8x2_storage_t)((words[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
+            const float2 v = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(pr, __NV_E4M3)));
+            // paired round-to-nearest-even conversion (the values are finite)
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(v.x * sc, v.y * sc);
+            hw[j] = *reinterpret_cast<const uint32_t*>(&hb);
+          }
+          const uint32_t off = (uint32_t)(c >> 6) * 8192u + (uint32_t)l * 128u +
+                               ((uint32_t)(((c & 63) >> 3) ^ (l & 7)) << 4);
+          *reinterpret_cast<uint4*>(dst + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&cv_full[cs]);
+          mbar_arrive(&st_empty[ss]);
+        }
+        ++it;
+        advance(t, kc);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t group = (uint32_t)(warp - 2 - kF8Warps) / 4u;
+    uint32_t tcount = group;
+    for (int64_t t = blockIdx.x + (int64_t)group * gridDim.x; t < P.tiles;
+         t += (int64_t)kEpiGroups * gridDim.x, tcount += kEpiGroups) {
+      const uint32_t buf = tcount % kAccBufs, aph = (tcount / kAccBufs) & 1u;
+      if (!mbar_wait(&tfull[buf], aph, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + buf * (uint32_t)N2;
+      const int64_t r = t / P.ctiles;
+      const int64_t c = (t - r * P.ctiles) * kTileM + row;
+      float hi[16], lo[16];
+      for (int k0 = 0; k0 < P.Np; k0 += 16) {
+        tmem_ld16(tbase + k0, hi);
+        tmem_ld16(tbase + P.Np + k0, lo);
+        tmem_wait_ld();
+        if (k0 + 16 >= P.Np) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+        if (c < P.C) {
+          TOut* yp = Y + (r * P.K) * P.C + c;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (k0 + j < P.K) yp[(int64_t)(k0 + j) * P.C] = to_out<TOut>(hi[j] + lo[j]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(ncols));
+  }
+}
+
 // One thread waits, through the kernels' bounded wait, on an mbarrier that no
 // thread or copy ever completes: the wait gives up after its time limit and
 // records TUCKER_ERR_TIMEOUT in the device error word, and the kernel returns
@@ -860,6 +1139,56 @@ int launch_ttm_tc_f32(const float* X, int64_t R, int64_t L, int64_t C, const flo
   const int64_t grid = std::min<int64_t>(P.tiles, sm_count());
   kern<<<(unsigned)grid, kF32Threads, smem, s>>>(mx, Y, P);
   TK_LAUNCH_CHECK("ttm_tc_f32");
+  return TUCKER_OK;
+}
+
+size_t smem_bytes_fp8(int Np, int nk) {
+  return 1024 + (size_t)kF8St * kF8StageBytes + (size_t)kF8Cv * kF8CvBytes +
+         (((size_t)nk * 2 * Np * 128 + 15) & ~size_t(15)) + (2 * kF8St + 2 * kF8Cv + 2 * kAccBufs) * 8 + 16;
+}
+
+// FP8 column-case TTM on the tensor cores: C % 64 == 0 (each 64-column half
+// of a tile row is one scale block; 16-byte TMA strides), C >= 64, K <= 32,
+// codes 16-byte aligned, B and the rings within shared memory.
+bool ttm_tc_fp8_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X) {
+  if (K < 1 || K > 32 || L < 1 || L > 1024 || C < 64 || C % 64 != 0) return false;
+  if ((uintptr_t)X % 16 != 0 || R > INT32_MAX || C > INT32_MAX) return false;
+  const int Np = (int)((K + 15) / 16 * 16), nk = (int)((L + kBoxL - 1) / kBoxL);
+  return smem_bytes_fp8(Np, nk) <= 227 * 1024;
+}
+
+int launch_ttm_tc_fp8(const void* Xq, const float* scales, int64_t R, int64_t L, int64_t C,
+                      const float* F, int64_t K, void* Y, bool y_bf16, cudaStream_t s) {
+  if (!ttm_tc_fp8_supported(R, L, C, K, Xq))
+    return fail(TUCKER_ERR_UNSUPPORTED, "ttm_tc_fp8: shape or alignment not supported");
+  TcParams P{};
+  P.R = R;
+  P.C = C;
+  P.L = (int)L;
+  P.K = (int)K;
+  P.Np = (int)((K + 15) / 16 * 16);
+  P.nk = (int)((L + kBoxL - 1) / kBoxL);
+  P.F = F;
+  P.ctiles = (C + kTileM - 1) / kTileM;
+  P.tiles = R * P.ctiles;
+  CUtensorMap mq;
+  const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)L, (cuuint64_t)R};
+  const cuuint64_t str[2] = {(cuuint64_t)C, (cuuint64_t)C * L};
+  const cuuint32_t box[3] = {(cuuint32_t)kTileM, (cuuint32_t)kBoxL, 1u};
+  int rc = make_map(&mq, Xq, 3, dims, str, box, CU_TENSOR_MAP_DATA_TYPE_UINT8, CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (rc) return rc;
+  const size_t smem = smem_bytes_fp8(P.Np, P.nk);
+  const int64_t grid = std::min<int64_t>(P.tiles, sm_count());
+  if (y_bf16) {
+    auto kern = ttm_tc_fp8_kernel<bf16_t>;
+    TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)grid, kF8Threads, smem, s>>>(mq, scales, static_cast<bf16_t*>(Y), P);
+  } else {
+    auto kern = ttm_tc_fp8_kernel<float>;
+    TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)grid, kF8Threads, smem, s>>>(mq, scales, static_cast<float*>(Y), P);
+  }
+  TK_LAUNCH_CHECK("ttm_tc_fp8");
   return TUCKER_OK;
 }
 

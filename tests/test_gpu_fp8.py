@@ -58,33 +58,50 @@ def test_convert_fp8_matches_oracle_bit_for_bit(tk, orc, n):
 
 
 TTM_CASES = [
-    ((64, 48, 40), 0, 16),      # columns kernel (C % 4 == 0)
-    ((64, 48, 40), 1, 9),
+    ((64, 48, 40), 0, 16),      # column case, C % 16 == 0 and C >= 64: tensor cores
+    ((64, 48, 40), 1, 9),       # C = 40 < 64: CUDA-core columns kernel (C % 4 == 0)
     ((30, 20, 64), 2, 16),      # last mode, L % 4 == 0: rows kernel
     ((30, 20, 63), 2, 7),       # last mode, L odd: any-shape kernel
     ((13, 7, 9), 1, 5),         # C odd: any-shape kernel
-    ((40, 36, 32, 30), 2, 20),  # K > 16: two K blocks
+    ((40, 36, 32, 30), 2, 20),  # C = 30: two K blocks on the CUDA cores
+    ((30, 70, 192), 1, 16),     # tensor cores: C = 192 leaves half a 128-position tile
+    ((5, 130, 320), 1, 32),     # tensor cores: three l chunks (last ragged), K = 32
+    ((30, 70, 80), 1, 16),      # C % 64 != 0 (scale blocks straddle tile halves): CUDA cores
+    ((3, 40, 2048), 1, 1),      # tensor cores: K = 1
+    ((2, 64, 64, 16), 1, 20),   # tensor cores: C = 1024, K = 20 (two 16-column groups)
 ]
 
 
 @pytest.mark.parametrize("dims,n,K", TTM_CASES)
-def test_ttm_fp8_matches_oracle_on_dequantised_values(tk, orc, dims, n, K):
+@pytest.mark.parametrize("policy", [0, 1])
+def test_ttm_fp8_matches_oracle_on_dequantised_values(tk, orc, dims, n, K, policy):
+    """CUDA cores (policy 1): the dequantised values s * E4M3(q) in FP32 and
+    FMA accumulation, within 5e-6 of sum |x f|.  Tensor cores (policy 0, the
+    column shapes they take): each dequantised value rounded to BF16
+    (relative 2^-9, a 32nd of the E4M3 step), F as a BF16 hi + lo pair, FP32
+    accumulation in TMEM: within (2^-8 + (L + 2) 2^-23) sum |x f|."""
     x = spread_values(int(np.prod(dims)), seed=7 * n + K)
     f8 = tk.tucker_convert_fp8(x.cuda())
     f8.shape = tuple(dims)
     F = workloads.random_factor(dims[n], K, seed=3 + n, dtype=torch.float32)
     out = list(dims)
     out[n] = K
-    Y = torch.empty(out, dtype=torch.float32, device="cuda")
-    tk.tucker_ttm(f8, n, F.cuda(), Y)
-    torch.cuda.synchronize()
+    Y = torch.full(out, float("nan"), dtype=torch.float32, device="cuda")
+    assert tk.lib().tucker_set_kernel_policy(policy) == 0
+    try:
+        tk.tucker_ttm(f8, n, F.cuda(), Y)
+        torch.cuda.synchronize()
+    finally:
+        tk.lib().tucker_set_kernel_policy(0)
+    assert tk.tucker_device_status() == 0
     q, s = orc.fp8_quantize(x.numpy())
     xd = orc.fp8_dequantize(q, s).reshape(dims)
     Fd = F.double().numpy()
     ref = orc.ttm(xd, n, Fd.T)
     bound = orc.ttm(np.abs(xd), n, np.abs(Fd).T)
     err = np.abs(Y.double().cpu().numpy() - ref)
-    assert np.all(err <= 5e-6 * bound + 1e-30), float(np.max(err / (bound + 1e-30)))
+    tol = 5e-6 if policy == 1 else 2.0 ** -8 + (dims[n] + 2) * 2.0 ** -23
+    assert np.all(err <= tol * bound + 1e-30), float(np.max(err / (bound + 1e-30)))
 
 
 def test_norm2_fp8(tk, orc):
