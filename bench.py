@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--planner", action="store_true",
                     help="host only: TTM-tree loads of the optimal tree vs the prior trees over the "
                          "paper's metadata benchmark (5-D and 6-D) and its real-tensor metadata")
+    ap.add_argument("--planner-gpu", action="store_true",
+                    help="time sweeps along the optimal and the prior trees on the benchmark shapes "
+                         "where the optimal tree gains most")
+    ap.add_argument("--planner-gpu-shapes", type=int, default=4)
     ap.add_argument("--ttm-pair", default=None,
                     help="time the fused root kernel (tucker_ttm_pair) alone: "
                          "'L0,L1,...:a:Ka:b:Kb[:f32|bf16]' (kernel studies and small ncu captures)")
@@ -214,11 +218,92 @@ def run_planner(args):
     for name, (L, K) in real.items():
         ld = loads(list(L), list(K))
         res["real"][name] = {k: round(ld[k] / ld["opt"], 3) for k in kinds}
+        # the elements-moved objective: the tree minimising |In| + |Out| over
+        # its nodes against the MAC-optimal tree, both in units of |T|
+        T = math.prod(L)
+        cm = tk.tucker_plan_cost(tk.tucker_plan(list(L), list(K), tk.TUCKER_F32))
+        ce = tk.tucker_plan_cost(tk.tucker_plan(list(L), list(K), tk.TUCKER_F32, cost_model=tk.COST_ELEMS))
+        res["real"][name]["elems_per_T"] = {"mac_optimal_tree": round(cm["tree_elems"] / T, 3),
+                                            "elems_optimal_tree": round(ce["tree_elems"] / T, 3)}
+        res["real"][name]["macs_elems_tree_over_mac_tree"] = round(ce["tree_macs"] / cm["tree_macs"], 3)
     return {"metric": "TTM-tree computational load, prior trees / optimal tree (Sec. 3, Sec. 6 benchmark)",
             "paper_reports": "up to 2.8x (5D) and 3.6x (6D) lower load than the best prior algorithm",
             "enumeration": "multisets of modes (the paper's counts 1134 / 642 are not reproduced by "
                            "ordered or unordered enumeration)",
             **res}
+
+
+def run_planner_gpu(args):
+    """The trees of Sec. 3 timed on the GPU: over the Sec. 6 benchmark
+    metadata restricted to L_n in {20, 50, 100} (the eigensolver takes L <= 200)
+    and 1e8 <= |T| <= 2e9, for N = 5 and 6 the shape where the optimal tree's
+    load is lowest against the best prior tree and the shape at the median
+    ratio; each is decomposed (planted Tucker, rho 1e-2, FP32)
+    with the optimal, K-order chain, h-order chain and balanced trees, and
+    one sweep (tucker_hooi_sweep_core + fit) is timed with CUDA events (mean
+    of 3 after a warm-up sweep).  Reports ms per sweep, the measured speed-up
+    of the optimal tree over the fastest prior tree, and the load ratio."""
+    import itertools
+
+    import torch
+
+    import paper_1707_05594_gb300 as tk
+    import workloads
+    from paper_1707_05594_gb300 import build as tkbuild
+    tkbuild.build()
+    tk.lib()
+    trees = {"opt": tk.TREE_OPTIMAL, "chain_k": tk.TREE_CHAIN_K, "chain_h": tk.TREE_CHAIN_H,
+             "balanced": tk.TREE_BALANCED}
+    modes = [(L, int(round(L / c))) for L in (20, 50, 100) for c in (1.25, 2, 5, 10)]
+    cands = []
+    for N in (5, 6):
+        for combo in itertools.combinations_with_replacement(range(len(modes)), N):
+            L = [modes[i][0] for i in combo]
+            K = [modes[i][1] for i in combo]
+            if math.prod(L) > 2e9 or math.prod(L) < 1e8 or max(K) > 64:
+                continue  # (the eigensolver takes K <= 64)
+            try:
+                ld = {k: tk.tucker_plan_cost(tk.tucker_plan(L, K, tk.TUCKER_F32, t))["tree_macs"]
+                      for k, t in trees.items()}
+            except tk.TuckerError:
+                continue
+            best = min(v for k, v in ld.items() if k != "opt")
+            cands.append((best / ld["opt"], tuple(L), tuple(K), ld))
+    # per order: the shape with the largest load ratio and the one at the median
+    picked = []
+    for N in (5, 6):
+        cn = sorted((c for c in cands if len(c[1]) == N), key=lambda x: -x[0])
+        if cn:
+            picked += [cn[0], cn[len(cn) // 2]]
+    picked = picked[:args.planner_gpu_shapes]
+    out = []
+    for i, (ratio, L, K, ld) in enumerate(picked):
+        w = workloads.planted_tucker(L, K, 1e-2, 70 + i, dtype=torch.float32, device="cuda")
+        T = w["T"]
+        row = {"L": list(L), "K": list(K), "elements": math.prod(L),
+               "load_best_prior_over_opt": round(ratio, 3), "ms_per_sweep": {}}
+        for name, tree in trees.items():
+            d = tk.Decomposition(T, K, tree=tree)
+            d.sthosvd()
+            d.sweep()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                d.sweep()
+            e1.record()
+            torch.cuda.synchronize()
+            row["ms_per_sweep"][name] = round(e0.elapsed_time(e1) / 3, 4)
+            del d
+        prior = min(v for k, v in row["ms_per_sweep"].items() if k != "opt")
+        row["speedup_opt_over_fastest_prior"] = round(prior / row["ms_per_sweep"]["opt"], 3)
+        out.append(row)
+        del T, w
+        torch.cuda.empty_cache()
+    return {"metric": "HOOI sweep time, optimal TTM-tree vs the prior trees of Sec. 3.2 (GB300, FP32)",
+            "selection": "benchmark shapes (L_n in {20, 50, 100}, K_n = L_n / c, 1e8 <= |T| <= 2e9): "
+                         "for N = 5 and 6, the largest and the median best-prior / optimal load ratio",
+            "shapes": out}
 
 
 # ----------------------------------------------------------------- env -----
@@ -830,6 +915,9 @@ def main():
     args = parse()
     if args.planner:
         print(json.dumps(run_planner(args)), flush=True)
+        return 0
+    if args.planner_gpu:
+        print(json.dumps(run_planner_gpu(args)), flush=True)
         return 0
     if args.impl == "reference":
         # rank 0 alone times the oracle; other ranks exit without work
