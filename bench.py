@@ -66,6 +66,8 @@ def parse():
                     help="time sweeps along the optimal and the prior trees on the benchmark shapes "
                          "where the optimal tree gains most")
     ap.add_argument("--planner-gpu-shapes", type=int, default=4)
+    ap.add_argument("--gauss-seidel", action="store_true",
+                    help="Jacobi-form tree sweeps vs Gauss-Seidel sweeps on a hard case")
     ap.add_argument("--ttm-pair", default=None,
                     help="time the fused root kernel (tucker_ttm_pair) alone: "
                          "'L0,L1,...:a:Ka:b:Kb[:f32|bf16]' (kernel studies and small ncu captures)")
@@ -304,6 +306,55 @@ def run_planner_gpu(args):
             "selection": "benchmark shapes (L_n in {20, 50, 100}, K_n = L_n / c, 1e8 <= |T| <= 2e9): "
                          "for N = 5 and 6, the largest and the median best-prior / optimal load ratio",
             "shapes": out}
+
+
+def run_gauss_seidel(args):
+    """The paper's Jacobi-form sweep (TTM-tree, Fig. 2) against the
+    Gauss-Seidel form (each mode uses the factors already updated in the
+    sweep; one TTM chain per mode) on a hard case: a planted 200^3 FP32
+    tensor, ranks 16, noise as large as the signal (rho 1.0).  From the same
+    STHOSVD, 8 sweeps of each: the fit after every sweep and the mean time per
+    sweep (CUDA events)."""
+    import torch
+
+    import paper_1707_05594_gb300 as tk
+    import workloads
+    from paper_1707_05594_gb300 import build as tkbuild
+    tkbuild.build()
+    tk.lib()
+    L, K, S = (200, 200, 200), (16, 16, 16), 8
+    w = workloads.planted_tucker(L, K, 1.0, 81, dtype=torch.float32, device="cuda")
+    T = w["T"]
+    p = tk.tucker_plan(L, K, tk.TUCKER_F32)
+    ws = tk.workspace(p)
+    nt = torch.empty(1, dtype=torch.float64, device="cuda")
+    fo = torch.empty(2, dtype=torch.float64, device="cuda")
+    tk.tucker_norm2(p, T, nt)
+    F0 = [torch.empty(L[n], K[n], device="cuda") for n in range(3)]
+    G = torch.empty(*K, device="cuda")
+    tk.tucker_sthosvd(p, T, F0, G, ws)
+    out = {}
+    for name in ("jacobi_tree", "gauss_seidel"):
+        F = [f.clone() for f in F0]
+        F2 = [torch.empty_like(f) for f in F]
+        fits, ms = [], 0.0
+        for _ in range(S):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if name == "jacobi_tree":
+                tk.tucker_hooi_sweep(p, T, F, F2, ws)
+            else:
+                tk.tucker_hooi_sweep_gs(p, T, F, F2, None, ws)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            F, F2 = F2, F
+            tk.tucker_core(p, T, F, G, ws)
+            tk.tucker_fit(p, G, nt, fo)
+            fits.append(round(fo[0].item(), 9))
+        out[name] = {"fit_after_sweep": fits, "ms_per_sweep": round(ms / S, 4)}
+    return {"metric": "fit per sweep and time per sweep, Jacobi-form tree vs Gauss-Seidel HOOI",
+            "workload": "planted 200^3 FP32, ranks 16, rho 1.0, seed 81, from one STHOSVD", **out}
 
 
 # ----------------------------------------------------------------- env -----
@@ -918,6 +969,9 @@ def main():
         return 0
     if args.planner_gpu:
         print(json.dumps(run_planner_gpu(args)), flush=True)
+        return 0
+    if args.gauss_seidel:
+        print(json.dumps(run_gauss_seidel(args)), flush=True)
         return 0
     if args.impl == "reference":
         # rank 0 alone times the oracle; other ranks exit without work

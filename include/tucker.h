@@ -156,6 +156,16 @@ int tucker_hooi_sweep_core(tucker_plan_t plan, const void* T, const void* const*
                            void* const* F_out, void* G_in, void* ws, size_t ws_bytes,
                            void* stream);
 
+/* One HOOI sweep in the Gauss-Seidel form (the standard HOOI of Kolda and
+ * Bader, against which Sec. 3 describes its Jacobi form, Fig. 2): for
+ * n = 0 .. N-1, Z_n = T x_{m != n} F_m^T with F_out[m] for m < n (already
+ * updated this sweep) and F_in[m] for m > n, along the plan's core-chain order
+ * without n; F_out[n] = the leading K_n eigenvectors of Z_(n) Z_(n)^T (warm-
+ * started from F_in[n]).  No TTM-tree: each mode needs its own chain.  G_out
+ * (if not NULL) receives the core of F_out.  F_out may not alias F_in. */
+int tucker_hooi_sweep_gs(tucker_plan_t plan, const void* T, const void* const* F_in,
+                         void* const* F_out, void* G_out, void* ws, size_t ws_bytes, void* stream);
+
 /* New core (Fig. 2): G = T x_0 F_0^T ... x_{N-1} F_{N-1}^T, with the chain's
  * mode order chosen to minimise multiply-adds. */
 int tucker_core(tucker_plan_t plan, const void* T, const void* const* F, void* G, void* ws,

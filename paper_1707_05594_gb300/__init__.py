@@ -80,6 +80,8 @@ def lib():
     L.tucker_hooi_sweep_core.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _vpp, _vpp,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                          ctypes.c_void_p]
+    L.tucker_hooi_sweep_gs.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _vpp, _vpp, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
     L.tucker_norm2.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.tucker_fit.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                              ctypes.c_void_p]
@@ -268,6 +270,16 @@ def tucker_hooi_sweep(plan: Plan, T, F_in: Sequence, F_out: Sequence, ws, stream
     _check(lib().tucker_hooi_sweep(plan.handle, _dp(T, "T"), _ptrs(F_in),
                                    _ptrs(F_out), _dp(ws, "ws"), ws.numel(),
                                    _stream(stream)), "tucker_hooi_sweep")
+
+
+def tucker_hooi_sweep_gs(plan: Plan, T, F_in: Sequence, F_out: Sequence, G_out, ws, stream=None):
+    """HOOI sweep in the Gauss-Seidel form (each mode uses the factors already
+    updated in this sweep); G_out (or None) receives the core of F_out."""
+    _req(T, "T")
+    _check(lib().tucker_hooi_sweep_gs(plan.handle, _dp(T, "T"), _ptrs(F_in), _ptrs(F_out),
+                                      _dp(G_out, "G_out") if G_out is not None else None,
+                                      _dp(ws, "ws"), ws.numel(), _stream(stream)),
+           "tucker_hooi_sweep_gs")
 
 
 def tucker_hooi_sweep_core(plan: Plan, T, F_in: Sequence, F_out: Sequence, G_in, ws, stream=None):

@@ -316,6 +316,72 @@ int tucker_core(tucker_plan_t plan, const void* T, const void* const* F, void* G
   return TUCKER_OK;
 }
 
+int tucker_hooi_sweep_gs(tucker_plan_t plan, const void* T, const void* const* F_in,
+                         void* const* F_out, void* G_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!plan || !T) return fail(TUCKER_ERR_INVALID_ARG, "tucker_hooi_sweep_gs: NULL plan or T");
+  const Plan& p = plan->p;
+  int rc = check_ptrs(F_in, p.N, "tucker_hooi_sweep_gs");
+  if (rc) return rc;
+  rc = check_ptrs(const_cast<const void* const*>(F_out), p.N, "tucker_hooi_sweep_gs");
+  if (rc) return rc;
+  for (int n = 0; n < p.N; ++n)
+    for (int j = 0; j < p.N; ++j)
+      if (F_out[n] == F_in[j])
+        return fail(TUCKER_ERR_INVALID_ARG, "tucker_hooi_sweep_gs: F_out aliases F_in");
+  rc = check_ws(p, ws, ws_bytes, "tucker_hooi_sweep_gs");
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* wsb = static_cast<char*>(ws);
+  const int fdt = factor_dtype(p.dtype);
+  const int idt = p.inter_dtype();
+  // ping-pong buffers sized for the largest intermediate of any chain
+  size_t mx = 1;
+  for (int n = 0; n < p.N; ++n) {
+    unsigned P = 0;
+    for (int i = 0; i < p.N; ++i) {
+      const int m = p.core_order[(size_t)i];
+      if (m == n) continue;
+      P |= 1u << m;
+      mx = std::max(mx, (size_t)tensor_size(p, P));
+    }
+  }
+  void* buf[2] = {wsb + p.off_scratch, wsb + p.off_scratch + align_up(mx * p.inter_bytes())};
+  for (int n = 0; n < p.N; ++n) {
+    // Z_n = T x_{m != n} F_m^T with the factors of this sweep for m < n
+    // (the Gauss-Seidel form) along the core-chain order without n
+    int64_t dims[kMaxModes];
+    std::memcpy(dims, p.L, sizeof(int64_t) * (size_t)p.N);
+    const void* cur = T;
+    int cur_dt = p.dtype, step = 0;
+    for (int i = 0; i < p.N; ++i) {
+      const int m = p.core_order[(size_t)i];
+      if (m == n) continue;
+      int64_t R, L, C;
+      view3(dims, p.N, m, &R, &L, &C);
+      ProfScope prof(plan->p, s, -3, m);
+      void* out = buf[step & 1];
+      rc = launch_ttm(cur_dt, cur, R, L, C, m < n ? F_out[m] : F_in[m], p.K[m], out, idt, s);
+      if (rc) return rc;
+      dims[m] = p.K[m];
+      cur = out;
+      cur_dt = idt;
+      ++step;
+    }
+    int64_t R, L, C;
+    view3(dims, p.N, n, &R, &L, &C);
+    double* W = reinterpret_cast<double*>(wsb + p.off_gram[n]);
+    TK_CUDA_TRY(cudaMemsetAsync(W, 0, (size_t)L * (size_t)L * sizeof(double), s));
+    rc = launch_gram(cur_dt, cur, R, L, C, W, s);
+    if (rc) return rc;
+    // the new F_n, warm-started from the input factor
+    EigProblem prob{W, F_out[n], (int)p.L[n], (int)p.K[n], F_in[n]};
+    rc = launch_eig_topk(&prob, 1, fdt, wsb + p.off_eig, p.bytes_eig, s);
+    if (rc) return rc;
+  }
+  if (G_out) return tucker_core(plan, T, const_cast<const void* const*>(F_out), G_out, ws, ws_bytes, stream);
+  return TUCKER_OK;
+}
+
 int tucker_sthosvd(tucker_plan_t plan, const void* T, void* const* F, void* G, void* ws,
                    size_t ws_bytes, void* stream) {
   if (!plan || !T || !G) return fail(TUCKER_ERR_INVALID_ARG, "tucker_sthosvd: NULL argument");

@@ -260,6 +260,22 @@ void core_chain(Plan& p) {
   p.bytes_scratch = std::max(p.bytes_scratch, 2 * align_up(mx * p.inter_bytes()));
 }
 
+// Gauss-Seidel sweeps: for each n a chain over the other modes in the
+// core-chain order, in two ping-pong buffers.
+void gs_buffers(Plan& p) {
+  size_t mx = 0;
+  for (int n = 0; n < p.N; ++n) {
+    unsigned P = 0;
+    for (int i = 0; i < p.N; ++i) {
+      const int m = p.core_order[(size_t)i];
+      if (m == n) continue;
+      P |= 1u << m;
+      mx = std::max(mx, (size_t)tensor_size(p, P));
+    }
+  }
+  p.bytes_scratch = std::max(p.bytes_scratch, 2 * align_up(mx * p.inter_bytes()));
+}
+
 // STHOSVD in natural order: Y_n = T[{0..n}] in two ping-pong buffers.
 void sthosvd_buffers(Plan& p) {
   size_t mx = 0;
@@ -368,6 +384,7 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
   if (!(o.flags & TUCKER_PLAN_NO_FUSED_ROOT)) choose_fused_root(p);
   memory_plan(p);
   core_chain(p);
+  gs_buffers(p);
   sthosvd_buffers(p);
 
   // workspace layout

@@ -300,3 +300,52 @@ def test_full_size_fp32_workload(tk, orc):
     np.testing.assert_allclose(Gg, G_ref, rtol=0, atol=1e-5 * np.abs(G_ref).max())
     fit_ref = orc.fit(orc.norm2(Th), orc.norm2(G_ref))
     assert abs(fit_g - fit_ref) <= 1e-5 * fit_ref
+
+
+GS_CASES = [
+    # L, K, rho, seed, dtype: the Gauss-Seidel form against the oracle's
+    ((24, 20, 18), (4, 3, 5), 0.5, 21, torch.float32),
+    ((30, 30, 30), (6, 4, 5), 1.0, 22, torch.float32),          # hard: fit moves across sweeps
+    ((16, 12, 10, 9), (3, 4, 2, 3), 0.3, 23, torch.float32),
+    ((10, 9, 8, 7, 6), (3, 3, 2, 2, 2), 0.2, 24, torch.float32),
+    ((33, 45), (7, 7), 0.4, 25, torch.float32),                  # N = 2
+    ((20, 17, 15), (5, 4, 6), 0.6, 26, torch.float64),
+]
+
+
+@pytest.mark.parametrize("L,K,rho,seed,dtype", GS_CASES)
+def test_gauss_seidel_sweeps_match_oracle(tk, orc, L, K, rho, seed, dtype):
+    """tucker_hooi_sweep_gs (each mode uses the factors already updated in the
+    sweep) against the oracle's Gauss-Seidel sweep, from the same STHOSVD, for
+    three sweeps: fits and factor subspaces within the FP32 (FP64) bars; the
+    Gauss-Seidel fit never falls from sweep to sweep."""
+    w = workloads.planted_tucker(L, K, rho, seed, dtype=dtype)
+    T = w["T"].cuda()
+    code = tk.TUCKER_F64 if dtype == torch.float64 else tk.TUCKER_F32
+    p = tk.tucker_plan(L, K, code)
+    ws = tk.workspace(p)
+    F = [torch.empty(L[n], K[n], dtype=dtype, device="cuda") for n in range(len(L))]
+    F2 = [torch.empty_like(f) for f in F]
+    G = torch.empty(*K, dtype=dtype, device="cuda")
+    nt = torch.empty(1, dtype=torch.float64, device="cuda")
+    fo = torch.empty(2, dtype=torch.float64, device="cuda")
+    tk.tucker_norm2(p, T, nt)
+    tk.tucker_sthosvd(p, T, F, G, ws)
+    Tn = w["T"].double().numpy() if dtype == torch.float64 else w["T"].numpy()
+    Fo, _ = orc.sthosvd(Tn, K)
+    fit_bar, ang_bar = bars(dtype)
+    prev = -1.0
+    for _ in range(3):
+        tk.tucker_hooi_sweep_gs(p, T, F, F2, G, ws)
+        F, F2 = F2, F
+        tk.tucker_fit(p, G, nt, fo)
+        torch.cuda.synchronize()
+        Fo, Go = orc.hooi_sweep(Tn, Fo, K, gauss_seidel=True)
+        fit_o = orc.fit(orc.norm2(Tn), orc.norm2(Go))
+        fit_g = fo[0].item()
+        assert abs(fit_g - fit_o) <= fit_bar * fit_o, (fit_g, fit_o)
+        for n in range(len(L)):
+            if K[n] < L[n]:
+                assert sin_angle(F[n].double().cpu().numpy(), Fo[n]) <= ang_bar, n
+        assert fit_g >= prev - 1e-6
+        prev = fit_g
