@@ -243,9 +243,12 @@ int tucker_eig_topk_noalloc(int batch, const int64_t* L, const int64_t* K, const
  * tucker_hooi_sweep records a start/end event pair on its stream around each
  * tree node's launches (node = index in tucker_plan_nodes order, label = its
  * mode, or -(n+2) for the Gram of leaf n) and around the batched eigensolver
- * (node = -1), and tucker_core around each chain step (node = -2, label =
- * mode).  Recording stops when `capacity` pairs are used.  capacity = 0
- * disables profiling and frees the events. */
+ * (node = -1), tucker_core around each chain step (node = -2, label =
+ * mode) and tucker_hooi_sweep_gs around each step of its chains (node = -3,
+ * label = mode).  With a fused root the first root child's record covers
+ * both children and the second one's is empty.  Recording stops when
+ * `capacity` pairs are used.  capacity = 0 disables profiling and frees the
+ * events. */
 typedef struct {
   int32_t node;
   int32_t label;
@@ -281,8 +284,9 @@ size_t tucker_fp8_bytes(int64_t n);
 int tucker_convert_fp8(const float* x, void* out, int64_t n, void* stream);
 
 /* Kernel selection, a bit mask (process-wide; 0 is the default):
- *   bit 0 (1): every TTM on the CUDA-core kernels (otherwise BF16 tensors use
- *              the tensor-core TTM, tcgen05 + TMA, wherever the shape allows);
+ *   bit 0 (1): every TTM on the CUDA-core kernels (otherwise BF16 and FP8
+ *              tensors use the tensor-core TTMs, tcgen05 + TMA, where the
+ *              shape allows and they are faster);
  *   bit 1 (2): HOOI sweeps always run the full eigensolver (otherwise they start
  *              from the input factors: two FP64 subspace-iteration steps and an
  *              a-posteriori check, falling back to the full path on the GPU
