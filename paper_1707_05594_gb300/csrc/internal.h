@@ -68,7 +68,7 @@ struct Plan {
   }
 };
 
-// whether the fused root TTM (ttm_slab.cu) takes the two root children of
+// whether the fused root TTM (ttm_fused_root.cu) takes the two root children of
 // modes a < b of a tensor of this type and these lengths
 bool fused_root_fits(int dtype, int N, const int64_t* L, const int64_t* K, int a, int b);
 
