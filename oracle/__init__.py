@@ -66,6 +66,9 @@ def _load():
     lib.orc_sthosvd.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_void_p, ctypes.c_int,
                                 ctypes.POINTER(_dp), _dp, _dp]
     lib.orc_sthosvd.restype = ctypes.c_int
+    lib.orc_sthosvd_order.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_dp), _dp, _dp]
+    lib.orc_sthosvd_order.restype = ctypes.c_int
     lib.orc_norm2_d.argtypes = [ctypes.c_int64, _dp]
     lib.orc_norm2_d.restype = ctypes.c_double
     lib.orc_norm2_f.argtypes = [ctypes.c_int64, ctypes.c_void_p]
@@ -91,6 +94,13 @@ def _load():
     lib.orc_tree_cost.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.orc_tree_cost.restype = _u64
+    lib.orc_sthosvd_order_cost.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.c_int]
+    lib.orc_sthosvd_order_cost.restype = _u64
+    lib.orc_sthosvd_order_bruteforce.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_u64),
+                                                 ctypes.POINTER(_u64)]
+    lib.orc_sthosvd_order_bruteforce.restype = ctypes.c_int
     # FP8 E4M3 storage with per-64 scales
     lib.orc_e4m3_decode.argtypes = [ctypes.c_int]
     lib.orc_e4m3_decode.restype = ctypes.c_double
@@ -206,16 +216,29 @@ def core(T: np.ndarray, Fs: Sequence[np.ndarray]) -> np.ndarray:
     return G
 
 
-def sthosvd(T: np.ndarray, K: Sequence[int], return_evals: bool = False):
-    """STHOSVD in natural mode order.  Returns (F list, G[, per-mode eigenvalues])."""
+def sthosvd(T: np.ndarray, K: Sequence[int], return_evals: bool = False,
+            order: Sequence[int] | None = None):
+    """STHOSVD, the modes taken in natural order or in `order` (a permutation).
+
+    Returns (F list, G[, per-mode eigenvalues]); mode n's eigenvalues are those
+    of the Gram its factor came from, whatever the order."""
     lib = _load()
     L = list(T.shape)
     Fout = [np.empty((L[n], K[n]), dtype=np.float64) for n in range(len(L))]
     G = np.empty(list(K), dtype=np.float64)
-    # mode n's Gram has size (dims at step n)[n] = L[n]
+    # mode n's Gram has size L[n] (mode n still has length L[n] when it is taken)
     ev = np.empty(sum(L), dtype=np.float64)
     Tc, tp, is_f = _tensor_arg(T)
-    rc = lib.orc_sthosvd(len(L), _i64(L), _i64(K), tp, is_f, _fptrs(Fout), _dptr(G), _dptr(ev))
+    if order is None:
+        rc = lib.orc_sthosvd(len(L), _i64(L), _i64(K), tp, is_f, _fptrs(Fout), _dptr(G), _dptr(ev))
+    else:
+        if len(order) != len(L):
+            raise ValueError("order must list every mode once")
+        perm = (ctypes.c_int * len(L))(*[int(m) for m in order])
+        rc = lib.orc_sthosvd_order(len(L), _i64(L), _i64(K), tp, is_f, perm, _fptrs(Fout), _dptr(G),
+                                   _dptr(ev))
+        if rc == -2:
+            raise ValueError("order must be a permutation of the modes")
     if rc < 0:
         raise RuntimeError("oracle Jacobi eigensolver did not converge")
     if return_evals:
@@ -314,6 +337,26 @@ def tree_cost(L: Sequence[int], K: Sequence[int], labels: Sequence[int], parents
 
 
 # --------------------------------------------------------------------------
+def sthosvd_order_cost(L: Sequence[int], K: Sequence[int], order: Sequence[int], elems: bool = False) -> int:
+    """Cost of STHOSVD with the modes in `order`: multiply-adds (Gram L_m |Y| +
+    TTM K_m |Y| per step) or elements moved (2 |Y| + |Y| K_m / L_m per step)."""
+    arr = (ctypes.c_int * len(L))(*[int(m) for m in order])
+    return int(_load().orc_sthosvd_order_cost(len(L), _i64(L), _i64(K), arr, 1 if elems else 0))
+
+
+def sthosvd_order_bruteforce(L: Sequence[int], K: Sequence[int], elems: bool = False):
+    """(least cost, the lexicographically first order reaching it, natural order's cost)
+    over all N! mode orders of STHOSVD."""
+    N = len(L)
+    best = (ctypes.c_int * N)()
+    bc, nc = _u64(), _u64()
+    rc = _load().orc_sthosvd_order_bruteforce(N, _i64(L), _i64(K), 1 if elems else 0, best,
+                                              ctypes.byref(bc), ctypes.byref(nc))
+    if rc:
+        raise ValueError("N out of range")
+    return int(bc.value), list(best), int(nc.value)
+
+
 # FP8 E4M3 storage with one FP32 scale per 64 consecutive elements
 # --------------------------------------------------------------------------
 def e4m3_decode(code: int) -> float:

@@ -30,6 +30,9 @@
  *                    kept as a cross-check only.
  *   orc_sthosvd      STHOSVD (Sec. 1/2.2 cite it; standard definition):
  *                    natural mode order, Gram + EVD per mode, then truncate.
+ *   orc_sthosvd_order  the same with the modes in a given order (the
+ *                    STHOSVD order optimisation, to which Sec. 1 says the
+ *                    tree ideas carry over, picks one).
  *   orc_core         Fig. 2 "New core".
  *   orc_fit          Sec. 2.2 error "normalized root mean square":
  *                    rel = ||T - Z||_F / ||T||_F, fit = 1 - rel, using
@@ -48,6 +51,13 @@
 #ifdef _OPENMP
 #include <omp.h>
 #endif
+
+/* L_0 + ... + L_{n-1} */
+static int64_t len_sum(const int64_t* d, int n) {
+  int64_t s = 0;
+  for (int i = 0; i < n; ++i) s += d[i];
+  return s;
+}
 
 static int64_t prod_range(const int64_t* d, int a, int b) {
   int64_t p = 1;
@@ -329,11 +339,20 @@ void orc_core(int N, const int64_t* L, const int64_t* K, const void* T, int t_is
   free(G);
 }
 
-/* STHOSVD, natural mode order: Y <- T; for n: F_n <- top-K_n eigvecs of
- * Y_(n) Y_(n)^T; Y <- Y x_n F_n^T.  G <- Y.  evals_out (optional) receives,
- * for each mode, all L_n eigenvalues of its Gram, concatenated. */
-int orc_sthosvd(int N, const int64_t* L, const int64_t* K, const void* T, int t_is_float,
-                double* const* F_out, double* G_out, double* evals_out) {
+/* STHOSVD with the modes taken in the order order[0..N-1] (a permutation of
+ * 0..N-1): Y <- T; for n = order[0], order[1], ...: F_n <- top-K_n eigvecs
+ * of Y_(n) Y_(n)^T; Y <- Y x_n F_n^T.  G <- Y (modes keep their positions,
+ * so G is K_0 x ... x K_{N-1} whatever the order).  evals_out (optional)
+ * receives, for each mode n at offset L_0 + ... + L_{n-1}, all L_n
+ * eigenvalues of the Gram that mode n's factor came from.  Returns -2 when
+ * order is not a permutation. */
+int orc_sthosvd_order(int N, const int64_t* L, const int64_t* K, const void* T, int t_is_float,
+                      const int* order, double* const* F_out, double* G_out, double* evals_out) {
+  int seen[16] = {0};
+  for (int i = 0; i < N; ++i) {
+    if (order[i] < 0 || order[i] >= N || seen[order[i]]) return -2;
+    seen[order[i]] = 1;
+  }
   int64_t dims[16];
   memcpy(dims, L, sizeof(int64_t) * (size_t)N);
   const int64_t n0 = numel(dims, N);
@@ -341,13 +360,14 @@ int orc_sthosvd(int N, const int64_t* L, const int64_t* K, const void* T, int t_
   for (int64_t i = 0; i < n0; ++i)
     Y[i] = t_is_float ? (double)((const float*)T)[i] : ((const double*)T)[i];
   int rc_all = 0;
-  int64_t eoff = 0;
-  for (int n = 0; n < N; ++n) {
+  for (int i = 0; i < N; ++i) {
+    const int n = order[i];
     double* W = (double*)malloc(sizeof(double) * (size_t)(dims[n] * dims[n]));
     orc_gram(N, dims, Y, n, W);
-    int rc = topk_eigvecs(dims[n], W, K[n], F_out[n], evals_out ? evals_out + eoff : NULL);
+    double* ev = NULL;
+    if (evals_out) ev = evals_out + len_sum(L, n);
+    int rc = topk_eigvecs(dims[n], W, K[n], F_out[n], ev);
     if (rc < 0) rc_all = -1;
-    eoff += dims[n];
     free(W);
     double* nxt = NULL;
     chain_step(N, dims, Y, NULL, n, F_out[n], K[n], &nxt);
@@ -357,6 +377,14 @@ int orc_sthosvd(int N, const int64_t* L, const int64_t* K, const void* T, int t_
   memcpy(G_out, Y, sizeof(double) * (size_t)numel(K, N));
   free(Y);
   return rc_all;
+}
+
+/* STHOSVD in natural mode order 0, 1, ..., N-1. */
+int orc_sthosvd(int N, const int64_t* L, const int64_t* K, const void* T, int t_is_float,
+                double* const* F_out, double* G_out, double* evals_out) {
+  int order[16];
+  for (int n = 0; n < N; ++n) order[n] = n;
+  return orc_sthosvd_order(N, L, K, T, t_is_float, order, F_out, G_out, evals_out);
 }
 
 /* Sum of squares in double. */

@@ -267,3 +267,72 @@ u64 orc_tree_cost(int N, const int64_t* L, const int64_t* K, int n_nodes, const 
   }
   return total;
 }
+
+/* ------------------------------------------------------------------------ */
+/* STHOSVD mode order (Sec. 1 notes that the tree ideas carry over to it).  */
+/* ------------------------------------------------------------------------ */
+/* Cost of STHOSVD with the modes in `order`.  Step i takes mode m = order[i]
+ * of the current tensor Y (modes order[0..i-1] already truncated to K):
+ *   elems == 0: multiply-adds.  The Gram Y_(m) Y_(m)^T has L_m * L_m entries,
+ *               each a sum of |Y| / L_m products: L_m * |Y|; the TTM
+ *               Y x_m F_m^T costs K_m * |Y| (Sec. 3.1's node cost).
+ *   elems != 0: elements moved.  The Gram reads Y (|Y|); the TTM reads Y and
+ *               writes |Y| * K_m / L_m.
+ * Returns ORC_INF when order is not a permutation of 0..N-1. */
+u64 orc_sthosvd_order_cost(int N, const int64_t* L, const int64_t* K, const int* order, int elems) {
+  set_problem(N, L, K);
+  unsigned P = 0;
+  u64 total = 0;
+  for (int i = 0; i < N; ++i) {
+    const int m = order[i];
+    if (m < 0 || m >= N || ((P >> m) & 1u)) return ORC_INF;
+    const u64 y = tsize(P);
+    if (elems)
+      total += y + y + tsize(P | (1u << m));
+    else
+      total += g_L[m] * y + g_K[m] * y;
+    P |= 1u << m;
+  }
+  return total;
+}
+
+static int g_perm[16], g_best_perm[16];
+static u64 g_best_cost, g_nat_cost;
+static int g_elems;
+
+static void perm_rec(int i, unsigned used) {
+  if (i == g_N) {
+    int64_t L[16], K[16];
+    for (int n = 0; n < g_N; ++n) { L[n] = (int64_t)g_L[n]; K[n] = (int64_t)g_K[n]; }
+    const u64 c = orc_sthosvd_order_cost(g_N, L, K, g_perm, g_elems);
+    if (c < g_best_cost) {
+      g_best_cost = c;
+      memcpy(g_best_perm, g_perm, sizeof(int) * (size_t)g_N);
+    }
+    return;
+  }
+  for (int m = 0; m < g_N; ++m) {
+    if ((used >> m) & 1u) continue;
+    g_perm[i] = m;
+    perm_rec(i + 1, used | (1u << m));
+  }
+}
+
+/* Every order of the N modes (N! of them, lexicographic): the least cost, an
+ * order reaching it (the lexicographically first), and the natural order's
+ * cost. */
+int orc_sthosvd_order_bruteforce(int N, const int64_t* L, const int64_t* K, int elems, int* best_order,
+                                 u64* best_cost, u64* natural_cost) {
+  if (N < 1 || N > 9) return -1;
+  int nat[16];
+  for (int n = 0; n < N; ++n) nat[n] = n;
+  g_nat_cost = orc_sthosvd_order_cost(N, L, K, nat, elems);
+  set_problem(N, L, K);
+  g_elems = elems;
+  g_best_cost = ORC_INF;
+  perm_rec(0, 0u);
+  memcpy(best_order, g_best_perm, sizeof(int) * (size_t)N);
+  *best_cost = g_best_cost;
+  *natural_cost = g_nat_cost;
+  return 0;
+}

@@ -255,6 +255,61 @@ def test_sthosvd_singular_values_of_unfolding(orc):
     np.testing.assert_allclose(evs[0], s ** 2, rtol=1e-11)
 
 
+@pytest.mark.parametrize("order", [(2, 0, 3, 1), (3, 2, 1, 0), (0, 1, 2, 3)])
+def test_sthosvd_order_steps_match_eigh(orc, order):
+    """STHOSVD in a given mode order, step by step against numpy: the tensor
+    before step i is T times the factors of the modes taken earlier (built
+    here by unfolding products, Sec. 2.1); mode m's factor spans the leading
+    K_m eigenvectors of that tensor's mode-m Gram (numpy eigh), its reported
+    eigenvalues are that Gram's, and G is the final tensor.  The discarded
+    eigenvalues then add up to ||T||^2 - ||G||^2 (each step removes exactly the
+    energy outside the kept subspace), whatever the order."""
+    L, K = (7, 5, 6, 4), (3, 2, 4, 2)
+    X = rng.standard_normal(L)
+    F, G, evs = orc.sthosvd(X, K, return_evals=True, order=order)
+    Y = X.copy()
+    discarded = 0.0
+    for m in order:
+        Ym = unfold(Y, m)
+        w, V = np.linalg.eigh(Ym @ Ym.T)
+        w, V = w[::-1], V[:, ::-1]
+        np.testing.assert_allclose(evs[m], w, rtol=1e-10, atol=1e-10 * w[0])
+        assert sin_angle(F[m], V[:, :K[m]]) < 1e-9, m
+        np.testing.assert_allclose(F[m].T @ F[m], np.eye(K[m]), atol=1e-12)
+        discarded += w[K[m]:].sum()
+        Y = ttm_by_unfolding(Y, m, F[m].T)
+    np.testing.assert_allclose(G, Y, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(orc.norm2(X) - orc.norm2(G), discarded, rtol=1e-9)
+
+
+def test_sthosvd_order_is_honoured_and_natural_is_default(orc):
+    """The natural order given explicitly is the default call bit for bit; a
+    different order gives a different (valid) decomposition on a generic
+    tensor: the factor of a mode taken late differs from the one taken first."""
+    L, K = (7, 5, 6), (3, 2, 2)
+    X = rng.standard_normal(L)
+    F0, G0 = orc.sthosvd(X, K)
+    F1, G1 = orc.sthosvd(X, K, order=(0, 1, 2))
+    assert all(np.array_equal(a, b) for a, b in zip(F0, F1)) and np.array_equal(G0, G1)
+    F2, G2 = orc.sthosvd(X, K, order=(2, 1, 0))
+    assert sin_angle(F2[0], F0[0]) > 1e-3
+    with pytest.raises(ValueError):
+        orc.sthosvd(X, K, order=(0, 0, 1))
+
+
+def test_sthosvd_any_order_recovers_exact_rank(orc):
+    """Zero noise, exact multilinear rank K: every order reproduces T and
+    finds the planted subspaces."""
+    L, K = (12, 10, 9), (3, 4, 2)
+    T, Fp, _ = planted(L, K, 0.0, 11)
+    nT2 = orc.norm2(T)
+    for order in [(1, 2, 0), (2, 0, 1)]:
+        F, G = orc.sthosvd(T, K, order=order)
+        for n in range(3):
+            assert sin_angle(F[n], Fp[n]) < 1e-12
+        assert orc.residual(T, G, F) < 1e-12 * math.sqrt(nT2)
+
+
 # --------------------------------------------------------------------------
 # FP8 E4M3 storage with per-64 scales (the precision form's FP8 variant)
 # --------------------------------------------------------------------------

@@ -91,3 +91,33 @@ def test_tree_validator(orc):
     bad = list(parents)
     bad[7] = 2  # leaf F3 under a path that lacks mode 1
     assert orc.tree_cost((2, 3, 4), (1, 2, 3), labels, bad) is None
+
+
+# ----------------------------------------------------- STHOSVD mode order ----
+GOLD_STH = os.path.join(os.path.dirname(__file__), "golden", "sthosvd_order_costs.json")
+
+
+def test_sthosvd_order_hand_derived_costs(orc):
+    """Every order of three hand-worked cases (multiply-adds and elements
+    moved), and the brute-force optimum, against the written-out derivations;
+    the third case has different optima under the two objectives."""
+    for case in json.load(open(GOLD_STH))["cases"]:
+        L, K = case["L"], case["K"]
+        for key, elems in (("macs", False), ("elems", True)):
+            for order, cost in case[key].items():
+                assert orc.sthosvd_order_cost(L, K, [int(m) for m in order.split(",")], elems) == cost
+            best, arg, nat = orc.sthosvd_order_bruteforce(L, K, elems)
+            assert [best, arg] == case["best_" + key]
+            assert nat == case[key][",".join(str(n) for n in range(len(L)))]
+
+
+def test_sthosvd_order_cost_properties(orc):
+    """Symmetric shapes cost the same in every order; a non-permutation is
+    rejected; the step cost is the sum of a Gram and a TTM, so with K = L (no
+    truncation) every order costs N * 2 * L * |T| when all L are equal."""
+    import itertools
+    L, K = (6, 6, 6, 6), (2, 2, 2, 2)
+    costs = {orc.sthosvd_order_cost(L, K, p) for p in itertools.permutations(range(4))}
+    assert len(costs) == 1
+    assert orc.sthosvd_order_cost(L, K, [0, 0, 1, 2]) == 2 ** 64 - 1
+    assert orc.sthosvd_order_cost((5, 5, 5), (5, 5, 5), [2, 0, 1]) == 3 * 2 * 5 * 125
