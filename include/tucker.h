@@ -86,6 +86,16 @@ typedef struct {
  * Results are those of the two separate TTMs (same order of summation). */
 #define TUCKER_PLAN_NO_FUSED_ROOT 1
 
+/* Plan flag: let tucker_sthosvd take the modes in the order of least cost
+ * instead of 0, 1, ..., N-1 (Sec. 1 notes that the tree ideas carry over to
+ * STHOSVD).  The step on mode m of the current tensor Y costs L_m*|Y| (its
+ * Gram) + K_m*|Y| (its TTM) multiply-adds, or 2*|Y| + |Y|*K_m/L_m elements
+ * moved under TUCKER_COST_ELEMS; the order minimising the sum is found by a
+ * DP over the set of modes already truncated, the natural order being kept
+ * whenever it is optimal.  A different order gives different (equally valid)
+ * STHOSVD factors; see tucker_plan_sthosvd. */
+#define TUCKER_PLAN_STHOSVD_ORDER 2
+
 typedef struct tucker_plan_s* tucker_plan_t;
 
 /* One node of a plan's TTM-tree, in depth-first pre-order (root first).
@@ -128,11 +138,18 @@ int tucker_plan_nodes(tucker_plan_t plan, tucker_node_t* nodes, int capacity, in
  * when the root is not fused.  Host only. */
 int tucker_plan_fused_root(tucker_plan_t plan, int* first, int* second);
 
+/* The mode order tucker_sthosvd takes (order: N ints, written) and its cost
+ * under the plan's cost model (cost may be NULL): natural unless the plan was
+ * made with TUCKER_PLAN_STHOSVD_ORDER.  Host only. */
+int tucker_plan_sthosvd(tucker_plan_t plan, int* order, uint64_t* cost);
+
 void tucker_plan_destroy(tucker_plan_t plan);
 
-/* STHOSVD initial decomposition (Sec. 2.2 cites it; natural mode order):
- * for n = 0..N-1, F_n <- leading K_n eigenvectors of Y_(n) Y_(n)^T and
- * Y <- Y x_n F_n^T, starting from Y = T; G <- Y.  F: N device pointers. */
+/* STHOSVD initial decomposition (Sec. 2.2 cites it): for n in the plan's
+ * STHOSVD order (natural unless TUCKER_PLAN_STHOSVD_ORDER),
+ * F_n <- leading K_n eigenvectors of Y_(n) Y_(n)^T and Y <- Y x_n F_n^T,
+ * starting from Y = T; G <- Y (K_0 x ... x K_{N-1} whatever the order).
+ * F: N device pointers. */
 int tucker_sthosvd(tucker_plan_t plan, const void* T, void* const* F, void* G, void* ws,
                    size_t ws_bytes, void* stream);
 

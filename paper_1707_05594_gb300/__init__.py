@@ -23,6 +23,7 @@ TUCKER_F32, TUCKER_F64, TUCKER_BF16, TUCKER_FP8_E4M3 = 0, 1, 2, 3
 TREE_OPTIMAL, TREE_CHAIN, TREE_CHAIN_K, TREE_CHAIN_H, TREE_BALANCED = 0, 1, 2, 3, 4
 COST_MACS, COST_ELEMS = 0, 1
 PLAN_NO_FUSED_ROOT = 1
+PLAN_STHOSVD_ORDER = 2
 ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "WORKSPACE", -4: "CUDA", -5: "TIMEOUT",
           -6: "NONFINITE"}
 
@@ -67,6 +68,7 @@ def lib():
                                    ctypes.POINTER(ctypes.c_size_t)]
     L.tucker_plan_fused_root.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]
+    L.tucker_plan_sthosvd.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), _u64p]
     L.tucker_plan_nodes.argtypes = [ctypes.c_void_p, ctypes.POINTER(Node), ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int)]
     L.tucker_plan_destroy.argtypes = [ctypes.c_void_p]
@@ -216,9 +218,10 @@ class Plan:
 
 def tucker_plan(L: Sequence[int], K: Sequence[int], dtype: int = TUCKER_F32,
                 tree: int = TREE_OPTIMAL, cost_model: int = COST_MACS,
-                fuse_root: bool = True) -> Plan:
+                fuse_root: bool = True, sthosvd_order: bool = False) -> Plan:
     h = ctypes.c_void_p()
-    opts = PlanOpts(dtype, tree, cost_model, 0 if fuse_root else PLAN_NO_FUSED_ROOT)
+    flags = (0 if fuse_root else PLAN_NO_FUSED_ROOT) | (PLAN_STHOSVD_ORDER if sthosvd_order else 0)
+    opts = PlanOpts(dtype, tree, cost_model, flags)
     _check(lib().tucker_plan(len(L), _i64(L), _i64(K), ctypes.byref(opts), ctypes.byref(h)),
            "tucker_plan")
     return Plan(h, tuple(int(x) for x in L), tuple(int(x) for x in K), dtype, tree)
@@ -230,6 +233,14 @@ def tucker_plan_fused_root(plan: Plan):
     _check(lib().tucker_plan_fused_root(plan.handle, ctypes.byref(a), ctypes.byref(b)),
            "tucker_plan_fused_root")
     return None if a.value < 0 else (a.value, b.value)
+
+
+def tucker_plan_sthosvd(plan: Plan):
+    """(mode order of tucker_sthosvd, its cost under the plan's cost model)."""
+    order = (ctypes.c_int * plan.N)()
+    cost = ctypes.c_uint64()
+    _check(lib().tucker_plan_sthosvd(plan.handle, order, ctypes.byref(cost)), "tucker_plan_sthosvd")
+    return list(order), cost.value
 
 
 def tucker_plan_cost(plan: Plan):
@@ -473,11 +484,11 @@ class Decomposition:
     core and the cached ||T||^2 on one device.  Every step calls the library."""
 
     def __init__(self, T, K: Sequence[int], tree: int = TREE_OPTIMAL,
-                 cost_model: int = COST_MACS):
+                 cost_model: int = COST_MACS, sthosvd_order: bool = False):
         import torch
         self.T = T
         self.code = _dtype_code(T)
-        self.plan = tucker_plan(T.shape, K, self.code, tree, cost_model)
+        self.plan = tucker_plan(T.shape, K, self.code, tree, cost_model, sthosvd_order=sthosvd_order)
         self.ws = workspace(self.plan, T.device)
         fdt = self.plan.factor_dtype
         L = T.shape

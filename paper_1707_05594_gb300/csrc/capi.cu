@@ -395,8 +395,8 @@ int tucker_sthosvd(tucker_plan_t plan, const void* T, void* const* F, void* G, v
   const int fdt = factor_dtype(p.dtype);
   size_t mx = 0;
   unsigned P = 0;
-  for (int n = 0; n < p.N; ++n) {
-    P |= 1u << n;
+  for (int i = 0; i < p.N; ++i) {
+    P |= 1u << p.sth_order[(size_t)i];
     mx = std::max(mx, (size_t)tensor_size(p, P));
   }
   void* buf[2] = {wsb + p.off_scratch, wsb + p.off_scratch + align_up(mx * p.inter_bytes())};
@@ -404,7 +404,8 @@ int tucker_sthosvd(tucker_plan_t plan, const void* T, void* const* F, void* G, v
   std::memcpy(dims, p.L, sizeof(int64_t) * (size_t)p.N);
   const void* cur = T;
   int cur_dt = p.dtype;
-  for (int n = 0; n < p.N; ++n) {
+  for (int i = 0; i < p.N; ++i) {
+    const int n = p.sth_order[(size_t)i];
     int64_t R, L, C;
     view3(dims, p.N, n, &R, &L, &C);
     double* W = reinterpret_cast<double*>(wsb + p.off_gram[n]);
@@ -414,8 +415,8 @@ int tucker_sthosvd(tucker_plan_t plan, const void* T, void* const* F, void* G, v
     EigProblem pr{W, F[n], (int)L, (int)p.K[n]};
     rc = launch_eig_topk(&pr, 1, fdt, wsb + p.off_eig, p.bytes_eig, s);
     if (rc) return rc;
-    void* out = (n == p.N - 1) ? G : buf[n & 1];
-    const int out_dt = (n == p.N - 1) ? fdt : p.inter_dtype();
+    void* out = (i == p.N - 1) ? G : buf[i & 1];
+    const int out_dt = (i == p.N - 1) ? fdt : p.inter_dtype();
     rc = launch_ttm(cur_dt, cur, R, L, C, F[n], p.K[n], out, out_dt, s);
     if (rc) return rc;
     dims[n] = p.K[n];

@@ -40,6 +40,8 @@ struct Plan {
   uint64_t tree_macs = 0, tree_elems = 0;
   std::vector<int> core_order;  // mode order of the new-core chain
   uint64_t core_macs = 0;
+  std::vector<int> sth_order;   // mode order of tucker_sthosvd
+  uint64_t sth_cost = 0;        // its cost under cost_model (Gram + TTM per step)
 
   // workspace layout (byte offsets)
   size_t off_scratch = 0, bytes_scratch = 0;  // tree intermediates / chains

@@ -276,12 +276,55 @@ void gs_buffers(Plan& p) {
   p.bytes_scratch = std::max(p.bytes_scratch, 2 * align_up(mx * p.inter_bytes()));
 }
 
-// STHOSVD in natural order: Y_n = T[{0..n}] in two ping-pong buffers.
-void sthosvd_buffers(Plan& p) {
+// Cost of one STHOSVD step on mode m of T[P] (the modes of P already
+// truncated): the Gram Y_(m) Y_(m)^T (L_m * |Y| multiply-adds, reading Y)
+// and the TTM Y x_m F_m^T (K_m * |Y|, reading Y and writing T[P + m]).
+uint64_t sthosvd_step_cost(const Plan& p, unsigned P, int m) {
+  const uint64_t y = tensor_size(p, P);
+  if (p.cost_model == TUCKER_COST_ELEMS) return 2 * y + tensor_size(p, P | (1u << m));
+  return (uint64_t)(p.L[m] + p.K[m]) * y;
+}
+
+// STHOSVD mode order: natural, or (TUCKER_PLAN_STHOSVD_ORDER) the order of
+// least cost by a DP over the set S of modes already truncated -- the cost of
+// a step depends only on S and the mode taken, as a TTM-tree node's does on
+// (P, n).  Among equal-cost orders the higher mode goes last, so the natural
+// order is kept whenever it is optimal.  Y then lives in two ping-pong
+// buffers sized for the largest tensor after a step (the last one is G).
+void sthosvd_order(Plan& p, bool optimise) {
+  const int N = p.N;
+  const unsigned full = (1u << N) - 1u;
+  p.sth_order.assign((size_t)N, 0);
+  for (int n = 0; n < N; ++n) p.sth_order[(size_t)n] = n;
+  if (optimise) {
+    std::vector<uint64_t> best((size_t)1 << N, kInf);
+    std::vector<int> last((size_t)1 << N, -1);
+    best[0] = 0;
+    for (unsigned S = 1; S <= full; ++S) {
+      for (int m = N - 1; m >= 0; --m) {
+        if (!((S >> m) & 1u)) continue;
+        const unsigned prev = S & ~(1u << m);
+        if (best[prev] == kInf) continue;
+        const uint64_t v = best[prev] + sthosvd_step_cost(p, prev, m);
+        if (v < best[S]) {
+          best[S] = v;
+          last[S] = m;
+        }
+      }
+    }
+    unsigned S = full;
+    for (int i = N - 1; i >= 0; --i) {
+      p.sth_order[(size_t)i] = last[S];
+      S &= ~(1u << last[S]);
+    }
+  }
+  p.sth_cost = 0;
   size_t mx = 0;
   unsigned P = 0;
-  for (int n = 0; n < p.N; ++n) {
-    P |= 1u << n;
+  for (int i = 0; i < N; ++i) {
+    const int m = p.sth_order[(size_t)i];
+    p.sth_cost += sthosvd_step_cost(p, P, m);
+    P |= 1u << m;
     mx = std::max(mx, (size_t)tensor_size(p, P));
   }
   p.bytes_scratch = std::max(p.bytes_scratch, 2 * align_up(mx * p.inter_bytes()));
@@ -322,7 +365,7 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown tree kind");
   if (o.cost_model != TUCKER_COST_MACS && o.cost_model != TUCKER_COST_ELEMS)
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown cost model");
-  if (o.flags & ~TUCKER_PLAN_NO_FUSED_ROOT)
+  if (o.flags & ~(TUCKER_PLAN_NO_FUSED_ROOT | TUCKER_PLAN_STHOSVD_ORDER))
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown flags");
   long double total = 1;
   for (int n = 0; n < N; ++n) {
@@ -385,7 +428,7 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
   memory_plan(p);
   core_chain(p);
   gs_buffers(p);
-  sthosvd_buffers(p);
+  sthosvd_order(p, (o.flags & TUCKER_PLAN_STHOSVD_ORDER) != 0);
 
   // workspace layout
   size_t off = 0;
@@ -438,6 +481,13 @@ int tucker_plan_fused_root(tucker_plan_t plan, int* first, int* second) {
   if (!plan || !first || !second) return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan_fused_root: NULL argument");
   *first = plan->p.fused_u1;
   *second = plan->p.fused_u2;
+  return TUCKER_OK;
+}
+
+int tucker_plan_sthosvd(tucker_plan_t plan, int* order, uint64_t* cost) {
+  if (!plan || !order) return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan_sthosvd: NULL argument");
+  for (int i = 0; i < plan->p.N; ++i) order[i] = plan->p.sth_order[(size_t)i];
+  if (cost) *cost = plan->p.sth_cost;
   return TUCKER_OK;
 }
 

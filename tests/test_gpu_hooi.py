@@ -349,3 +349,49 @@ def test_gauss_seidel_sweeps_match_oracle(tk, orc, L, K, rho, seed, dtype):
                 assert sin_angle(F[n].double().cpu().numpy(), Fo[n]) <= ang_bar, n
         assert fit_g >= prev - 1e-6
         prev = fit_g
+
+
+STH_ORDER_CASES = [
+    # L, K, rho, seed, dtype: shapes whose cheapest STHOSVD order is not the
+    # natural one (the planner's order is checked against that below)
+    ((40, 12, 30, 25), (3, 10, 4, 20), 0.3, 51, torch.float32),
+    ((36, 8, 5, 30, 6), (4, 2, 5, 6, 3), 0.2, 53, torch.float32),
+    ((40, 12, 30, 25), (3, 10, 4, 20), 0.3, 54, torch.float64),
+]
+
+
+@pytest.mark.parametrize("L,K,rho,seed,dtype", STH_ORDER_CASES)
+def test_sthosvd_in_planned_order_matches_oracle(tk, orc, L, K, rho, seed, dtype):
+    """tucker_sthosvd with TUCKER_PLAN_STHOSVD_ORDER takes the modes in the
+    planner's order: factors and core against the oracle's STHOSVD in that
+    order (principal angles, core entries after sign alignment, fit), then
+    one HOOI sweep from them."""
+    w = workloads.planted_tucker(L, K, rho, seed, dtype=dtype)
+    T = w["T"]
+    Tn = T.numpy()
+    d = tk.Decomposition(T.cuda(), K, sthosvd_order=True)
+    order, cost = tk.tucker_plan_sthosvd(d.plan)
+    best, _, nat = orc.sthosvd_order_bruteforce(L, K)
+    assert order != list(range(len(L))) and cost == best < nat
+    d.sthosvd()
+    Fg = [f.double().cpu().numpy() for f in d.F]
+    Gg = d.G.double().cpu().numpy()
+    fit_g = d.fit()
+    Fo, Go = orc.sthosvd(Tn, K, order=order)
+    fit_bar, ang_bar = bars(dtype)
+    nT2 = orc.norm2(Tn)
+    fit_o = orc.fit(nT2, orc.norm2(Go))
+    assert abs(fit_g - fit_o) <= fit_bar * abs(fit_o), (fit_g, fit_o)
+    for n in range(len(L)):
+        if K[n] < L[n]:
+            assert sin_angle(Fg[n], Fo[n]) <= ang_bar, n
+    # the core follows the factors' signs: compare it after aligning them
+    Fa = align_signs(Fg, Fo)
+    Ga = orc.core(Tn, Fa)
+    assert np.abs(Ga - Go).max() <= (1e-7 if dtype == torch.float64 else 1e-3) * np.abs(Go).max()
+    assert abs(orc.norm2(Gg) - orc.norm2(Go)) <= fit_bar * orc.norm2(Go)
+    d.sweep()
+    F1o, _ = orc.hooi_sweep(Tn, Fo, K)
+    for n in range(len(L)):
+        if K[n] < L[n]:
+            assert sin_angle(d.F[n].double().cpu().numpy(), F1o[n]) <= ang_bar, n

@@ -1,6 +1,7 @@
 """CPU-side checks of the library: it loads, exports every symbol declared in
 include/tucker.h, and its host planner (no device work) agrees with the
 planner oracle.  No kernel is launched here."""
+import math
 import os
 import random
 import re
@@ -195,7 +196,7 @@ def test_plan_flags_validated(tk):
     h = ctypes.c_void_p()
     L = (tk._i64((8, 4, 4)))
     K = (tk._i64((3, 2, 2)))
-    opts = tk.PlanOpts(tk.TUCKER_F32, tk.TREE_OPTIMAL, tk.COST_MACS, 2)
+    opts = tk.PlanOpts(tk.TUCKER_F32, tk.TREE_OPTIMAL, tk.COST_MACS, 4)
     assert tk.lib().tucker_plan(3, L, K, ctypes.byref(opts), ctypes.byref(h)) == -1
     # no fused root where the trailing block is too large (200^4: 64 MB)
     assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (20,) * 4)) is None
@@ -212,6 +213,50 @@ def test_elems_cost_model(tk, orc):
         assert cm["tree_macs"] <= ce["tree_macs"]
         labels, parents, _ = tree_of(tk, pe)
         assert orc.tree_cost(L, K, labels, parents) == ce["tree_macs"]
+
+
+def test_sthosvd_order_matches_bruteforce(tk, orc):
+    """The planner's STHOSVD order (DP over the set of truncated modes) reaches
+    the least cost of all N! orders, under both objectives; its reported cost
+    is the oracle's cost of the order it returns; natural order whenever that
+    is optimal, and always without the flag."""
+    # shapes the planner accepts (K_n <= product of the other K); the brute
+    # force itself is pinned to hand-derived costs in the planner-oracle tests
+    cases = [((10, 2, 10), (2, 1, 2)), ((10, 2, 10, 7), (6, 1, 2, 3)), ((40, 12, 30, 25), (3, 10, 4, 20)),
+             ((672, 672, 33, 627), (279, 279, 29, 153)), ((200,) * 4, (20,) * 4)]
+    rnd = random.Random(11)
+    for _ in range(60):
+        N = rnd.choice([2, 3, 4, 5, 6])
+        L = [rnd.choice([2, 3, 5, 8, 13, 40, 97]) for _ in range(N)]
+        K = [rnd.randint(1, l) for l in L]
+        if all(K[n] <= math.prod(K) // K[n] for n in range(N)):
+            cases.append((L, K))
+    for L, K in cases:
+        for cm, elems in ((tk.COST_MACS, False), (tk.COST_ELEMS, True)):
+            best, _, nat = orc.sthosvd_order_bruteforce(L, K, elems)
+            order, cost = tk.tucker_plan_sthosvd(tk.tucker_plan(L, K, cost_model=cm, sthosvd_order=True))
+            assert sorted(order) == list(range(len(L)))
+            assert cost == best == orc.sthosvd_order_cost(L, K, order, elems), (L, K, elems)
+            if nat == best:
+                assert order == list(range(len(L))), (L, K, elems, order)
+            order0, cost0 = tk.tucker_plan_sthosvd(tk.tucker_plan(L, K, cost_model=cm))
+            assert order0 == list(range(len(L))) and cost0 == nat
+    assert sum(1 for L, K in cases if orc.sthosvd_order_bruteforce(L, K)[2] >
+               orc.sthosvd_order_bruteforce(L, K)[0]) >= 10
+
+
+def test_sthosvd_order_workspace_covers_the_order(tk):
+    """The workspace of a plan with an optimised STHOSVD order holds two
+    buffers of the largest tensor after any step of that order."""
+    L, K = (10, 2, 10, 7), (6, 1, 2, 3)
+    p = tk.tucker_plan(L, K, sthosvd_order=True)
+    order, _ = tk.tucker_plan_sthosvd(p)
+    assert order != [0, 1, 2, 3]
+    mx, P = 0, set()
+    for m in order[:-1]:
+        P.add(m)
+        mx = max(mx, math.prod(K[n] if n in P else L[n] for n in range(4)))
+    assert tk.tucker_plan_cost(p)["ws_bytes"] >= 2 * 4 * mx
 
 
 def test_batch_plan_layout(tk):
