@@ -364,8 +364,8 @@ STH_ORDER_CASES = [
 def test_sthosvd_in_planned_order_matches_oracle(tk, orc, L, K, rho, seed, dtype):
     """tucker_sthosvd with TUCKER_PLAN_STHOSVD_ORDER takes the modes in the
     planner's order: factors and core against the oracle's STHOSVD in that
-    order (principal angles, core entries after sign alignment, fit), then
-    one HOOI sweep from them."""
+    order (principal angles, fit and ||G||^2; G is the core of the returned
+    factors), then one HOOI sweep from them."""
     w = workloads.planted_tucker(L, K, rho, seed, dtype=dtype)
     T = w["T"]
     Tn = T.numpy()
@@ -385,10 +385,12 @@ def test_sthosvd_in_planned_order_matches_oracle(tk, orc, L, K, rho, seed, dtype
     for n in range(len(L)):
         if K[n] < L[n]:
             assert sin_angle(Fg[n], Fo[n]) <= ang_bar, n
-    # the core follows the factors' signs: compare it after aligning them
-    Fa = align_signs(Fg, Fo)
-    Ga = orc.core(Tn, Fa)
-    assert np.abs(Ga - Go).max() <= (1e-7 if dtype == torch.float64 else 1e-3) * np.abs(Go).max()
+    # G is the core of the GPU's own factors (T x_n F_n^T over every mode, in
+    # any order), and its energy is the oracle's; entries are not compared
+    # with the oracle's, since single eigenvectors may turn inside the kept
+    # subspace by (eigensolver residual) / (eigenvalue gap)
+    Gc = orc.core(Tn, Fg)
+    assert np.abs(Gg - Gc).max() <= (1e-10 if dtype == torch.float64 else 1e-4) * np.abs(Gc).max()
     assert abs(orc.norm2(Gg) - orc.norm2(Go)) <= fit_bar * orc.norm2(Go)
     d.sweep()
     F1o, _ = orc.hooi_sweep(Tn, Fo, K)
