@@ -170,7 +170,8 @@ def run_planner(args):
     in K-order and h-order, balanced tree), over the benchmark metadata of
     Sec. 6 -- every multiset of N modes with L_n in {20, 50, 100, 400} and
     K_n = L_n / c, c in {1.25, 2, 5, 10}, |T| <= 8e9 -- and the three real
-    tensors of Table 2.  Host only (the planner needs metadata alone)."""
+    tensors of Table 2; and the STHOSVD cost in natural mode order against the
+    least-cost order.  Host only (the planner needs metadata alone)."""
     import itertools
     import statistics as st
 
@@ -187,10 +188,16 @@ def run_planner(args):
             out[name] = tk.tucker_plan_cost(p)["tree_macs"]
         return out
 
+    def sth_gain(L, K):
+        # STHOSVD multiply-adds (Gram + TTM per step): natural order / least-cost order
+        nat = tk.tucker_plan_sthosvd(tk.tucker_plan(L, K))[1]
+        return nat / tk.tucker_plan_sthosvd(tk.tucker_plan(L, K, sthosvd_order=True))[1]
+
     modes = [(L, int(round(L / c))) for L in (20, 50, 100, 400) for c in (1.25, 2, 5, 10)]
     res = {}
     for N in (5, 6):
         ratios_best, ratios = [], {k: [] for k in kinds}
+        sth_ratios = []
         skipped = 0
         t0 = time.perf_counter()
         for combo in itertools.combinations_with_replacement(range(len(modes)), N):
@@ -206,12 +213,15 @@ def run_planner(args):
             for k in kinds:
                 ratios[k].append(ld[k] / ld["opt"])
             ratios_best.append(min(ld[k] for k in kinds) / ld["opt"])
+            sth_ratios.append(sth_gain(L, K))
         res[f"{N}D"] = {
             "tensors": len(ratios_best), "skipped_rank_deficient": skipped,
             "best_prior_over_opt": {"median": round(st.median(ratios_best), 3),
                                     "max": round(max(ratios_best), 3),
                                     "min": round(min(ratios_best), 3)},
             **{f"{k}_over_opt_median": round(st.median(v), 3) for k, v in ratios.items()},
+            "sthosvd_natural_over_opt_order": {"median": round(st.median(sth_ratios), 3),
+                                               "max": round(max(sth_ratios), 3)},
             "seconds": round(time.perf_counter() - t0, 2)}
     real = {"HCCI": ((672, 672, 627, 16), (279, 279, 153, 14)),
             "TJLR": ((460, 700, 360, 16, 4), (306, 232, 239, 16, 4)),
@@ -228,6 +238,9 @@ def run_planner(args):
         res["real"][name]["elems_per_T"] = {"mac_optimal_tree": round(cm["tree_elems"] / T, 3),
                                             "elems_optimal_tree": round(ce["tree_elems"] / T, 3)}
         res["real"][name]["macs_elems_tree_over_mac_tree"] = round(ce["tree_macs"] / cm["tree_macs"], 3)
+        order, _ = tk.tucker_plan_sthosvd(tk.tucker_plan(list(L), list(K), sthosvd_order=True))
+        res["real"][name]["sthosvd"] = {"opt_order": order,
+                                        "natural_over_opt_order": round(sth_gain(list(L), list(K)), 3)}
     return {"metric": "TTM-tree computational load, prior trees / optimal tree (Sec. 3, Sec. 6 benchmark)",
             "paper_reports": "up to 2.8x (5D) and 3.6x (6D) lower load than the best prior algorithm",
             "enumeration": "multisets of modes (the paper's counts 1134 / 642 are not reproduced by "
