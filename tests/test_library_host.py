@@ -245,6 +245,15 @@ def test_sthosvd_order_matches_bruteforce(tk, orc):
                orc.sthosvd_order_bruteforce(L, K)[0]) >= 10
 
 
+def test_plan_sthosvd_rejects_null(tk):
+    import ctypes
+    order = (ctypes.c_int * 4)()
+    assert tk.lib().tucker_plan_sthosvd(None, order, None) == -1
+    p = tk.tucker_plan((10, 2, 10, 7), (6, 1, 2, 3))
+    assert tk.lib().tucker_plan_sthosvd(p.handle, None, None) == -1
+    assert tk.lib().tucker_plan_sthosvd(p.handle, order, None) == 0 and list(order) == [0, 1, 2, 3]
+
+
 def test_sthosvd_order_workspace_covers_the_order(tk):
     """The workspace of a plan with an optimised STHOSVD order holds two
     buffers of the largest tensor after any step of that order."""
