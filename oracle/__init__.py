@@ -85,6 +85,12 @@ def _load():
     lib.orc_tree_bruteforce.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.POINTER(_u64),
                                         ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
     lib.orc_tree_bruteforce.restype = ctypes.c_int
+    lib.orc_tree_bruteforce_model.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, ctypes.POINTER(_u64),
+                                              ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
+    lib.orc_tree_bruteforce_model.restype = ctypes.c_int
+    lib.orc_tree_cost_model.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    lib.orc_tree_cost_model.restype = _u64
     lib.orc_tree_dp.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int]
     lib.orc_tree_dp.restype = _u64
     lib.orc_chain_cost.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.POINTER(ctypes.c_int)]
@@ -288,12 +294,13 @@ def residual(T: np.ndarray, G: np.ndarray, Fs: Sequence[np.ndarray]) -> float:
 # --------------------------------------------------------------------------
 # Sec. 3 planner oracle
 # --------------------------------------------------------------------------
-def tree_bruteforce(L: Sequence[int], K: Sequence[int]):
-    """Enumerate every TTM-tree: (count, min cost, max cost) in MACs."""
+def tree_bruteforce(L: Sequence[int], K: Sequence[int], elems: bool = False):
+    """Enumerate every TTM-tree: (count, min cost, max cost) in MACs, or in
+    elements moved (|In| + |Out| per internal node) with elems=True."""
     lib = _load()
     c, mn, mx = _u64(), _u64(), _u64()
-    rc = lib.orc_tree_bruteforce(len(L), _i64(L), _i64(K), ctypes.byref(c), ctypes.byref(mn),
-                                 ctypes.byref(mx))
+    rc = lib.orc_tree_bruteforce_model(len(L), _i64(L), _i64(K), 1 if elems else 0, ctypes.byref(c),
+                                       ctypes.byref(mn), ctypes.byref(mx))
     if rc != 0:
         raise ValueError("brute force supports 2 <= N <= 6")
     return c.value, mn.value, mx.value
@@ -327,12 +334,14 @@ def balanced_cost(L: Sequence[int], K: Sequence[int], order: Sequence[int] | Non
     return int(_load().orc_balanced_cost(len(L), _i64(L), _i64(K), arr))
 
 
-def tree_cost(L: Sequence[int], K: Sequence[int], labels: Sequence[int], parents: Sequence[int]):
-    """Validate a tree (Sec. 3.1 properties i-iv) and return its cost, or None."""
+def tree_cost(L: Sequence[int], K: Sequence[int], labels: Sequence[int], parents: Sequence[int],
+              elems: bool = False):
+    """Validate a tree (Sec. 3.1 properties i-iv) and return its cost (MACs, or
+    elements moved with elems=True), or None."""
     n = len(labels)
     la = (ctypes.c_int * n)(*labels)
     pa = (ctypes.c_int * n)(*parents)
-    r = int(_load().orc_tree_cost(len(L), _i64(L), _i64(K), n, la, pa))
+    r = int(_load().orc_tree_cost_model(len(L), _i64(L), _i64(K), n, la, pa, 1 if elems else 0))
     return None if r == ORC_INF else r
 
 

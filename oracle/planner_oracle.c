@@ -12,6 +12,8 @@
  *   Sec. 3.1 "Computational Load": a node u labelled n costs K_n * |In(u)| and
  *     its output has |In(u)| * K_n / L_n elements; a tree costs the sum over
  *     its internal nodes.  |T[P]| = prod_{n in P} K_n * prod_{n not in P} L_n.
+ *     The enumeration and the tree validator also take a second node cost,
+ *     the elements a node moves (|In(u)| + |Out(u)|), summed the same way.
  *   Sec. 3.2: chain trees (N independent chains, a mode ordering), K-order,
  *     h-order and balanced trees (Kaya-Ucar divide and conquer).
  *   Sec. 3.3: the (P, Q, R) recurrence.  The printed split term is read as
@@ -48,6 +50,15 @@ static u64 tsize(unsigned P) {
 
 static int popc(unsigned x) { int c = 0; while (x) { x &= x - 1; ++c; } return c; }
 
+/* Node cost of a TTM along mode m applied to T[P]: Sec. 3.1's multiply-adds
+ * K_m * |T[P]|, or (g_cost_elems) the elements the node moves, its input read
+ * and its output written, |T[P]| + |T[P + m]|. */
+static int g_cost_elems;
+static u64 node_cost(unsigned P, int m) {
+  if (g_cost_elems) return tsize(P) + tsize(P | (1u << m));
+  return g_K[m] * tsize(P);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Brute-force enumeration of all TTM-trees.                                 */
 /* ------------------------------------------------------------------------ */
@@ -77,7 +88,7 @@ static void expand(unsigned P, unsigned Qrem, int nt, u64 cost) {
       if (!((avail >> m) & 1u)) continue;
       g_tasks[nt].P = P | (1u << m);
       g_tasks[nt].Q = B;
-      expand(P, remain, nt + 1, cost + g_K[m] * tsize(P));
+      expand(P, remain, nt + 1, cost + node_cost(P, m));
     }
     if (S == rest) break;
     S = (S - rest) & rest; /* next subset of rest */
@@ -98,14 +109,22 @@ static void enum_tasks(int nt, u64 cost) {
 
 /* Enumerates every TTM-tree; returns the number of trees and the min / max
  * cost over them.  Feasible for N <= 5 (N = 5 has tens of millions). */
-int orc_tree_bruteforce(int N, const int64_t* L, const int64_t* K, u64* n_trees, u64* min_cost,
-                        u64* max_cost) {
+int orc_tree_bruteforce_model(int N, const int64_t* L, const int64_t* K, int elems, u64* n_trees,
+                              u64* min_cost, u64* max_cost) {
   if (N < 2 || N > 6) return -1;
   set_problem(N, L, K);
+  g_cost_elems = elems;
   g_count = 0; g_min = ORC_INF; g_max = 0;
   expand(0u, g_full, 0, 0);
+  g_cost_elems = 0;
   *n_trees = g_count; *min_cost = g_min; *max_cost = g_max;
   return 0;
+}
+
+/* The same in multiply-adds (Sec. 3.1's cost). */
+int orc_tree_bruteforce(int N, const int64_t* L, const int64_t* K, u64* n_trees, u64* min_cost,
+                        u64* max_cost) {
+  return orc_tree_bruteforce_model(N, L, K, 0, n_trees, min_cost, max_cost);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -215,8 +234,8 @@ u64 orc_balanced_cost(int N, const int64_t* L, const int64_t* K, const int* orde
  * Sec. 3.1 and returns its cost.  label[i] = mode for an internal node,
  * -1 for the root, -(n + 2) for the leaf of F~_n.  parent[i] = -1 for the root.
  * Returns ORC_INF if any property fails. */
-u64 orc_tree_cost(int N, const int64_t* L, const int64_t* K, int n_nodes, const int* label,
-                  const int* parent) {
+static u64 tree_cost_impl(int N, const int64_t* L, const int64_t* K, int n_nodes, const int* label,
+                          const int* parent) {
   set_problem(N, L, K);
   int root = -1, leaves = 0;
   unsigned leaf_seen = 0;
@@ -246,7 +265,7 @@ u64 orc_tree_cost(int N, const int64_t* L, const int64_t* K, int n_nodes, const 
     if (label[i] >= 0) {
       const int m = label[i];
       if (m >= N || ((P >> m) & 1u)) return ORC_INF;
-      total += g_K[m] * tsize(P);
+      total += node_cost(P, m);
     } else if (label[i] <= -2) {
       const int n = -label[i] - 2;
       if (n >= N || ((leaf_seen >> n) & 1u)) return ORC_INF;
@@ -266,6 +285,20 @@ u64 orc_tree_cost(int N, const int64_t* L, const int64_t* K, int n_nodes, const 
     if (!has_child) return ORC_INF;
   }
   return total;
+}
+
+u64 orc_tree_cost(int N, const int64_t* L, const int64_t* K, int n_nodes, const int* label,
+                  const int* parent) {
+  return tree_cost_impl(N, L, K, n_nodes, label, parent);
+}
+
+/* The cost of a given tree in elements moved (elems != 0) or multiply-adds. */
+u64 orc_tree_cost_model(int N, const int64_t* L, const int64_t* K, int n_nodes, const int* label,
+                        const int* parent, int elems) {
+  g_cost_elems = elems;
+  const u64 c = tree_cost_impl(N, L, K, n_nodes, label, parent);
+  g_cost_elems = 0;
+  return c;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -80,6 +80,33 @@ def test_optimal_tree_matches_oracle_dp_and_bruteforce(tk, orc):
             assert sum(1 for p in parents if p == i) <= 2
 
 
+def test_elems_tree_matches_bruteforce(tk, orc):
+    """The planner's DP under the elements-moved node cost (COST_ELEMS) reaches
+    the least cost over every TTM-tree of any arity (explicit enumeration of
+    the planner oracle), and the tree it returns is a valid TTM-tree whose
+    elements-moved cost the oracle recomputes to the reported tree_elems."""
+    rnd = random.Random(5)
+    checked = 0
+    for trial in range(200):
+        N = rnd.choice([2, 3, 4, 4])
+        L = [rnd.choice([2, 3, 5, 8, 20, 50]) for _ in range(N)]
+        K = [rnd.randint(1, l) for l in L]
+        try:
+            plan = tk.tucker_plan(L, K, cost_model=tk.COST_ELEMS)
+        except tk.TuckerError:
+            continue  # rank-deficient core (K_n > prod of the others)
+        labels, parents, _ = tree_of(tk, plan)
+        cost = orc.tree_cost(L, K, labels, parents, elems=True)
+        assert cost is not None, (L, K, labels, parents)
+        assert cost == tk.tucker_plan_cost(plan)["tree_elems"]
+        assert cost == orc.tree_bruteforce(L, K, elems=True)[1], (L, K)
+        checked += 1
+    assert checked >= 80
+    L, K = (13, 7, 20, 5, 9), (4, 7, 3, 2, 5)  # one N = 5 case
+    plan = tk.tucker_plan(L, K, cost_model=tk.COST_ELEMS)
+    assert tk.tucker_plan_cost(plan)["tree_elems"] == orc.tree_bruteforce(L, K, elems=True)[1]
+
+
 @pytest.mark.parametrize("tree,fn", [(1, "chain"), (2, "chain_k"), (3, "chain_h"), (4, "balanced")])
 def test_prior_scheme_trees_match_oracle(tk, orc, tree, fn):
     rnd = random.Random(11 + tree)

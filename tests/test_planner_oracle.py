@@ -121,3 +121,34 @@ def test_sthosvd_order_cost_properties(orc):
     assert len(costs) == 1
     assert orc.sthosvd_order_cost(L, K, [0, 0, 1, 2]) == 2 ** 64 - 1
     assert orc.sthosvd_order_cost((5, 5, 5), (5, 5, 5), [2, 0, 1]) == 3 * 2 * 5 * 125
+
+
+# -------------------------------------------- elements-moved node cost -------
+def test_elems_model_hand_derived(orc):
+    """Elements moved (|In| + |Out| per internal node) on 4^3, K = 2: a first
+    TTM moves 64 + 32 = 96, a second 32 + 16 = 48.  Chain trees: 3 chains of
+    96 + 48 = 432 (the most any of the 14 trees moves).  Optimal: the root's
+    output is read by at least two first-level TTMs (96 each) and each of the
+    3 leaves needs one more TTM (48 each): 2*96 + 3*48 = 336, reached by the
+    balanced tree."""
+    cnt, mn, mx = orc.tree_bruteforce((4, 4, 4), (2, 2, 2), elems=True)
+    assert (cnt, mn, mx) == (14, 336, 432)
+    # balanced tree of Sec. 3.2 as (label, parent): root; x0 -> {x1 -> F2, x2 -> F1}; x1 -> x2 -> F0
+    labels = [-1, 0, 1, -4, 2, -3, 1, 2, -2]
+    parents = [-1, 0, 1, 2, 1, 4, 0, 6, 7]
+    assert orc.tree_cost((4, 4, 4), (2, 2, 2), labels, parents, elems=True) == 336
+    assert orc.tree_cost((4, 4, 4), (2, 2, 2), labels, parents) == 448
+
+
+def test_elems_model_scales_on_uniform_shapes(orc):
+    """With every L_n = L and K_n = K a node moves |In| (1 + K / L) elements
+    for K |In| multiply-adds, so every tree's two costs differ by the factor
+    (L + K) / (L K): the least and the largest costs scale exactly."""
+    rnd = random.Random(3)
+    for _ in range(12):
+        N = rnd.choice([2, 3, 4])
+        l = rnd.choice([3, 5, 8, 20])
+        k = rnd.randint(1, l)
+        _, mn_m, mx_m = orc.tree_bruteforce([l] * N, [k] * N)
+        _, mn_e, mx_e = orc.tree_bruteforce([l] * N, [k] * N, elems=True)
+        assert mn_m * (l + k) == mn_e * l * k and mx_m * (l + k) == mx_e * l * k
