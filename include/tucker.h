@@ -138,9 +138,11 @@ int tucker_plan_nodes(tucker_plan_t plan, tucker_node_t* nodes, int capacity, in
  * when the root is not fused.  Host only. */
 int tucker_plan_fused_root(tucker_plan_t plan, int* first, int* second);
 
-/* The mode order tucker_sthosvd takes (order: N ints, written) and its cost
- * under the plan's cost model (cost may be NULL): natural unless the plan was
- * made with TUCKER_PLAN_STHOSVD_ORDER.  Host only. */
+/* The mode order tucker_sthosvd takes (Sec. 1: the tree ideas carry over to
+ * STHOSVD): writes N mode indices to order (caller-owned host array) and, if
+ * cost is not NULL, the order's cost under the plan's cost model (see
+ * TUCKER_PLAN_STHOSVD_ORDER).  Natural order unless the plan was made with
+ * that flag.  Host only; TUCKER_ERR_INVALID_ARG if plan or order is NULL. */
 int tucker_plan_sthosvd(tucker_plan_t plan, int* order, uint64_t* cost);
 
 void tucker_plan_destroy(tucker_plan_t plan);
