@@ -196,7 +196,8 @@ int tucker_norm2(tucker_plan_t plan, const void* T, double* out, void* stream);
 /* Synchronous finiteness check of n elements of type dtype at X (a tensor,
  * factor or core): returns TUCKER_ERR_NONFINITE when any is NaN or Inf (their
  * sum of squares is not finite), TUCKER_OK otherwise.  Allocates nothing;
- * waits for `stream`. */
+ * waits for `stream`.  Concurrent calls from several host threads run one
+ * after another. */
 int tucker_check_finite(const void* X, int dtype, int64_t n, void* stream);
 
 /* Error metric of Sec. 2.2 ("normalized root mean square"), using

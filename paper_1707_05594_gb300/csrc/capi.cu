@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "nvtx3/nvToolsExt.h"
@@ -434,12 +435,16 @@ int tucker_norm2(tucker_plan_t plan, const void* T, double* out, void* stream) {
 }
 
 // ||X||^2 of the finiteness check: a device double of the library, so the
-// check allocates nothing.
+// check allocates nothing.  One check runs at a time (the check is
+// synchronous anyway), so calls from several host threads or streams do not
+// share the accumulator.
 static __device__ double g_check_norm2;
+static std::mutex g_check_mutex;
 
 int tucker_check_finite(const void* X, int dtype, int64_t n, void* stream) {
   if (!X || n < 0) return fail(TUCKER_ERR_INVALID_ARG, "tucker_check_finite: invalid argument");
   if (n == 0) return TUCKER_OK;
+  std::lock_guard<std::mutex> lock(g_check_mutex);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* d = nullptr;
   TK_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void**>(&d), g_check_norm2));
