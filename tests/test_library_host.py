@@ -80,6 +80,68 @@ def test_optimal_tree_matches_oracle_dp_and_bruteforce(tk, orc):
             assert sum(1 for p in parents if p == i) <= 2
 
 
+def check_memory_plan(tk, plan, inter_bytes):
+    """Simulates the depth-first execution of the plan's tree: when node v
+    runs, the outputs of its ancestors are live (each is read by a later
+    descendant), and with a fused root the second root child's output is live
+    from the moment the first one runs until its own subtree ends.  No two
+    buffers live at the same time may overlap, and all lie in the workspace."""
+    nodes = tk.tucker_plan_nodes(plan)
+    ws = tk.tucker_plan_cost(plan)["ws_bytes"]
+    n = len(nodes)
+    end = list(range(1, n + 1))  # subtree of u = [u, end[u]) in pre-order
+    for v in range(n - 1, 0, -1):
+        p = nodes[v]["parent"]
+        end[p] = max(end[p], end[v])
+    fused = tk.tucker_plan_fused_root(plan)
+    buf = {u: (nd["ws_offset"], nd["ws_offset"] + nd["out_elems"] * inter_bytes)
+           for u, nd in enumerate(nodes) if nd["label"] >= 0}
+    for u, (a, b) in buf.items():
+        assert 0 <= a < b <= ws, (u, a, b, ws)
+    for v in buf:
+        live = set()
+        w = nodes[v]["parent"]
+        while w > 0:
+            live.add(w)
+            w = nodes[w]["parent"]
+        if fused:
+            u1, u2 = fused
+            if u1 <= v < end[u2] and v != u2:
+                live.add(u2)
+            if v == u2:
+                live.discard(u1)
+        a, b = buf[v]
+        for w in live:
+            c, d = buf[w]
+            assert b <= c or d <= a, ("overlap", v, w, buf[v], buf[w])
+
+
+def test_memory_plan_has_no_live_overlap(tk):
+    """The stack memory plan (Sec. 3.1: live intermediates bounded by the tree
+    depth) never places two simultaneously live outputs on the same bytes:
+    every tree kind, with and without the fused root, several dtypes."""
+    shapes = [((200,) * 4, (20,) * 4), ((64,) * 5, (16,) * 5),
+              ((64, 56, 48, 40, 32, 24), (16, 14, 12, 10, 8, 6)),
+              ((16, 56, 48, 40, 32, 24), (16, 14, 12, 10, 8, 6)),
+              ((12, 28, 12, 13, 9), (4, 7, 4, 3, 2)), ((40, 21, 10, 18), (20, 10, 2, 4))]
+    rnd = random.Random(17)
+    for _ in range(60):
+        N = rnd.choice([2, 3, 4, 5, 6, 7, 8])
+        L = [rnd.choice([2, 3, 5, 8, 13, 24, 40]) for _ in range(N)]
+        K = [rnd.randint(1, l) for l in L]
+        if all(K[n] <= math.prod(K) // K[n] for n in range(N)):
+            shapes.append((L, K))
+    fused_seen = 0
+    for L, K in shapes:
+        for dtype, ib in ((tk.TUCKER_F32, 4), (tk.TUCKER_BF16, 2), (tk.TUCKER_F64, 8)):
+            for tree in (tk.TREE_OPTIMAL, tk.TREE_CHAIN, tk.TREE_BALANCED):
+                for fuse in (True, False):
+                    p = tk.tucker_plan(L, K, dtype, tree, fuse_root=fuse)
+                    fused_seen += tk.tucker_plan_fused_root(p) is not None
+                    check_memory_plan(tk, p, ib)
+    assert fused_seen >= 4
+
+
 def test_elems_tree_matches_bruteforce(tk, orc):
     """The planner's DP under the elements-moved node cost (COST_ELEMS) reaches
     the least cost over every TTM-tree of any arity (explicit enumeration of
