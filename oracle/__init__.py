@@ -100,6 +100,10 @@ def _load():
     lib.orc_tree_cost.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.orc_tree_cost.restype = _u64
+    lib.orc_core_chain_cost.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.POINTER(ctypes.c_int)]
+    lib.orc_core_chain_cost.restype = _u64
+    lib.orc_core_chain_bruteforce.argtypes = [ctypes.c_int, _i64p, _i64p]
+    lib.orc_core_chain_bruteforce.restype = _u64
     lib.orc_sthosvd_order_cost.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.POINTER(ctypes.c_int),
                                            ctypes.c_int]
     lib.orc_sthosvd_order_cost.restype = _u64
@@ -346,6 +350,17 @@ def tree_cost(L: Sequence[int], K: Sequence[int], labels: Sequence[int], parents
 
 
 # --------------------------------------------------------------------------
+def core_chain_cost(L: Sequence[int], K: Sequence[int], order: Sequence[int]) -> int:
+    """Multiply-adds of the new-core chain (Fig. 2) with the modes in `order`."""
+    arr = (ctypes.c_int * len(L))(*[int(m) for m in order])
+    return int(_load().orc_core_chain_cost(len(L), _i64(L), _i64(K), arr))
+
+
+def core_chain_bruteforce(L: Sequence[int], K: Sequence[int]) -> int:
+    """Least new-core chain cost over all N! mode orders."""
+    return int(_load().orc_core_chain_bruteforce(len(L), _i64(L), _i64(K)))
+
+
 def sthosvd_order_cost(L: Sequence[int], K: Sequence[int], order: Sequence[int], elems: bool = False) -> int:
     """Cost of STHOSVD with the modes in `order`: multiply-adds (Gram L_m |Y| +
     TTM K_m |Y| per step) or elements moved (2 |Y| + |Y| K_m / L_m per step)."""

@@ -369,3 +369,47 @@ int orc_sthosvd_order_bruteforce(int N, const int64_t* L, const int64_t* K, int 
   *natural_cost = g_nat_cost;
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* New-core chain order (Fig. 2 "New core": one chain over all N modes).    */
+/* ------------------------------------------------------------------------ */
+/* Multiply-adds of the chain T x_{order[0]} F^T x_{order[1]} F^T ...: step i
+ * costs K_m * |T[P]| (Sec. 3.1's node cost), P the modes applied before it.
+ * ORC_INF when order is not a permutation. */
+u64 orc_core_chain_cost(int N, const int64_t* L, const int64_t* K, const int* order) {
+  set_problem(N, L, K);
+  unsigned P = 0;
+  u64 total = 0;
+  for (int i = 0; i < N; ++i) {
+    const int m = order[i];
+    if (m < 0 || m >= N || ((P >> m) & 1u)) return ORC_INF;
+    total += g_K[m] * tsize(P);
+    P |= 1u << m;
+  }
+  return total;
+}
+
+static u64 g_chain_best;
+
+static void chain_perm_rec(int i, unsigned used, int* perm, const int64_t* L, const int64_t* K) {
+  if (i == g_N) {
+    const u64 c = orc_core_chain_cost(g_N, L, K, perm); /* re-sets the same problem */
+    if (c < g_chain_best) g_chain_best = c;
+    return;
+  }
+  for (int m = 0; m < g_N; ++m) {
+    if ((used >> m) & 1u) continue;
+    perm[i] = m;
+    chain_perm_rec(i + 1, used | (1u << m), perm, L, K);
+  }
+}
+
+/* Least chain cost over all N! orders. */
+u64 orc_core_chain_bruteforce(int N, const int64_t* L, const int64_t* K) {
+  if (N < 1 || N > 9) return ORC_INF;
+  int perm[16];
+  set_problem(N, L, K);
+  g_chain_best = ORC_INF;
+  chain_perm_rec(0, 0u, perm, L, K);
+  return g_chain_best;
+}

@@ -142,6 +142,22 @@ def test_memory_plan_has_no_live_overlap(tk):
     assert fused_seen >= 4
 
 
+def test_core_chain_order_matches_bruteforce(tk, orc):
+    """The new-core chain's mode order (a DP over the set of modes applied)
+    reaches the least multiply-adds over all N! orders."""
+    shapes = [((200,) * 4, (20,) * 4), ((64,) * 5, (16,) * 5),
+              ((64, 56, 48, 40, 32, 24), (16, 14, 12, 10, 8, 6)), ((40, 12, 30, 25), (3, 10, 4, 20))]
+    rnd = random.Random(23)
+    for _ in range(80):
+        N = rnd.choice([2, 3, 4, 5, 6, 7])
+        L = [rnd.choice([2, 3, 5, 8, 13, 40, 97]) for _ in range(N)]
+        K = [rnd.randint(1, l) for l in L]
+        if all(K[n] <= math.prod(K) // K[n] for n in range(N)):
+            shapes.append((L, K))
+    for L, K in shapes:
+        assert tk.tucker_plan_cost(tk.tucker_plan(L, K))["core_macs"] == orc.core_chain_bruteforce(L, K), (L, K)
+
+
 def test_elems_tree_matches_bruteforce(tk, orc):
     """The planner's DP under the elements-moved node cost (COST_ELEMS) reaches
     the least cost over every TTM-tree of any arity (explicit enumeration of

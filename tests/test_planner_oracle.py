@@ -152,3 +152,15 @@ def test_elems_model_scales_on_uniform_shapes(orc):
         _, mn_m, mx_m = orc.tree_bruteforce([l] * N, [k] * N)
         _, mn_e, mx_e = orc.tree_bruteforce([l] * N, [k] * N, elems=True)
         assert mn_m * (l + k) == mn_e * l * k and mx_m * (l + k) == mx_e * l * k
+
+
+# --------------------------------------------------- new-core chain order ----
+def test_core_chain_hand_derived_costs(orc):
+    """Every order of three hand-worked new-core chains and the least cost."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "core_chain_costs.json")))
+    for case in gold["cases"]:
+        L, K = case["L"], case["K"]
+        for order, cost in case["orders"].items():
+            assert orc.core_chain_cost(L, K, [int(m) for m in order.split(",")]) == cost
+        assert orc.core_chain_bruteforce(L, K) == case["best"]
+    assert orc.core_chain_cost((4, 4, 4), (2, 2, 2), [0, 0, 1]) == 2 ** 64 - 1
