@@ -318,7 +318,34 @@ def run_planner_gpu(args):
     return {"metric": "HOOI sweep time, optimal TTM-tree vs the prior trees of Sec. 3.2 (GB300, FP32)",
             "selection": "benchmark shapes (L_n in {20, 50, 100}, K_n = L_n / c, 1e8 <= |T| <= 2e9): "
                          "for N = 5 and 6, the largest and the median best-prior / optimal load ratio",
-            "shapes": out}
+            "shapes": out, "time_vs_cost": tree_time_fit(out, trees)}
+
+
+def tree_time_fit(rows, trees):
+    """How well each tree cost predicts the measured sweep times: least-squares
+    fits of ms per sweep over every (shape, tree) pair against the tree's bytes
+    moved (|In| + |Out| per TTM node, FP32), its multiply-adds (Sec. 3.1), and
+    both plus its number of TTM launches; the RMS relative error of each fit."""
+    import numpy as np
+
+    import paper_1707_05594_gb300 as tk
+    feats, ms = [], []
+    for r in rows:
+        for name, tree in trees.items():
+            p = tk.tucker_plan(r["L"], r["K"], tk.TUCKER_F32, tree)
+            c = tk.tucker_plan_cost(p)
+            nodes = sum(1 for n in tk.tucker_plan_nodes(p) if n["label"] >= 0)
+            feats.append([c["tree_elems"] * 4 / 1e9, c["tree_macs"] / 1e9, nodes])
+            ms.append(r["ms_per_sweep"][name])
+    if len(ms) < 4:
+        return None
+    A, y = np.array(feats), np.array(ms)
+    out = {"pairs": len(ms)}
+    for cols, name in (([0], "gb_moved"), ([1], "gmacs"), ([0, 1, 2], "gb_gmacs_launches")):
+        x = np.linalg.lstsq(A[:, cols], y, rcond=None)[0]
+        err = float(np.sqrt(np.mean(((A[:, cols] @ x - y) / y) ** 2)))
+        out[name] = {"ms_per_unit": [round(float(v), 4) for v in x], "rms_rel_err": round(err, 3)}
+    return out
 
 
 def run_gauss_seidel(args):
