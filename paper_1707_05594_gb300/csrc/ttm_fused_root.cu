@@ -1,5 +1,5 @@
 // ttm_fused_root.cu -- the fused root of the TTM-tree: both root children
-// (T x_a Fa^T and T x_b Fb^T, Sec. 2.1 and the tree of Sec. 4) computed
+// (T x_a Fa^T and T x_b Fb^T, Sec. 2.1; the TTM-tree of Sec. 3.1) computed
 // from one read of T.  T is staged into shared memory block by block with
 // the helpers of slab_common.cuh and both contractions are taken from there,
 // FP32 FMA in increasing l as in the single TTMs.
