@@ -197,7 +197,7 @@ def run_planner(args):
     res = {}
     for N in (5, 6):
         ratios_best, ratios = [], {k: [] for k in kinds}
-        sth_ratios = []
+        sth_ratios, elems_saved, macs_added = [], [], []
         skipped = 0
         t0 = time.perf_counter()
         for combo in itertools.combinations_with_replacement(range(len(modes)), N):
@@ -214,6 +214,10 @@ def run_planner(args):
                 ratios[k].append(ld[k] / ld["opt"])
             ratios_best.append(min(ld[k] for k in kinds) / ld["opt"])
             sth_ratios.append(sth_gain(L, K))
+            cm = tk.tucker_plan_cost(tk.tucker_plan(L, K, tk.TUCKER_F32))
+            ce = tk.tucker_plan_cost(tk.tucker_plan(L, K, tk.TUCKER_F32, cost_model=tk.COST_ELEMS))
+            elems_saved.append(1 - ce["tree_elems"] / cm["tree_elems"])
+            macs_added.append(ce["tree_macs"] / cm["tree_macs"] - 1)
         res[f"{N}D"] = {
             "tensors": len(ratios_best), "skipped_rank_deficient": skipped,
             "best_prior_over_opt": {"median": round(st.median(ratios_best), 3),
@@ -222,6 +226,16 @@ def run_planner(args):
             **{f"{k}_over_opt_median": round(st.median(v), 3) for k, v in ratios.items()},
             "sthosvd_natural_over_opt_order": {"median": round(st.median(sth_ratios), 3),
                                                "max": round(max(sth_ratios), 3)},
+            "elems_tree_vs_mac_tree": {
+                "differs": sum(1 for e in elems_saved if e > 0),
+                "elements_saved_max": round(max(elems_saved), 4),
+                "elements_saved_median_where_differs": (
+                    round(st.median([e for e in elems_saved if e > 0]), 4)
+                    if any(e > 0 for e in elems_saved) else 0.0),
+                "macs_added_max": round(max(macs_added), 4),
+                "macs_added_median_where_differs": (
+                    round(st.median([m for m, e in zip(macs_added, elems_saved) if e > 0]), 4)
+                    if any(e > 0 for e in elems_saved) else 0.0)},
             "seconds": round(time.perf_counter() - t0, 2)}
     real = {"HCCI": ((672, 672, 627, 16), (279, 279, 153, 14)),
             "TJLR": ((460, 700, 360, 16, 4), (306, 232, 239, 16, 4)),
