@@ -6,12 +6,14 @@ TEST INFRASTRUCTURE ONLY: this package may be imported by ``tests/``,
 legs of ``bench.py`` -- nothing else.  It shares no code with the CUDA path
 (``paper_1707_05594_gb300``) and never imports it.
 
-The arithmetic lives in ``oracle.c`` / ``planner_oracle.c`` (plain C, double
-precision, naive loops); this module only marshals numpy arrays.
+The arithmetic lives in ``oracle.c`` / ``planner_oracle.c`` / ``fp8_oracle.c``
+(plain C, double precision, naive loops); this module only marshals numpy
+arrays.
 
-Citations are to the paper: Sec. 2.1 (TTM, TTM-chain), Sec. 2.2 and Fig. 2
-(Tucker model, HOOI), Sec. 3.1-3.3 (TTM-trees, cost, recurrence), Sec. 5
-(SVD via Gram + EVD).
+Citations are to the paper: Sec. 1 (STHOSVD, and that the tree ideas carry
+over to it: its mode order), Sec. 2.1 (TTM, TTM-chain), Sec. 2.2 and Fig. 2
+(Tucker model, HOOI, new core), Sec. 3.1-3.3 (TTM-trees, cost, recurrence),
+Sec. 5 (SVD via Gram + EVD).
 """
 from __future__ import annotations
 
