@@ -237,7 +237,8 @@ int tucker_gram(int N, const int64_t* dims, const void* Z, int z_dtype, int n, d
  * output of type f_dtype (TUCKER_F64: double, else float), columns ordered by
  * decreasing eigenvalue, sign as in tucker_hooi_sweep.  ws: device scratch of
  * at least tucker_eig_ws_bytes(batch, L, K) bytes.  Requires L[b] <= 200 and
- * K[b] <= min(L[b], 64). */
+ * K[b] <= min(L[b], 64) (else TUCKER_ERR_UNSUPPORTED); f_dtype must be
+ * TUCKER_F32 or TUCKER_F64 (else TUCKER_ERR_INVALID_ARG). */
 int tucker_eig_topk(int batch, const int64_t* L, const int64_t* K, const double* const* W,
                     void* const* F, int f_dtype, void* ws, size_t ws_bytes, void* stream);
 size_t tucker_eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
@@ -249,9 +250,13 @@ size_t tucker_eig_ws_bytes(int batch, const int64_t* L, const int64_t* K);
  * tucker_eig_topk, but no workspace: the scratch is a fixed array of about
  * 4 MiB compiled into the library, held on every GPU that loads it until the
  * process exits.  Limits: batch <= 8, every L <= 200 and K <= min(L, 64);
- * larger problems return TUCKER_ERR_UNSUPPORTED.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * larger problems return TUCKER_ERR_UNSUPPORTED; an f_dtype other than
+ * TUCKER_F32 or TUCKER_F64 returns TUCKER_ERR_INVALID_ARG.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current and keeps it for the life of the process; make that
+ * first call before any stream capture.  A cudaDeviceReset (or any teardown of
+ * the device's primary context) invalidates the kept address: do not call this
+ * entry point on that device afterwards.  All calls share
  * the one array: calls that may overlap on the GPU (different streams, or
  * different host threads) race on it and must be serialised by the caller.
  * The call allocates nothing (no cudaMalloc, cudaFree or allocating library

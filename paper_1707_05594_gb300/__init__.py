@@ -348,11 +348,34 @@ def tucker_eig_ws_bytes(Ls: Sequence[int], Ks: Sequence[int]) -> int:
     return int(lib().tucker_eig_ws_bytes(len(Ls), _i64(Ls), _i64(Ks)))
 
 
+def _eig_args(Ws: Sequence, Fs: Sequence):
+    """(L list, K list, factor dtype code) of an eigensolver call, after the
+    checks the C entry points cannot make on raw pointers: one output per
+    matrix, every W a float64 (L, L) matrix, every F an (L, K) matrix and all
+    F of one type, float32 or float64."""
+    import torch
+    if len(Ws) == 0 or len(Ws) != len(Fs):
+        raise ValueError("need one output factor per matrix")
+    fdt = Fs[0].dtype
+    if fdt not in (torch.float32, torch.float64):
+        raise TypeError(f"factors must be float32 or float64, not {fdt}")
+    Ls, Ks = [], []
+    for W, F in zip(Ws, Fs):
+        if W.dtype != torch.float64 or W.dim() != 2 or W.shape[0] != W.shape[1]:
+            raise TypeError("every W must be a square float64 matrix")
+        if F.dtype != fdt:
+            raise TypeError("all factors must have the same dtype")
+        if F.dim() != 2 or F.shape[0] != W.shape[0]:
+            raise ValueError("every F must be an (L, K) matrix with L = W.shape[0]")
+        Ls.append(int(W.shape[0]))
+        Ks.append(int(F.shape[1]))
+    return Ls, Ks, (TUCKER_F64 if fdt == torch.float64 else TUCKER_F32)
+
+
 def tucker_eig_topk(Ws: Sequence, Fs: Sequence, ws, stream=None):
-    Ls = [W.shape[0] for W in Ws]
-    Ks = [F.shape[1] for F in Fs]
+    Ls, Ks, fcode = _eig_args(Ws, Fs)
     _check(lib().tucker_eig_topk(len(Ws), _i64(Ls), _i64(Ks), _ptrs(Ws), _ptrs(Fs),
-                                 _dtype_code(Fs[0]), _dp(ws, "ws"), ws.numel(),
+                                 fcode, _dp(ws, "ws"), ws.numel(),
                                  _stream(stream)), "tucker_eig_topk")
 
 
@@ -360,10 +383,9 @@ def tucker_eig_topk_noalloc(Ws: Sequence, Fs: Sequence, stream=None):
     """Leading eigenvectors without any device allocation or workspace: for
     callers that must not allocate (see include/tucker.h).  Uses a fixed
     scratch array inside the library shared by all calls."""
-    Ls = [W.shape[0] for W in Ws]
-    Ks = [F.shape[1] for F in Fs]
+    Ls, Ks, fcode = _eig_args(Ws, Fs)
     _check(lib().tucker_eig_topk_noalloc(len(Ws), _i64(Ls), _i64(Ks), _ptrs(Ws), _ptrs(Fs),
-                                         _dtype_code(Fs[0]), _stream(stream)),
+                                         fcode, _stream(stream)),
            "tucker_eig_topk_noalloc")
 
 

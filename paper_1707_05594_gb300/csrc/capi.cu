@@ -140,6 +140,8 @@ int tucker_eig_topk(int batch, const int64_t* L, const int64_t* K, const double*
                     void* const* F, int f_dtype, void* ws, size_t ws_bytes, void* stream) {
   if (batch < 1 || !L || !K || !W || !F)
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_eig_topk: invalid argument");
+  if (f_dtype != TUCKER_F32 && f_dtype != TUCKER_F64)
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_eig_topk: f_dtype must be TUCKER_F32 or TUCKER_F64");
   std::vector<EigProblem> probs((size_t)batch);
   for (int b = 0; b < batch; ++b) {
     if (!W[b] || !F[b]) return fail(TUCKER_ERR_INVALID_ARG, "tucker_eig_topk: NULL matrix");

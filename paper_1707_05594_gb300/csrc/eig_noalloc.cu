@@ -64,6 +64,9 @@ extern "C" int tucker_eig_topk_noalloc(int batch, const int64_t* L, const int64_
                                        void* stream) {
   if (batch < 1 || !L || !K || !W || !F)
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_eig_topk_noalloc: invalid argument");
+  if (f_dtype != TUCKER_F32 && f_dtype != TUCKER_F64)
+    return fail(TUCKER_ERR_INVALID_ARG,
+                "tucker_eig_topk_noalloc: f_dtype must be TUCKER_F32 or TUCKER_F64");
   if (batch > kNoallocMaxBatch)
     return fail(TUCKER_ERR_UNSUPPORTED,
                 "tucker_eig_topk_noalloc: at most 8 matrices per call (fixed scratch)");

@@ -482,3 +482,39 @@ def test_optimal_tree_never_above_prior_trees_on_benchmark_metadata(tk):
             other = tk.tucker_plan_cost(tk.tucker_plan(L, K, tree=tree))["tree_macs"]
             assert opt <= other, (L, K, tree)
         checked += 1
+
+
+def test_eig_wrappers_reject_bad_factor_types(tk):
+    # the C entry points see only raw pointers: the binding must refuse a
+    # factor type the solver does not write, a mixed list, a non-double W and
+    # a factor whose row count is not W's size, before anything is launched
+    import torch
+    W = torch.eye(8, dtype=torch.float64)
+    cases = [
+        ([W], [torch.empty(8, 2, dtype=torch.bfloat16)], TypeError),
+        ([W, W], [torch.empty(8, 2, dtype=torch.float32), torch.empty(8, 2, dtype=torch.float64)],
+         TypeError),
+        ([W.float()], [torch.empty(8, 2, dtype=torch.float32)], TypeError),
+        ([W], [torch.empty(7, 2, dtype=torch.float32)], ValueError),
+        ([W, W], [torch.empty(8, 2, dtype=torch.float32)], ValueError),
+    ]
+    ws = torch.empty(256, dtype=torch.uint8)
+    for Ws, Fs, exc in cases:
+        with pytest.raises(exc):
+            tk.tucker_eig_topk(Ws, Fs, ws)
+        with pytest.raises(exc):
+            tk.tucker_eig_topk_noalloc(Ws, Fs)
+
+
+def test_eig_entry_points_reject_unknown_factor_dtype(tk):
+    # the host-side check of the C ABI runs before any device work
+    import ctypes
+    L = tk.lib()
+    Ls, Ks = tk._i64([8]), tk._i64([2])
+    ptrs = (ctypes.c_void_p * 1)(ctypes.c_void_p(256))
+    for code in (tk.TUCKER_BF16, tk.TUCKER_FP8_E4M3, 7):
+        rc = L.tucker_eig_topk(1, Ls, Ks, ptrs, ptrs, code, ctypes.c_void_p(256), 4096, None)
+        assert rc == -1
+        assert b"f_dtype" in L.tucker_last_error()
+        rc = L.tucker_eig_topk_noalloc(1, Ls, Ks, ptrs, ptrs, code, None)
+        assert rc == -1

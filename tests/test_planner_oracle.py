@@ -22,6 +22,22 @@ def test_hand_derived_costs(orc):
         assert mx >= case["chain_natural"]
 
 
+def test_hand_derived_ordered_chains(orc):
+    # Sec. 3.2 mode orderings: K-order by increasing K_n, h-order by
+    # increasing K_n / L_n; the chain costs under each were worked by hand
+    data = json.load(open(GOLD))["ordered_chains"]
+    for case in data["cases"]:
+        L, K = case["L"], case["K"]
+        assert orc.k_order(L, K) == case["k_order"]
+        assert orc.h_order(L, K) == case["h_order"]
+        assert orc.chain_cost(L, K, orc.k_order(L, K)) == case["chain_k_order"]
+        assert orc.chain_cost(L, K, orc.h_order(L, K)) == case["chain_h_order"]
+        assert orc.chain_cost(L, K) == case["chain_natural"]
+        if "chain_k_reversed" in case:
+            assert orc.chain_cost(L, K, orc.k_order(L, K)[::-1]) == case["chain_k_reversed"]
+            assert orc.chain_cost(L, K, orc.h_order(L, K)[::-1]) == case["chain_h_reversed"]
+
+
 def test_hand_counted_tree_numbers(orc):
     data = json.load(open(GOLD))["tree_counts"]
     for n_str, count in data.items():

@@ -66,6 +66,27 @@ def test_noalloc_matches_workspace_entry_point(tk, fdt):
             assert np.abs(B.T @ B - np.eye(K)).max() <= tol
 
 
+def test_noalloc_allocates_no_device_memory(tk):
+    # the entry point's one contract: repeated calls take no device memory
+    # from the driver and none from torch's allocator.  A first call of the
+    # same problems loads the kernels they use (lazy module loading takes
+    # device memory once), so the counters are read after it.
+    sizes = [(200, 20), (96, 12), (16, 4)]
+    Ws = gram_batch(sizes, seed=30)
+    Fs = [torch.empty(L, K, dtype=torch.float32, device="cuda") for L, K in sizes]
+    tk.tucker_eig_topk_noalloc(Ws, Fs)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(5):
+        tk.tucker_eig_topk_noalloc(Ws, Fs)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0
+    assert all(bool(torch.isfinite(F).all()) for F in Fs)
+
+
 def test_noalloc_rejects_beyond_the_fixed_scratch(tk):
     W = torch.zeros(256, 256, dtype=torch.float64, device="cuda")
     F = torch.empty(256, 4, dtype=torch.float32, device="cuda")
