@@ -50,8 +50,11 @@ typedef enum {
   TUCKER_F32 = 0,  /* float32; factors/core float32                        */
   TUCKER_F64 = 1,  /* float64; factors/core float64                        */
   TUCKER_BF16 = 2, /* bfloat16 (raw uint16 bits); factors/core float32     */
-  TUCKER_FP8_E4M3 = 3 /* FP8 E4M3 codes + one float32 scale per 64 elements  */
-                      /* (layout at tucker_fp8_bytes); factors/core float32  */
+  TUCKER_FP8_E4M3 = 3, /* FP8 E4M3 codes + one float32 scale per 64 elements */
+                       /* (layout at tucker_fp8_bytes); factors/core float32 */
+  TUCKER_BF16_SPLIT = 4 /* an FP32 tensor stored as two BF16 tensors hi + lo   */
+                        /* (layout at tucker_bf16_split_bytes); factors/core   */
+                        /* and tree intermediates float32                      */
 } tucker_dtype_t;
 
 /* Which TTM-tree the plan executes (Sec. 3.2 / 3.3). */
@@ -81,9 +84,14 @@ typedef struct {
  * the trailing block of T from mode a on (L_a * ... * L_{N-1} elements) fits
  * in 8 KB and K_a, K_b <= 32, a sweep computes both children from one read of
  * T (one kernel that stages each block in shared memory and contracts it
- * along a and along b); the second child's buffer then sits after the first
- * child's subtree (see ws_offset), which can enlarge the workspace.
- * Results are those of the two separate TTMs (same order of summation). */
+ * along a and along b); for FP32 tensors with b = a + 2 whose later lengths
+ * meet the tensor-core TTM's conditions, when an FP32 tensor-core policy bit
+ * is set (see tucker_set_kernel_policy; otherwise the two run as separate
+ * TTMs), one tensor-core kernel computes both, running through T block by
+ * block of mode a + 1 (each block read from HBM once and found in L2 by the
+ * second mode's tiles).  The second child's buffer then sits after the first
+ * child's subtree (see ws_offset), which can enlarge the workspace.  Results
+ * are those of the two separate TTMs (the same bits). */
 #define TUCKER_PLAN_NO_FUSED_ROOT 1
 
 /* Plan flag: let tucker_sthosvd take the modes in the order of least cost
@@ -308,6 +316,25 @@ int tucker_convert_bf16(const float* x, uint16_t* hi, uint16_t* lo, int64_t n, v
 size_t tucker_fp8_bytes(int64_t n);
 int tucker_convert_fp8(const float* x, void* out, int64_t n, void* stream);
 
+/* Split BF16 storage (the optional split first TTM of the precision form):
+ * an FP32 tensor x of n elements held as hi = bf16(x) and lo = bf16(x - hi)
+ * (tucker_convert_bf16), which keeps ~16 significant bits (|x - hi - lo| <=
+ * 2^-18 |x|) at the 4 bytes per element of FP32.  One buffer of
+ * tucker_bf16_split_bytes(n) bytes holds the n hi values, then, from byte
+ * offset tucker_bf16_split_lo_offset(n) (the first 256-byte boundary at or
+ * after 2n), the n lo values; the buffer itself 256-byte aligned.  Plans of
+ * type TUCKER_BF16_SPLIT read such a T in every TTM whose input is T (Sec.
+ * 2.1): on the tensor cores, each k-step issuing A_hi [F_hi | F_lo] and
+ * A_lo F_hi, FP32 accumulation; their tree intermediates, factors and core
+ * are FP32.  tucker_plan returns TUCKER_ERR_UNSUPPORTED for such a plan
+ * unless every mode's TTM of T takes the tensor-core tile (mode not last: the
+ * product of the later lengths a multiple of 8 and >= 64; last mode: its
+ * length a multiple of 8; K_n <= 64) and its factor fits in shared memory;
+ * STHOSVD and the Gram of T are not offered for this type (run them on the
+ * FP32 tensor). */
+size_t tucker_bf16_split_bytes(int64_t n);
+size_t tucker_bf16_split_lo_offset(int64_t n);
+
 /* Kernel selection, a bit mask (process-wide; 0 is the default):
  *   bit 0 (1): every TTM on the CUDA-core kernels (otherwise BF16 and FP8
  *              tensors use the tensor-core TTMs, tcgen05 + TMA, where the
@@ -329,8 +356,23 @@ int tucker_convert_fp8(const float* x, void* out, int64_t n, void* stream);
  *   bit 4 (16): BF16 TTMs on the tensor cores wherever the shape allows
  *              (otherwise column shapes whose tensor-core tiles would be less
  *              than 60 % useful -- l in stages of 64, 128 positions per tile
- *              -- run on the CUDA cores, which are faster there).
- * Used to compare the paths.  TUCKER_ERR_INVALID_ARG outside 0..31. */
+ *              -- run on the CUDA cores, which are faster there);
+ *   bit 5 (32): FP32 TTMs of the column case with C % 4 == 0, C >= 64 and
+ *              K <= 32 on the tensor cores with exact integer slices: per
+ *              64-l chunk each position's values and each factor column are
+ *              scaled by a power of two and cut into three 8-bit integer
+ *              slices held in BF16, whose products and sums the tensor core
+ *              forms without rounding; only the slicing and an FP32 epilogue
+ *              round, so the result is as accurate as an FP32 contraction
+ *              and unbiased (slower than the CUDA cores at present);
+ *   bit 6 (64): those FP32 TTMs on the tensor cores in TF32 with split
+ *              operands instead (x_hi f_hi + x_hi f_lo + x_lo f_hi; less conversion
+ *              work, but the tensor core's FP32 accumulation rounds toward
+ *              zero, which biases every output by ~1e-7 relative and the
+ *              fit identity by ~1e-5 on the 1e-2-noise workloads);
+ *   bit 7 (128): with bit 6, one accumulator per tile instead of one per
+ *              64-l chunk summed in registers.
+ * Used to compare the paths.  TUCKER_ERR_INVALID_ARG outside 0..255. */
 int tucker_set_kernel_policy(int policy);
 
 /* Device error word of the tensor-core kernels: 0, or TUCKER_ERR_TIMEOUT if a

@@ -19,7 +19,7 @@ from typing import List, Sequence
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtucker_gb300.so")
 
-TUCKER_F32, TUCKER_F64, TUCKER_BF16, TUCKER_FP8_E4M3 = 0, 1, 2, 3
+TUCKER_F32, TUCKER_F64, TUCKER_BF16, TUCKER_FP8_E4M3, TUCKER_BF16_SPLIT = 0, 1, 2, 3, 4
 TREE_OPTIMAL, TREE_CHAIN, TREE_CHAIN_K, TREE_CHAIN_H, TREE_BALANCED = 0, 1, 2, 3, 4
 COST_MACS, COST_ELEMS = 0, 1
 PLAN_NO_FUSED_ROOT = 1
@@ -104,6 +104,10 @@ def lib():
     L.tucker_fp8_bytes.restype = ctypes.c_size_t
     L.tucker_convert_fp8.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_void_p]
+    L.tucker_bf16_split_bytes.argtypes = [ctypes.c_int64]
+    L.tucker_bf16_split_bytes.restype = ctypes.c_size_t
+    L.tucker_bf16_split_lo_offset.argtypes = [ctypes.c_int64]
+    L.tucker_bf16_split_lo_offset.restype = ctypes.c_size_t
     L.tucker_device_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     L.tucker_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
     L.tucker_check_finite.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
@@ -174,6 +178,8 @@ def _dtype_code(t) -> int:
     import torch
     if isinstance(t, Fp8Tensor):
         return TUCKER_FP8_E4M3
+    if isinstance(t, Bf16SplitTensor):
+        return TUCKER_BF16_SPLIT
     if t.dtype == torch.float32:
         return TUCKER_F32
     if t.dtype == torch.float64:
@@ -447,6 +453,58 @@ def tucker_convert_fp8(x, stream=None) -> Fp8Tensor:
     _check(lib().tucker_convert_fp8(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(buf.data_ptr()),
                                     x.numel(), _stream(stream)), "tucker_convert_fp8")
     return Fp8Tensor(buf, x.shape)
+
+
+class Bf16SplitTensor:
+    """An FP32 tensor held as two BF16 tensors hi = bf16(x), lo = bf16(x - hi)
+    in one uint8 CUDA buffer (the layout of tucker_bf16_split_bytes: hi, then
+    lo from tucker_bf16_split_lo_offset).  Passed wherever a plan of type
+    TUCKER_BF16_SPLIT takes T."""
+
+    def __init__(self, buf, shape):
+        self.buf = buf
+        self.shape = tuple(int(x) for x in shape)
+        self.is_cuda = buf.is_cuda
+        self.device = buf.device
+
+    def data_ptr(self):
+        return self.buf.data_ptr()
+
+    def is_contiguous(self):
+        return True
+
+    def dim(self):
+        return len(self.shape)
+
+    def numel(self):
+        n = 1
+        for x in self.shape:
+            n *= x
+        return n
+
+    def hi(self):
+        import torch
+        return self.buf[:2 * self.numel()].view(torch.bfloat16).view(self.shape)
+
+    def lo(self):
+        import torch
+        off = int(lib().tucker_bf16_split_lo_offset(self.numel()))
+        return self.buf[off:off + 2 * self.numel()].view(torch.bfloat16).view(self.shape)
+
+
+def tucker_bf16_split(x, stream=None) -> Bf16SplitTensor:
+    """Split BF16 copy (hi + lo) of the float32 CUDA tensor x."""
+    import torch
+    _req(x, "x")
+    if x.dtype != torch.float32:
+        raise TypeError("tucker_bf16_split takes a float32 tensor")
+    n = x.numel()
+    buf = torch.empty(max(256, int(lib().tucker_bf16_split_bytes(n))), dtype=torch.uint8, device=x.device)
+    off = int(lib().tucker_bf16_split_lo_offset(n))
+    _check(lib().tucker_convert_bf16(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(buf.data_ptr()),
+                                     ctypes.c_void_p(buf.data_ptr() + off), n, _stream(stream)),
+           "tucker_bf16_split")
+    return Bf16SplitTensor(buf, x.shape)
 
 
 def tucker_set_kernel_policy(policy: int) -> None:

@@ -74,6 +74,35 @@ struct ProfScope {
 
 std::atomic<uint64_t> g_launches{0};
 
+// Both root children Ya = X x_a Fa^T, Yb = X x_b Fb^T (a < b): from one read
+// of X by the fused kernel when the trailing block fits, else (FP32 tensors,
+// 16-byte aligned, a tensor-core policy bit set) by the tensor-core pair that
+// reads X once blocked by mode a + 1 -- exact slices under policy bit 32, TF32
+// under bit 64 -- else as two TTMs.
+int launch_root_pair(int dtype, const void* X, const int64_t* L, int N, int a, int b, const float* Fa,
+                     int64_t Ka, const float* Fb, int64_t Kb, void* Ya, void* Yb, int y_dtype,
+                     cudaStream_t s) {
+  int64_t K[kMaxModes];
+  for (int i = 0; i < N; ++i) K[i] = 1;
+  K[a] = Ka;
+  K[b] = Kb;
+  if (fused_root_fits(dtype, N, L, K, a, b))
+    return launch_ttm_fused_root(dtype, X, L, N, a, b, Fa, Ka, Fb, Kb, Ya, Yb, y_dtype, s);
+  if (dtype == TUCKER_F32 && y_dtype == TUCKER_F32 && (kernel_policy() & 1) == 0) {
+    const float* x = static_cast<const float*>(X);
+    if ((kernel_policy() & 64) && ttm_tf32_pair_supported(L, N, a, b, Ka, Kb, X))
+      return launch_ttm_tf32_pair(x, L, N, a, b, Fa, Ka, Fb, Kb, static_cast<float*>(Ya), static_cast<float*>(Yb), s);
+    if ((kernel_policy() & (32 | 64)) == 32 && ttm_x3_pair_supported(L, N, a, b, Ka, Kb, X))
+      return launch_ttm_x3_pair(x, L, N, a, b, Fa, Ka, Fb, Kb, static_cast<float*>(Ya), static_cast<float*>(Yb), s);
+  }
+  int64_t R, Ln, C;
+  view3(L, N, a, &R, &Ln, &C);
+  int rc = launch_ttm(dtype, X, R, Ln, C, Fa, Ka, Ya, y_dtype, s);
+  if (rc) return rc;
+  view3(L, N, b, &R, &Ln, &C);
+  return launch_ttm(dtype, X, R, Ln, C, Fb, Kb, Yb, y_dtype, s);
+}
+
 }  // namespace
 
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -117,10 +146,10 @@ int tucker_ttm_pair(int N, const int64_t* dims, const void* X, int x_dtype, int 
   for (int i = 0; i < N; ++i) K[i] = 1;
   K[a] = Ka;
   K[b] = Kb;
-  if (!fused_root_fits(x_dtype, N, dims, K, a, b))
+  if (!root_pair_fits(x_dtype, N, dims, K, a, b))
     return fail(TUCKER_ERR_UNSUPPORTED, "tucker_ttm_pair: shape or type not supported");
-  return launch_ttm_fused_root(x_dtype, X, dims, N, a, b, Fa, Ka, Fb, Kb, Ya, Yb, y_dtype,
-                               static_cast<cudaStream_t>(stream));
+  return launch_root_pair(x_dtype, X, dims, N, a, b, Fa, Ka, Fb, Kb, Ya, Yb, y_dtype,
+                          static_cast<cudaStream_t>(stream));
 }
 
 int tucker_gram(int N, const int64_t* dims, const void* Z, int z_dtype, int n, double* W,
@@ -201,9 +230,9 @@ int tucker_hooi_sweep_core(tucker_plan_t plan, const void* T, const void* const*
       const int a = std::min(nd.label, n2.label), b = std::max(nd.label, n2.label);
       void* y1 = wsb + p.off_scratch + nd.ws_off;
       void* y2 = wsb + p.off_scratch + n2.ws_off;
-      rc = launch_ttm_fused_root(p.dtype, T, p.L, p.N, a, b, static_cast<const float*>(F_in[a]), p.K[a],
-                                 static_cast<const float*>(F_in[b]), p.K[b], nd.label == a ? y1 : y2,
-                                 nd.label == a ? y2 : y1, idt, s);
+      rc = launch_root_pair(p.dtype, T, p.L, p.N, a, b, static_cast<const float*>(F_in[a]), p.K[a],
+                            static_cast<const float*>(F_in[b]), p.K[b], nd.label == a ? y1 : y2,
+                            nd.label == a ? y2 : y1, idt, s);
       if (rc) return rc;
     } else if (nd.label >= 0) {
       int64_t R, L, C;

@@ -318,6 +318,24 @@ int launch_ttm_fp8(const void* X, int64_t R, int64_t L, int64_t C, const float* 
 int launch_norm2_fp8(const void* X, int64_t n, double* out, cudaStream_t s);
 // Tensor-core TTM for FP32 tensors (column case, ttm_tc.cu): FP32 tiles split
 // into BF16 hi + lo in shared memory, products within ~2^-16 of FP32.
+// FP32 TTMs on the tensor cores in TF32 with split operands (ttm_tf32.cu):
+// one TTM of the column case, or the two root children of a sweep (modes a
+// and b = a + 2) from one pass over T blocked by mode a + 1 (L2 reuse).
+bool ttm_tf32_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X);
+int launch_ttm_tf32(const float* X, int64_t R, int64_t L, int64_t C, const float* F, int64_t K, float* Y,
+                    cudaStream_t s);
+bool ttm_tf32_pair_supported(const int64_t* dims, int N, int a, int b, int64_t Ka, int64_t Kb,
+                             const void* X);
+int launch_ttm_tf32_pair(const float* X, const int64_t* dims, int N, int a, int b, const float* Fa, int64_t Ka,
+                         const float* Fb, int64_t Kb, float* Ya, float* Yb, cudaStream_t s);
+// the same with exact BF16 integer slices (ttm_x3_kernel, the default)
+bool ttm_x3_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X);
+int launch_ttm_x3(const float* X, int64_t R, int64_t L, int64_t C, const float* F, int64_t K, float* Y,
+                  cudaStream_t s);
+bool ttm_x3_pair_supported(const int64_t* dims, int N, int a, int b, int64_t Ka, int64_t Kb, const void* X);
+int launch_ttm_x3_pair(const float* X, const int64_t* dims, int N, int a, int b, const float* Fa, int64_t Ka,
+                       const float* Fb, int64_t Kb, float* Ya, float* Yb, cudaStream_t s);
+
 bool ttm_tc_f32_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X);
 int launch_ttm_tc_f32(const float* X, int64_t R, int64_t L, int64_t C, const float* F, int64_t K,
                       float* Y, cudaStream_t s);

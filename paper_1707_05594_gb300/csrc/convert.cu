@@ -64,3 +64,9 @@ extern "C" int tucker_convert_bf16(const float* x, uint16_t* hi, uint16_t* lo, i
   TK_LAUNCH_CHECK("convert_bf16");
   return TUCKER_OK;
 }
+
+extern "C" size_t tucker_bf16_split_lo_offset(int64_t n) { return n > 0 ? bf16_split_lo_offset(n) : 0; }
+
+extern "C" size_t tucker_bf16_split_bytes(int64_t n) {
+  return n > 0 ? bf16_split_lo_offset(n) + (size_t)n * 2 : 0;
+}

@@ -164,8 +164,9 @@ int launch_gram(int z_dtype, const void* Z, int64_t R, int64_t L, int64_t C, dou
                                                         W, tiles, mpb);
       break;
     case TUCKER_FP8_E4M3:
+    case TUCKER_BF16_SPLIT:
       return fail(TUCKER_ERR_UNSUPPORTED,
-                  "gram: FP8 tensors are read by TTMs only (run STHOSVD on the FP32 tensor)");
+                  "gram: FP8 and split BF16 tensors are read by TTMs only (run STHOSVD on the FP32 tensor)");
     default:
       return fail(TUCKER_ERR_INVALID_ARG, "gram: unknown dtype");
   }

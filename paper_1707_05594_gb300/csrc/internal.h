@@ -55,7 +55,7 @@ struct Plan {
   std::vector<void*> prof_events;  // 2 * prof_cap events
   std::vector<int> prof_node, prof_label;
 
-  size_t elem_bytes() const {
+  size_t elem_bytes() const {  // bytes of T per element (hi + lo for the split type)
     return dtype == TUCKER_F64 ? 8 : (dtype == TUCKER_BF16 ? 2 : (dtype == TUCKER_FP8_E4M3 ? 1 : 4));
   }
   // tree intermediates: FP64 for FP64 tensors, BF16 for BF16 and FP8 tensors
@@ -73,6 +73,17 @@ struct Plan {
 // whether the fused root TTM (ttm_fused_root.cu) takes the two root children of
 // modes a < b of a tensor of this type and these lengths
 bool fused_root_fits(int dtype, int N, const int64_t* L, const int64_t* K, int a, int b);
+// whether a sweep computes the root children of modes a < b together: the
+// fused kernel above, or (FP32 tensors, b = a + 2) the tensor-core pair that
+// reads T once, blocked by mode a + 1 so that the second mode's tiles find
+// each block in L2
+bool root_pair_fits(int dtype, int N, const int64_t* L, const int64_t* K, int a, int b);
+
+// byte offset of the lo half in a split BF16 tensor of n elements
+inline size_t bf16_split_lo_offset(int64_t n) { return align_up((size_t)n * 2); }
+// whether the tensor-core TTM reads a split BF16 tensor of this [R][L][C]
+// view with K outputs (shape, alignment-free part, and shared memory)
+bool ttm_tc_split_fits(int64_t R, int64_t L, int64_t C, int64_t K);
 
 // thread-local error text
 void set_error(const std::string& msg);

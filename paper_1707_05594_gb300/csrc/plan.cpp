@@ -209,14 +209,14 @@ void memory_plan(Plan& p) {
 }
 
 // Fused root: the first two root children in depth-first order, when both
-// are TTM nodes whose pair of modes the fused kernel takes.
+// are TTM nodes whose pair of modes one kernel takes (root_pair_fits).
 void choose_fused_root(Plan& p) {
   int u[2] = {-1, -1}, found = 0;
   for (size_t i = 1; i < p.nodes.size() && found < 2; ++i)
     if (p.nodes[i].parent == 0 && p.nodes[i].label >= 0) u[found++] = (int)i;
   if (found < 2) return;
   const int m1 = p.nodes[(size_t)u[0]].label, m2 = p.nodes[(size_t)u[1]].label;
-  if (!fused_root_fits(p.dtype, p.N, p.L, p.K, std::min(m1, m2), std::max(m1, m2))) return;
+  if (!root_pair_fits(p.dtype, p.N, p.L, p.K, std::min(m1, m2), std::max(m1, m2))) return;
   p.fused_u1 = u[0];
   p.fused_u2 = u[1];
 }
@@ -359,7 +359,7 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
   tucker_plan_opts_t o{TUCKER_F32, TUCKER_TREE_OPTIMAL, TUCKER_COST_MACS, 0};
   if (opts) o = *opts;
   if (o.dtype != TUCKER_F32 && o.dtype != TUCKER_F64 && o.dtype != TUCKER_BF16 &&
-      o.dtype != TUCKER_FP8_E4M3)
+      o.dtype != TUCKER_FP8_E4M3 && o.dtype != TUCKER_BF16_SPLIT)
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown dtype");
   if (o.tree < TUCKER_TREE_OPTIMAL || o.tree > TUCKER_TREE_BALANCED)
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: unknown tree kind");
@@ -383,6 +383,20 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
       return fail(TUCKER_ERR_INVALID_ARG,
                   "tucker_plan: K_n exceeds the product of the other core lengths "
                   "(Z_(n) would have rank below K_n)");
+  }
+
+  if (o.dtype == TUCKER_BF16_SPLIT) {
+    // every TTM whose input is T reads the split tensor on the tensor cores
+    for (int n = 0; n < N; ++n) {
+      int64_t R = 1, C = 1;
+      for (int j = 0; j < n; ++j) R *= L[j];
+      for (int j = n + 1; j < N; ++j) C *= L[j];
+      if (!ttm_tc_split_fits(R, L[n], C, K[n]))
+        return fail(TUCKER_ERR_UNSUPPORTED,
+                    "tucker_plan: TUCKER_BF16_SPLIT needs every mode's TTM of T on the tensor cores "
+                    "(later lengths' product a multiple of 8 and >= 64, or a last mode whose length "
+                    "is a multiple of 8; K_n <= 64)");
+    }
   }
 
   tucker_plan_s* h = new (std::nothrow) tucker_plan_s();

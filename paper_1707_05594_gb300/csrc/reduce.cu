@@ -47,6 +47,21 @@ __global__ void __launch_bounds__(kRedThreads)
   if (threadIdx.x == 0) atomicAdd(out, s);
 }
 
+// ||hi + lo||^2 of a split BF16 tensor: each value rebuilt in FP32 (exact:
+// hi + lo has at most 16 significant bits) and squared in FP64.
+__global__ void __launch_bounds__(kRedThreads)
+    norm2_split_kernel(const uint16_t* __restrict__ hi, const uint16_t* __restrict__ lo, int64_t n,
+                       double* __restrict__ out) {
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * kRedThreads;
+  for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += stride) {
+    const double v = (double)(bf16_to_float(hi[i]) + bf16_to_float(lo[i]));
+    acc += v * v;
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
 // fit = 1 - sqrt(max(0, ||T||^2 - ||G||^2)) / ||T||, with out[1] = ||G||^2
 // already reduced by norm2_kernel.
 __global__ void fit_finish_kernel(const double* __restrict__ normT2, double* __restrict__ out) {
@@ -77,6 +92,12 @@ int launch_norm2(int dtype, const void* X, int64_t n, double* out, cudaStream_t 
       break;
     case TUCKER_FP8_E4M3:
       return launch_norm2_fp8(X, n, out, s);
+    case TUCKER_BF16_SPLIT: {
+      const uint16_t* h = static_cast<const uint16_t*>(X);
+      const uint16_t* l = reinterpret_cast<const uint16_t*>(static_cast<const char*>(X) + bf16_split_lo_offset(n));
+      norm2_split_kernel<<<grid, kRedThreads, 0, s>>>(h, l, n, out);
+      break;
+    }
     default:
       return fail(TUCKER_ERR_INVALID_ARG, "norm2: unknown dtype");
   }

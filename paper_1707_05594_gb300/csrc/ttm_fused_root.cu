@@ -228,4 +228,9 @@ int launch_ttm_fused_root(int dtype, const void* X, const int64_t* L, int N, int
   return TUCKER_OK;
 }
 
+bool root_pair_fits(int dtype, int N, const int64_t* L, const int64_t* K, int a, int b) {
+  if (fused_root_fits(dtype, N, L, K, a, b)) return true;
+  return dtype == TUCKER_F32 && ttm_x3_pair_supported(L, N, a, b, K[a], K[b], nullptr);
+}
+
 }  // namespace tk

@@ -440,6 +440,16 @@ int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, cons
       if ((kernel_policy() & 5) == 4 && ttm_tc_f32_supported(R, L, C, K, X))
         return launch_ttm_tc_f32(static_cast<const float*>(X), R, L, C, static_cast<const float*>(F), K,
                                  static_cast<float*>(Y), s);
+      // column case on the tensor cores when a policy bit asks for it:
+      // exact integer slices (bit 32) or the TF32 split kernel (bit 64)
+      if ((kernel_policy() & 1) == 0 && C > 1) {
+        if ((kernel_policy() & 64) && ttm_tf32_supported(R, L, C, K, X))
+          return launch_ttm_tf32(static_cast<const float*>(X), R, L, C, static_cast<const float*>(F), K,
+                                 static_cast<float*>(Y), s);
+        if ((kernel_policy() & (32 | 64)) == 32 && ttm_x3_supported(R, L, C, K, X))
+          return launch_ttm_x3(static_cast<const float*>(X), R, L, C, static_cast<const float*>(F), K,
+                               static_cast<float*>(Y), s);
+      }
       if ((kernel_policy() & 8) == 0 && ttm_slab_preferred(TUCKER_F32, R, L, C, K))
         return launch_ttm_slab(TUCKER_F32, X, R, L, C, static_cast<const float*>(F), K, Y, y_dtype, s);
       return launch_typed<float, float>(X, R, L, C, F, K, Y, s);
@@ -467,6 +477,15 @@ int launch_ttm(int x_dtype, const void* X, int64_t R, int64_t L, int64_t C, cons
     }
     case TUCKER_FP8_E4M3:
       return launch_ttm_fp8(X, R, L, C, static_cast<const float*>(F), K, Y, y_dtype, s);
+    case TUCKER_BF16_SPLIT: {
+      // hi and lo halves of one buffer; the tensor cores multiply both
+      if (y_dtype != TUCKER_F32)
+        return fail(TUCKER_ERR_UNSUPPORTED, "ttm: split BF16 input needs FP32 output");
+      const void* X_lo = static_cast<const char*>(X) + bf16_split_lo_offset(R * L * C);
+      if ((kernel_policy() & 1) != 0 || !ttm_tc_supported(R, L, C, K, X, X_lo))
+        return fail(TUCKER_ERR_UNSUPPORTED, "ttm: split BF16 tensors are read by the tensor cores only");
+      return launch_ttm_tc(X, X_lo, R, L, C, static_cast<const float*>(F), K, Y, false, s);
+    }
     default: return fail(TUCKER_ERR_INVALID_ARG, "ttm: unknown dtype");
   }
 }

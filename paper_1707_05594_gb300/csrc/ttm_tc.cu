@@ -33,13 +33,15 @@
 #include <atomic>
 #include <mutex>
 
-#include "common.cuh"
+#include "tc_common.cuh"
 
 namespace tk {
 
 __device__ int g_tk_status = 0;  // 0 = ok, else the code of the first timeout
 
 namespace {
+
+using namespace tc;
 
 constexpr int kStagesPlain = 8;  // ring depth, one A tensor per stage
 constexpr int kStagesSplit = 5;  // ring depth, hi and lo A tensors per stage
@@ -50,80 +52,11 @@ constexpr int kStageBytes = kTileM * kBoxL * 2;  // one A tensor, 16 KB
 constexpr int kAccBufs = 4;      // TMEM accumulator buffers
 constexpr int kEpiGroups = 2;    // epilogue warp groups (4 warps each), alternate tiles
 constexpr int kThreads = 64 + kEpiGroups * 128;
-constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
+// Bounded wait on this translation unit's error word (see tc_common.cuh).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  return mbar_wait_status(bar, parity, abort_flag, &g_tk_status);
 }
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: true when the phase completed, false on timeout or when
-// another role has already given up (abort flag).
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 255u) {
-      if (*abort_flag) return false;
-      if (globaltimer() - t0 > kTimeoutNs) {
-        *abort_flag = 1;
-        atomicCAS(&g_tk_status, 0, TUCKER_ERR_TIMEOUT);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
-      "%4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
-      "%4, %5}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading and
-// stride byte offsets (>> 4), version 1, swizzle mode in bits 61-63.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo,
-                                              uint32_t swizzle) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)swizzle << 61);
-}
-constexpr uint32_t kSwizzleNone = 0, kSwizzle128 = 2;
 
 // Instruction descriptor for kind::f16 with BF16 A and B, FP32 accumulate,
 // M = 128, B K-major; A K-major (0) or MN-major (1).
@@ -139,36 +72,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// 16 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 template <typename TOut>
 __device__ __forceinline__ TOut to_out(float v) {
   return OutCvt<TOut>::run(v);
@@ -986,10 +889,11 @@ EncodeFn encoder() {
   return fn;
 }
 
+}  // namespace
+
 int make_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims,
-             const cuuint64_t* strides_bytes, const cuuint32_t* box,
-             CUtensorMapDataType dtype = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-             CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
+             const cuuint64_t* strides_bytes, const cuuint32_t* box, CUtensorMapDataType dtype,
+             CUtensorMapSwizzle swz) {
   EncodeFn enc = encoder();
   if (!enc) return fail(TUCKER_ERR_CUDA, "ttm_tc: cuTensorMapEncodeTiled unavailable");
   const cuuint32_t estr[3] = {1, 1, 1};
@@ -999,6 +903,19 @@ int make_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims,
   if (r != CUDA_SUCCESS) return fail(TUCKER_ERR_CUDA, "ttm_tc: cuTensorMapEncodeTiled failed");
   return TUCKER_OK;
 }
+
+int* device_status_ptr() {
+  static int* ptr = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tk_status) == cudaSuccess) ptr = static_cast<int*>(p);
+  });
+  return ptr;
+}
+
+namespace {
+
 
 size_t smem_bytes(int Np, int nk, bool split_a) {
   const size_t stages = (size_t)stages_for(split_a);
@@ -1029,6 +946,12 @@ bool ttm_tc_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X,
   if (R > INT32_MAX || C > INT32_MAX) return false;
   if (C == 1) return L % 8 == 0 && R >= 1;
   return C % 8 == 0 && C >= 64;
+}
+
+bool ttm_tc_split_fits(int64_t R, int64_t L, int64_t C, int64_t K) {
+  if (!ttm_tc_supported(R, L, C, K, nullptr, nullptr)) return false;
+  const int Np = (int)((K + 15) / 16 * 16), nk = (int)((L + kBoxL - 1) / kBoxL);
+  return smem_bytes(Np, nk, true) <= 227 * 1024;
 }
 
 // Share of a tensor-core tile's work that is the TTM's own: l runs in stages
@@ -1202,8 +1125,8 @@ int kernel_policy() { return g_policy.load(std::memory_order_relaxed); }
 }  // namespace tk
 
 extern "C" int tucker_set_kernel_policy(int policy) {
-  if (policy < 0 || policy > 31)
-    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 31]");
+  if (policy < 0 || policy > 255)
+    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 255]");
   tk::g_policy.store(policy, std::memory_order_relaxed);
   return TUCKER_OK;
 }

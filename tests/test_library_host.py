@@ -303,8 +303,18 @@ def test_plan_flags_validated(tk):
     K = (tk._i64((3, 2, 2)))
     opts = tk.PlanOpts(tk.TUCKER_F32, tk.TREE_OPTIMAL, tk.COST_MACS, 4)
     assert tk.lib().tucker_plan(3, L, K, ctypes.byref(opts), ctypes.byref(h)) == -1
-    # no fused root where the trailing block is too large (200^4: 64 MB)
-    assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (20,) * 4)) is None
+    # the trailing block of 200^4 (64 MB) is too large for the fused kernel:
+    # its BF16 plan keeps the root children apart, while its FP32 plan takes
+    # the L2-blocked tensor-core pair (modes 0 and 2, blocked by mode 1)
+    assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (20,) * 4, tk.TUCKER_BF16)) is None
+    p = tk.tucker_plan((200,) * 4, (20,) * 4)
+    f = tk.tucker_plan_fused_root(p)
+    assert f is not None
+    nodes = tk.tucker_plan_nodes(p)
+    assert sorted(nodes[u]["label"] for u in f) == [0, 2]
+    # the pair needs one mode between its two modes, a 16-byte row stride and K <= 32
+    assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (40,) * 4)) is None
+    assert tk.tucker_plan_fused_root(tk.tucker_plan((200, 200, 200, 201), (20,) * 4)) is None
 
 
 def test_elems_cost_model(tk, orc):
