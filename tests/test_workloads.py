@@ -101,3 +101,15 @@ def test_named_workloads_match_their_stated_sizes():
     assert W["uneven6"]["K"] == (16, 14, 12, 10, 8, 6)
     assert W["small_hooi"]["L"] == (64,) * 3 and W["small_hooi"]["dtype"] == torch.float64
     assert workloads.BATCH_WORKLOADS["batch4096"]["count"] == 4096
+
+
+def test_perturbed_factors_are_orthonormal_and_seeded():
+    F = [workloads.orthonormal_factor(30, 5, workloads._gen(1, torch.device("cpu")), "cpu")]
+    a = workloads.perturbed_factors(F, 0.05, 7)
+    b = workloads.perturbed_factors(F, 0.05, 7)
+    c = workloads.perturbed_factors(F, 0.05, 8)
+    assert torch.equal(a[0], b[0]) and not torch.equal(a[0], c[0])
+    assert torch.allclose(a[0].T @ a[0], torch.eye(5, dtype=torch.float64), atol=1e-12)
+    # close to the input subspace, but not equal to it
+    s = torch.linalg.svdvals(F[0].T @ a[0])
+    assert 0.8 < float(s.min()) < 1.0

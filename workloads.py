@@ -132,6 +132,23 @@ def random_factor(L: int, K: int, seed: int, dtype=torch.float32, device="cpu",
     return torch.randn(L, K, generator=g, device=device, dtype=torch.float64).to(dtype)
 
 
+def perturbed_factors(Fs, eps: float, seed: int):
+    """Starting factors near given ones: Q of the QR of F + eps * Gaussian
+    (float64, on the host; positive R diagonal), one per factor -- the input
+    factors that full-size parity tests hand to the GPU sweep and to the
+    oracle's sweep alike."""
+    g = _gen(seed, torch.device("cpu"))
+    out = []
+    for F in Fs:
+        F = F.detach().to("cpu", torch.float64)
+        A = F + eps * torch.randn(F.shape, generator=g, dtype=torch.float64)
+        Q, R = torch.linalg.qr(A)
+        s = torch.sign(torch.diagonal(R))
+        s[s == 0] = 1
+        out.append((Q * s).contiguous())
+    return out
+
+
 # The named workloads used by bench.py and the parity tests.
 WORKLOADS = {
     "small_hooi": dict(L=(64, 64, 64), K=(8, 8, 8), rho=1e-3, seed=1, spectrum=None,
