@@ -75,10 +75,10 @@ struct ProfScope {
 std::atomic<uint64_t> g_launches{0};
 
 // Both root children Ya = X x_a Fa^T, Yb = X x_b Fb^T (a < b): from one read
-// of X by the fused kernel when the trailing block fits, else (FP32 tensors,
-// 16-byte aligned, a tensor-core policy bit set) by the tensor-core pair that
-// reads X once blocked by mode a + 1 -- exact slices under policy bit 32, TF32
-// under bit 64 -- else as two TTMs.
+// of X by the fused kernel when the trailing block fits, else by a
+// tensor-core pair that reads X once blocked by mode a + 1 (BF16 tensors; FP32
+// tensors when a policy bit selects exact slices (32) or TF32 (64)), else as
+// two TTMs.
 int launch_root_pair(int dtype, const void* X, const int64_t* L, int N, int a, int b, const float* Fa,
                      int64_t Ka, const float* Fb, int64_t Kb, void* Ya, void* Yb, int y_dtype,
                      cudaStream_t s) {
@@ -88,6 +88,9 @@ int launch_root_pair(int dtype, const void* X, const int64_t* L, int N, int a, i
   K[b] = Kb;
   if (fused_root_fits(dtype, N, L, K, a, b))
     return launch_ttm_fused_root(dtype, X, L, N, a, b, Fa, Ka, Fb, Kb, Ya, Yb, y_dtype, s);
+  if (dtype == TUCKER_BF16 && (y_dtype == TUCKER_BF16 || y_dtype == TUCKER_F32) && (kernel_policy() & 1) == 0 &&
+      ttm_tc_pair_supported(L, N, a, b, Ka, Kb, X))
+    return launch_ttm_tc_pair(X, L, N, a, b, Fa, Ka, Fb, Kb, Ya, Yb, y_dtype == TUCKER_BF16, s);
   if (dtype == TUCKER_F32 && y_dtype == TUCKER_F32 && (kernel_policy() & 1) == 0) {
     const float* x = static_cast<const float*>(X);
     if ((kernel_policy() & 64) && ttm_tf32_pair_supported(L, N, a, b, Ka, Kb, X))

@@ -290,6 +290,11 @@ int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t
                   const float* F, int64_t K, void* Y, bool y_bf16, cudaStream_t s);
 // useful share of the tensor-core tiles for a shape (l stages of 64, 128-position tiles)
 double ttm_tc_efficiency(int64_t L, int64_t C);
+// the two root children (modes a, b = a + 2) of a BF16 tensor from one pass
+// over it blocked by mode a + 1 (ttm_tc_pair_kernel)
+bool ttm_tc_pair_supported(const int64_t* dims, int N, int a, int b, int64_t Ka, int64_t Kb, const void* X);
+int launch_ttm_tc_pair(const void* X, const int64_t* dims, int N, int a, int b, const float* Fa, int64_t Ka,
+                       const float* Fb, int64_t Kb, void* Ya, void* Yb, bool y_bf16, cudaStream_t s);
 // Short-row TTMs (ttm_slab.cu): C == 1 with 256 * L elements in 32 KB, or
 // 1 < C < 64 with a slab of L * C elements in 8 KB; FP32 or BF16 input, F
 // FP32, K <= 32; Y FP32 (or BF16 for BF16 input).

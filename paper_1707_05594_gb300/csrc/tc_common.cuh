@@ -65,6 +65,36 @@ __device__ __noinline__ bool mbar_wait_status(uint64_t* bar, uint32_t parity, vo
   }
 }
 
+// One try_wait that may suspend the thread (up to hint_ns) until the phase
+// completes, instead of returning at once: a waiting warp then takes no issue
+// slots from the warps that do the work.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait as mbar_wait_status, each attempt suspending the thread for up
+// to 20 us; the deadline and the abort flag are checked between attempts.
+__device__ __noinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                             int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (;;) {
+    if (mbar_try_wait_hint(bar, parity, 20000u)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      atomicCAS(status, 0, TUCKER_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {
   asm volatile(

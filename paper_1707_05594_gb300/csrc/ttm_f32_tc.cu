@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
         const CUtensorMap* map = t.j == 0 ? &map0 : &map1;
         for (int kc = 0; kc < J.nk; ++kc, ++it) {
           const uint32_t s = it % nst, ph = (it / nst) & 1u;
-          if (!mbar_wait_status(&st_empty[s], ph ^ 1u, abort_flag, P.status)) {
+          if (!mbar_wait_sleep(&st_empty[s], ph ^ 1u, abort_flag, P.status)) {
             ok = false;
             break;
           }
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
         for (int kc = 0; kc < J.nk; ++kc, ++it) {
           if (P.chunk_acc || kc == 0) {
             buf = cnt % kT32AccBufs;
-            if (!mbar_wait_status(&acc_empty[buf], ((cnt / kT32AccBufs) & 1u) ^ 1u, abort_flag, P.status)) {
+            if (!mbar_wait_sleep(&acc_empty[buf], ((cnt / kT32AccBufs) & 1u) ^ 1u, abort_flag, P.status)) {
               ok = false;
               break;
             }
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
             d_tmem = tmem_base + acc_col0 + buf * (uint32_t)kT32AccCols;
           }
           const uint32_t as = it % kT32AStages, aph = (it / kT32AStages) & 1u;
-          if (!mbar_wait_status(&a_full[as], aph, abort_flag, P.status)) {
+          if (!mbar_wait_sleep(&a_full[as], aph, abort_flag, P.status)) {
             ok = false;
             break;
           }
@@ -340,8 +340,8 @@ __global__ void __launch_bounds__(kT32Threads, 1)
       for (int kc = 0; kc < J.nk; ++kc, ++it) {
         const uint32_t s = it % nst, ph = (it / nst) & 1u;
         const uint32_t as = it % kT32AStages, aph = (it / kT32AStages) & 1u;
-        if (!mbar_wait_status(&st_full[s], ph, abort_flag, P.status) ||
-            !mbar_wait_status(&a_empty[as], aph ^ 1u, abort_flag, P.status)) {
+        if (!mbar_wait_sleep(&st_full[s], ph, abort_flag, P.status) ||
+            !mbar_wait_sleep(&a_empty[as], aph ^ 1u, abort_flag, P.status)) {
           ok = false;
           break;
         }
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
       const int nbuf = P.chunk_acc ? J.nk : 1;
       for (int b = 0; b < nbuf; ++b, ++cnt) {
         const uint32_t buf = cnt % kT32AccBufs;
-        if (!mbar_wait_status(&acc_full[buf], (cnt / kT32AccBufs) & 1u, abort_flag, P.status)) {
+        if (!mbar_wait_sleep(&acc_full[buf], (cnt / kT32AccBufs) & 1u, abort_flag, P.status)) {
           ok = false;
           break;
         }
@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
         const CUtensorMap* map = t.j == 0 ? &map0 : &map1;
         for (int kc = 0; kc < J.nk; ++kc, ++it) {
           const uint32_t s = it % nst, ph = (it / nst) & 1u;
-          if (!mbar_wait_status(&st_empty[s], ph ^ 1u, abort_flag, P.status)) {
+          if (!mbar_wait_sleep(&st_empty[s], ph ^ 1u, abort_flag, P.status)) {
             ok = false;
             break;
           }
@@ -705,12 +705,12 @@ __global__ void __launch_bounds__(kT32Threads, 1)
         const uint32_t id3 = idesc_bf16_kk(3 * J.Kp), id2 = idesc_bf16_kk(2 * J.Kp);
         for (int kc = 0; kc < J.nk; ++kc, ++it) {
           const uint32_t buf = it % nacc;
-          if (!mbar_wait_status(&acc_empty[buf], ((it / nacc) & 1u) ^ 1u, abort_flag, P.status)) {
+          if (!mbar_wait_sleep(&acc_empty[buf], ((it / nacc) & 1u) ^ 1u, abort_flag, P.status)) {
             ok = false;
             break;
           }
           const uint32_t as = it % kXAStages, aph = (it / kXAStages) & 1u;
-          if (!mbar_wait_status(&a_full[as], aph, abort_flag, P.status)) {
+          if (!mbar_wait_sleep(&a_full[as], aph, abort_flag, P.status)) {
             ok = false;
             break;
           }
@@ -744,8 +744,8 @@ __global__ void __launch_bounds__(kT32Threads, 1)
       for (int kc = 0; kc < J.nk; ++kc, ++it) {
         const uint32_t s = it % nst, ph = (it / nst) & 1u;
         const uint32_t as = it % kXAStages, aph = (it / kXAStages) & 1u;
-        if (!mbar_wait_status(&st_full[s], ph, abort_flag, P.status) ||
-            !mbar_wait_status(&a_empty[as], aph ^ 1u, abort_flag, P.status)) {
+        if (!mbar_wait_sleep(&st_full[s], ph, abort_flag, P.status) ||
+            !mbar_wait_sleep(&a_empty[as], aph ^ 1u, abort_flag, P.status)) {
           ok = false;
           break;
         }
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
         xb[half * 128 + p] = m;
         __syncwarp();
         if (lane == 0) mbar_arrive(&xchg[q]);
-        if (!mbar_wait_status(&xchg[q], it & 1u, abort_flag, P.status)) {
+        if (!mbar_wait_sleep(&xchg[q], it & 1u, abort_flag, P.status)) {
           ok = false;
           break;
         }
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
         if (half == 0) {
           // the chunk's position scale for the epilogue
           const uint32_t j = it % kXSxRing;
-          if (!mbar_wait_status(&sx_empty[j], ((it / kXSxRing) & 1u) ^ 1u, abort_flag, P.status)) {
+          if (!mbar_wait_sleep(&sx_empty[j], ((it / kXSxRing) & 1u) ^ 1u, abort_flag, P.status)) {
             ok = false;
             break;
           }
@@ -826,8 +826,8 @@ __global__ void __launch_bounds__(kT32Threads, 1)
       for (int i = 0; i < 32; ++i) y[i] = 0.f;
       for (int kc = 0; kc < J.nk; ++kc, ++it) {
         const uint32_t buf = it % nacc, j = it % kXSxRing;
-        if (!mbar_wait_status(&acc_full[buf], (it / nacc) & 1u, abort_flag, P.status) ||
-            !mbar_wait_status(&sx_full[j], (it / kXSxRing) & 1u, abort_flag, P.status)) {
+        if (!mbar_wait_sleep(&acc_full[buf], (it / nacc) & 1u, abort_flag, P.status) ||
+            !mbar_wait_sleep(&sx_full[j], (it / kXSxRing) & 1u, abort_flag, P.status)) {
           ok = false;
           break;
         }

@@ -230,6 +230,7 @@ int launch_ttm_fused_root(int dtype, const void* X, const int64_t* L, int N, int
 
 bool root_pair_fits(int dtype, int N, const int64_t* L, const int64_t* K, int a, int b) {
   if (fused_root_fits(dtype, N, L, K, a, b)) return true;
+  if (dtype == TUCKER_BF16) return ttm_tc_pair_supported(L, N, a, b, K[a], K[b], nullptr);
   return dtype == TUCKER_F32 && ttm_x3_pair_supported(L, N, a, b, K[a], K[b], nullptr);
 }
 

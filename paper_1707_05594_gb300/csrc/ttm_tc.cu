@@ -851,6 +851,237 @@ __global__ void __launch_bounds__(kF8Threads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// BF16 root pair (column case, L2-blocked).  A sweep's two root children read
+// the same tensor T along modes a and b = a + 2.  With mode m = a + 1 as the
+// block index the work list runs block after block (value of i_m); within a
+// block first the tiles of mode a's TTM (T viewed as [R_a][L_a][L_m * S],
+// tiles of 128 of one block's S positions), then those of mode b's TTM (T
+// viewed as [R_hi][L_m][L_b][C_b], rows of block i_m), so the block of T
+// (|T| / L_m elements, 33 MB at 64^5 in BF16) is read from HBM once and
+// found in L2 by the second TTM.  Per tile the pipeline is ttm_tc_kernel's
+// column case: two 64-position boxes per 64-l stage by TMA (128-byte
+// swizzle, MN-major A), [F_hi | F_lo] of the tile's job as B, four TMEM
+// accumulators, two epilogue groups of four warps on alternate tiles.
+// ---------------------------------------------------------------------------
+struct PairJob {
+  int L, K, Np, nk;
+  int block_c;       // 1: positions g * S + c (mode a); 0: rows (rh * G + g) (mode b)
+  int64_t R;         // rows (mode a) or R_hi (mode b)
+  int64_t S;         // positions per row: S (mode a) or C_b (mode b)
+  int64_t ct;        // 128-position tiles per row
+  int64_t per_block; // tiles per block
+  uint32_t b_off;    // byte offset of this job's B in shared memory
+  const float* F;
+  void* Y;
+};
+struct PairParams {
+  PairJob job[2];
+  int64_t G, per_block, units;
+};
+struct PairTile {
+  int j;
+  int64_t r, c0, g;
+};
+__device__ __forceinline__ PairTile pair_decode(const PairParams& P, int64_t w) {
+  PairTile t;
+  t.g = w / P.per_block;
+  int64_t i = w - t.g * P.per_block;
+  t.j = i >= P.job[0].per_block ? 1 : 0;
+  if (t.j) i -= P.job[0].per_block;
+  const PairJob& J = P.job[t.j];
+  const int64_t row = i / J.ct;
+  t.c0 = (i - row * J.ct) * kTileM;
+  t.r = J.block_c ? row : row * P.G + t.g;
+  return t;
+}
+
+// SMEM (dynamic, 1024-aligned): [A ring: kStagesPlain x 16 KB][B job 0][B job 1]
+//   [barriers][tmem slot][abort flag]
+template <typename TOut>
+__global__ void __launch_bounds__(kThreads, 1)
+    ttm_tc_pair_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+                       const PairParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr uint32_t kStages = (uint32_t)kStagesPlain;
+  unsigned char* ring = smem;
+  unsigned char* bsm = ring + (size_t)kStages * kStageBytes;
+  const size_t b_end = (size_t)P.job[1].b_off + (size_t)P.job[1].nk * 2 * P.job[1].Np * 128;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + ((b_end + 15) & ~size_t(15)));
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kStages;
+  uint64_t* tfull = bars + 2 * kStages;
+  uint64_t* tempty = tfull + kAccBufs;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + kAccBufs);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int N2max = 2 * max(P.job[0].Np, P.job[1].Np);  // accumulator buffer stride
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(kAccBufs * N2max)) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (uint32_t s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < kAccBufs; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // B of each job = [F_hi | F_lo]^T as BF16, K-major without swizzle (as in
+  // ttm_tc_kernel)
+  for (int j = 0; j < 2; ++j) {
+    const PairJob& J = P.job[j];
+    const int N2 = 2 * J.Np;
+    for (int idx = threadIdx.x; idx < N2 * J.nk * kBoxL; idx += kThreads) {
+      const int row = idx / (J.nk * kBoxL);
+      const int l = idx - row * (J.nk * kBoxL);
+      const int k = row < J.Np ? row : row - J.Np;
+      float f = 0.f;
+      if (k < J.K && l < J.L) f = J.F[(int64_t)l * J.K + k];
+      const uint16_t hi = f2bf(f);
+      const float rem = f - __uint_as_float((uint32_t)hi << 16);
+      const uint16_t v = row < J.Np ? hi : f2bf(rem);
+      const int chunk = l / kBoxL, lc = l - chunk * kBoxL;
+      const size_t off = (size_t)J.b_off + (size_t)chunk * N2 * 128 + (size_t)(row >> 3) * 1024 +
+                         (size_t)(lc >> 3) * 128 + (size_t)(row & 7) * 16 + (size_t)(lc & 7) * 2;
+      *reinterpret_cast<uint16_t*>(bsm + off) = v;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
+        const PairTile t = pair_decode(P, w);
+        const PairJob& J = P.job[t.j];
+        const CUtensorMap* map = t.j ? &map1 : &map0;
+        const int cx = (int)(J.block_c ? t.g * J.S + t.c0 : t.c0);
+        for (int kc = 0; kc < J.nk; ++kc, ++it) {
+          const uint32_t s = it % kStages, ph = (it / kStages) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], (uint32_t)kStageBytes);
+          unsigned char* dst = ring + (size_t)s * kStageBytes;
+          tma_load_3d(dst, map, &full[s], cx, kc * kBoxL, (int)t.r);
+          tma_load_3d(dst + kStageBytes / 2, map, &full[s], cx + 64, kc * kBoxL, (int)t.r);
+        }
+      }
+      const uint32_t issued = it;
+      for (uint32_t j = (issued > kStages ? issued - kStages : 0); j < issued; ++j) {
+        const uint32_t s = j % kStages, ph = (j / kStages) & 1u;
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(&full[s], ph) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t b_base = smem_u32(bsm);
+      uint32_t it = 0, tcount = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x, ++tcount) {
+        const PairTile t = pair_decode(P, w);
+        const PairJob& J = P.job[t.j];
+        const int N2 = 2 * J.Np;
+        const uint32_t idesc_full = idesc_bf16(N2, 1);
+        const uint32_t buf = tcount % kAccBufs, aph = (tcount / kAccBufs) & 1u;
+        if (!mbar_wait(&tempty[buf], aph ^ 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + buf * (uint32_t)N2max;
+        for (int kc = 0; kc < J.nk; ++kc, ++it) {
+          const uint32_t s = it % kStages, ph = (it / kStages) & 1u;
+          if (!mbar_wait(&full[s], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(ring + (size_t)s * kStageBytes);
+#pragma unroll
+          for (int ks = 0; ks < kBoxL / 16; ++ks) {
+            const uint64_t ad = smem_desc(a_base + ks * 2048, 8192, 1024, kSwizzle128);
+            const uint32_t b_chunk = b_base + J.b_off + (uint32_t)(kc * N2 * 128);
+            const uint64_t bd = smem_desc(b_chunk + ks * 256, 128, 1024, kSwizzleNone);
+            mma_bf16(d_tmem, ad, bd, idesc_full, (kc > 0 || ks > 0) ? 1u : 0u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[buf]);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t group = (uint32_t)(warp - 2) / 4u;
+    uint32_t tcount = group;
+    for (int64_t w = blockIdx.x + (int64_t)group * gridDim.x; w < P.units;
+         w += (int64_t)kEpiGroups * gridDim.x, tcount += kEpiGroups) {
+      const PairTile t = pair_decode(P, w);
+      const PairJob& J = P.job[t.j];
+      const uint32_t buf = tcount % kAccBufs, aph = (tcount / kAccBufs) & 1u;
+      if (!mbar_wait(&tfull[buf], aph, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + buf * (uint32_t)N2max;
+      const int64_t c = t.c0 + row;
+      int64_t ystride;
+      TOut* yp;
+      if (J.block_c) {
+        ystride = P.G * J.S;
+        yp = static_cast<TOut*>(J.Y) + (t.r * J.K) * ystride + t.g * J.S + c;
+      } else {
+        ystride = J.S;
+        yp = static_cast<TOut*>(J.Y) + (t.r * J.K) * ystride + c;
+      }
+      float hi[16], lo[16];
+      for (int k0 = 0; k0 < J.Np; k0 += 16) {
+        tmem_ld16(tbase + k0, hi);
+        tmem_ld16(tbase + J.Np + k0, lo);
+        tmem_wait_ld();
+        if (k0 + 16 >= J.Np) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+        if (c < J.S) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (k0 + j < J.K) yp[(int64_t)(k0 + j) * ystride] = to_out<TOut>(hi[j] + lo[j]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(ncols));
+  }
+}
+
 // One thread waits, through the kernels' bounded wait, on an mbarrier that no
 // thread or copy ever completes: the wait gives up after its time limit and
 // records TUCKER_ERR_TIMEOUT in the device error word, and the kernel returns
@@ -1017,6 +1248,95 @@ int launch_ttm_tc(const void* X, const void* X_lo, int64_t R, int64_t L, int64_t
                   : launch_variant<false, true, float>(mh, ml, Y, P, smem, s);
   return y_bf16 ? launch_variant<false, false, bf16_t>(mh, ml, Y, P, smem, s)
                 : launch_variant<false, false, float>(mh, ml, Y, P, smem, s);
+}
+
+// The BF16 root pair (ttm_tc_pair_kernel): modes a and b = a + 2 of a BF16
+// tensor blocked by mode a + 1; S = prod dims[a+2..] and C_b = prod
+// dims[b+1..] multiples of 8 (16-byte TMA coordinates) and >= 64, K <= 64,
+// L <= 1024, both B operands within shared memory, 32-bit coordinates.
+bool ttm_tc_pair_supported(const int64_t* dims, int N, int a, int b, int64_t Ka, int64_t Kb, const void* X) {
+  if (a < 0 || b != a + 2 || b >= N) return false;
+  if (Ka < 1 || Ka > 64 || Kb < 1 || Kb > 64 || dims[a] > 1024 || dims[b] > 1024) return false;
+  const int m = a + 1;
+  const int64_t S = prod(dims, m + 1, N), Cb = prod(dims, b + 1, N);
+  if (S < 64 || S % 8 != 0 || Cb < 64 || Cb % 8 != 0) return false;
+  if ((uintptr_t)X % 16 != 0 || S * dims[m] > INT32_MAX || prod(dims, 0, a) > INT32_MAX ||
+      prod(dims, 0, b) > INT32_MAX)
+    return false;
+  const int64_t Npa = (Ka + 15) / 16 * 16, Npb = (Kb + 15) / 16 * 16;
+  const size_t bb = (size_t)((dims[a] + kBoxL - 1) / kBoxL) * 2 * Npa * 128 +
+                    (size_t)((dims[b] + kBoxL - 1) / kBoxL) * 2 * Npb * 128;
+  const size_t smem = 1024 + (size_t)kStagesPlain * kStageBytes + ((bb + 15) & ~size_t(15)) +
+                      (2 * kStagesPlain + 2 * kAccBufs) * 8 + 16;
+  return smem <= 227 * 1024 && 4 * 2 * std::max(Npa, Npb) <= 512;
+}
+
+int launch_ttm_tc_pair(const void* X, const int64_t* dims, int N, int a, int b, const float* Fa, int64_t Ka,
+                       const float* Fb, int64_t Kb, void* Ya, void* Yb, bool y_bf16, cudaStream_t s) {
+  if (!ttm_tc_pair_supported(dims, N, a, b, Ka, Kb, X))
+    return fail(TUCKER_ERR_UNSUPPORTED, "ttm_tc_pair: shape or alignment not supported");
+  const int m = a + 1;
+  PairParams P{};
+  P.G = dims[m];
+  PairJob& A = P.job[0];
+  A.L = (int)dims[a];
+  A.K = (int)Ka;
+  A.Np = (int)((Ka + 15) / 16 * 16);
+  A.nk = (int)((dims[a] + kBoxL - 1) / kBoxL);
+  A.block_c = 1;
+  A.R = prod(dims, 0, a);
+  A.S = prod(dims, m + 1, N);
+  A.ct = (A.S + kTileM - 1) / kTileM;
+  A.per_block = A.R * A.ct;
+  A.b_off = 0;
+  A.F = Fa;
+  A.Y = Ya;
+  PairJob& B = P.job[1];
+  B.L = (int)dims[b];
+  B.K = (int)Kb;
+  B.Np = (int)((Kb + 15) / 16 * 16);
+  B.nk = (int)((dims[b] + kBoxL - 1) / kBoxL);
+  B.block_c = 0;
+  B.R = prod(dims, 0, m);
+  B.S = prod(dims, b + 1, N);
+  B.ct = (B.S + kTileM - 1) / kTileM;
+  B.per_block = B.R * B.ct;
+  B.b_off = (uint32_t)((size_t)A.nk * 2 * A.Np * 128);
+  B.F = Fb;
+  B.Y = Yb;
+  P.per_block = A.per_block + B.per_block;
+  P.units = P.G * P.per_block;
+  CUtensorMap ma, mb;
+  {
+    const int64_t Ca = P.G * A.S;
+    const cuuint64_t d3[3] = {(cuuint64_t)Ca, (cuuint64_t)A.L, (cuuint64_t)A.R};
+    const cuuint64_t st[2] = {(cuuint64_t)Ca * 2, (cuuint64_t)(Ca * A.L) * 2};
+    const cuuint32_t box[3] = {64, kBoxL, 1};
+    const int rc = make_map(&ma, X, 3, d3, st, box);
+    if (rc) return rc;
+  }
+  {
+    const cuuint64_t d3[3] = {(cuuint64_t)B.S, (cuuint64_t)B.L, (cuuint64_t)prod(dims, 0, b)};
+    const cuuint64_t st[2] = {(cuuint64_t)B.S * 2, (cuuint64_t)(B.S * B.L) * 2};
+    const cuuint32_t box[3] = {64, kBoxL, 1};
+    const int rc = make_map(&mb, X, 3, d3, st, box);
+    if (rc) return rc;
+  }
+  const size_t bb = (size_t)B.b_off + (size_t)B.nk * 2 * B.Np * 128;
+  const size_t smem = 1024 + (size_t)kStagesPlain * kStageBytes + ((bb + 15) & ~size_t(15)) +
+                      (2 * kStagesPlain + 2 * kAccBufs) * 8 + 16;
+  const int64_t grid = std::min<int64_t>(P.units, sm_count());
+  if (y_bf16) {
+    auto kern = ttm_tc_pair_kernel<bf16_t>;
+    TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)grid, kThreads, smem, s>>>(ma, mb, P);
+  } else {
+    auto kern = ttm_tc_pair_kernel<float>;
+    TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)grid, kThreads, smem, s>>>(ma, mb, P);
+  }
+  TK_LAUNCH_CHECK("ttm_tc_pair");
+  return TUCKER_OK;
 }
 
 size_t smem_bytes_f32(int Np, int nk) {

@@ -266,3 +266,51 @@ def test_sweeps_with_exact_slices_match_oracle(tk, orc, L, K, rho, seed):
         assert abs(fit_g - fit_o) <= 1e-5 * fit_o, (s, fit_g, fit_o)
         for n in range(len(L)):
             assert sin_angle(Fg[n], Fo[n]) <= 1e-4, (s, n)
+
+
+BF16_PAIR_CASES = [
+    ((64, 64, 64, 64), 0, 16, 16),
+    ((3, 40, 7, 36, 64), 1, 9, 32),
+    ((70, 5, 96, 136), 0, 20, 7),
+    ((8, 64, 64, 64, 64), 1, 16, 5),
+]
+
+
+@pytest.mark.parametrize("shape,a,Ka,Kb", BF16_PAIR_CASES)
+@pytest.mark.parametrize("ydt", [torch.bfloat16, torch.float32])
+def test_bf16_tensor_core_pair_equals_single_ttms(tk, orc, shape, a, Ka, Kb, ydt):
+    """The BF16 root pair from one pass over T blocked by mode a + 1 gives the
+    bits of the two single tensor-core TTMs (policy 16: tensor cores wherever
+    the shape allows; each output position is summed by the same MMAs in the
+    same order whichever tile holds it), and those are within the BF16
+    tensor-core bound of the oracle used for the single TTM (F carried as
+    [F_hi | F_lo], FP32 accumulation in TMEM):
+    (2^-15 + (L + 2) 2^-23) * sum |x f|."""
+    b = a + 2
+    X = workloads.random_tensor(shape, seed=sum(shape) + 17 * a, dtype=torch.bfloat16).cuda()
+    Fa = workloads.random_factor(shape[a], Ka, seed=Ka + 3, dtype=torch.float32, orthonormal=False).cuda()
+    Fb = workloads.random_factor(shape[b], Kb, seed=Kb + 4, dtype=torch.float32, orthonormal=False).cuda()
+    oa, ob = list(shape), list(shape)
+    oa[a], ob[b] = Ka, Kb
+    Ya, Yb = torch.empty(oa, dtype=ydt, device="cuda"), torch.empty(ob, dtype=ydt, device="cuda")
+    Ya1, Yb1 = torch.empty(oa, dtype=torch.float32, device="cuda"), torch.empty(ob, dtype=torch.float32, device="cuda")
+    tk.tucker_ttm_pair(X, a, Fa, Ya, b, Fb, Yb)
+    assert tk.lib().tucker_set_kernel_policy(16) == 0
+    try:
+        tk.tucker_ttm(X, a, Fa, Ya1)
+        tk.tucker_ttm(X, b, Fb, Yb1)
+        torch.cuda.synchronize()
+    finally:
+        tk.lib().tucker_set_kernel_policy(0)
+    assert status_ok(tk)
+    if ydt == torch.float32:
+        assert torch.equal(Ya, Ya1) and torch.equal(Yb, Yb1)
+    else:
+        assert torch.equal(Ya, Ya1.to(torch.bfloat16)) and torch.equal(Yb, Yb1.to(torch.bfloat16))
+    Xd = X.double().cpu().numpy()
+    for n, F, Y in ((a, Fa, Ya1), (b, Fb, Yb1)):
+        Fd = F.double().cpu().numpy()
+        ref = orc.ttm(Xd, n, Fd.T)
+        mag = orc.ttm(np.abs(Xd), n, np.abs(Fd).T)
+        bound = (2.0 ** -15 + (shape[n] + 2) * 2.0 ** -23) * mag
+        assert np.all(np.abs(Y.double().cpu().numpy() - ref) <= bound)

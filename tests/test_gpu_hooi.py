@@ -397,3 +397,40 @@ def test_sthosvd_in_planned_order_matches_oracle(tk, orc, L, K, rho, seed, dtype
     for n in range(len(L)):
         if K[n] < L[n]:
             assert sin_angle(d.F[n].double().cpu().numpy(), F1o[n]) <= ang_bar, n
+
+
+@pytest.mark.parametrize("L,K,rho,seed", [
+    ((4, 4, 20, 20, 20), (2, 2, 4, 4, 4), 0.3, 91),
+    ((16, 16, 40, 40, 40), (8, 8, 16, 16, 16), 1e-2, 92),
+])
+def test_elements_objective_tree_sweeps_match_oracle(tk, orc, L, K, rho, seed):
+    """A plan built with the elements-moved objective (TUCKER_COST_ELEMS) on a
+    shape where it chooses a different TTM-tree from the multiply-add
+    objective of Sec. 3.1: its sweeps still compute Fig. 2's HOOI (every
+    tree yields the same Z_n), so STHOSVD + 3 sweeps match the oracle's chain
+    sweeps at the FP32 bars, like the MAC-optimal tree's sweeps."""
+    pm = tk.tucker_plan(L, K)
+    pe = tk.tucker_plan(L, K, cost_model=tk.COST_ELEMS)
+    tm = [(n["label"], n["parent"]) for n in tk.tucker_plan_nodes(pm)]
+    te = [(n["label"], n["parent"]) for n in tk.tucker_plan_nodes(pe)]
+    assert tm != te
+    assert tk.tucker_plan_cost(pe)["tree_elems"] < tk.tucker_plan_cost(pm)["tree_elems"]
+    w = workloads.planted_tucker(L, K, rho, seed, dtype=torch.float32)
+    d = tk.Decomposition(w["T"].cuda(), K, cost_model=tk.COST_ELEMS)
+    d.sthosvd()
+    gpu = []
+    for _ in range(3):
+        d.sweep()
+        gpu.append(([f.double().cpu().numpy() for f in d.F], d.fit()))
+    torch.cuda.synchronize()
+    Tn = w["T"].numpy()
+    nT2 = orc.norm2(Tn)
+    Fo, Go = orc.sthosvd(Tn, K)
+    for s in range(3):
+        Fo, Go = orc.hooi_sweep(Tn, Fo, K)
+        fit_o = orc.fit(nT2, orc.norm2(Go))
+        Fg, fit_g = gpu[s]
+        assert abs(fit_g - fit_o) <= 1e-5 * fit_o, (s, fit_g, fit_o)
+        for n in range(len(L)):
+            if K[n] < L[n]:
+                assert sin_angle(Fg[n], Fo[n]) <= 1e-4, (s, n)

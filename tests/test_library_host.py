@@ -304,14 +304,15 @@ def test_plan_flags_validated(tk):
     opts = tk.PlanOpts(tk.TUCKER_F32, tk.TREE_OPTIMAL, tk.COST_MACS, 4)
     assert tk.lib().tucker_plan(3, L, K, ctypes.byref(opts), ctypes.byref(h)) == -1
     # the trailing block of 200^4 (64 MB) is too large for the fused kernel:
-    # its BF16 plan keeps the root children apart, while its FP32 plan takes
-    # the L2-blocked tensor-core pair (modes 0 and 2, blocked by mode 1)
-    assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (20,) * 4, tk.TUCKER_BF16)) is None
-    p = tk.tucker_plan((200,) * 4, (20,) * 4)
-    f = tk.tucker_plan_fused_root(p)
-    assert f is not None
-    nodes = tk.tucker_plan_nodes(p)
-    assert sorted(nodes[u]["label"] for u in f) == [0, 2]
+    # its FP32 and BF16 plans take the L2-blocked tensor-core pair (modes 0
+    # and 2, blocked by mode 1); FP8 plans keep the root children apart
+    assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (20,) * 4, tk.TUCKER_FP8_E4M3)) is None
+    for dt in (tk.TUCKER_F32, tk.TUCKER_BF16):
+        p = tk.tucker_plan((200,) * 4, (20,) * 4, dt)
+        f = tk.tucker_plan_fused_root(p)
+        assert f is not None
+        nodes = tk.tucker_plan_nodes(p)
+        assert sorted(nodes[u]["label"] for u in f) == [0, 2]
     # the pair needs one mode between its two modes, a 16-byte row stride and K <= 32
     assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (40,) * 4)) is None
     assert tk.tucker_plan_fused_root(tk.tucker_plan((200, 200, 200, 201), (20,) * 4)) is None
