@@ -84,12 +84,11 @@ typedef struct {
  * the trailing block of T from mode a on (L_a * ... * L_{N-1} elements) fits
  * in 8 KB and K_a, K_b <= 32, a sweep computes both children from one read of
  * T (one kernel that stages each block in shared memory and contracts it
- * along a and along b); for FP32 tensors with b = a + 2 whose later lengths
- * meet the tensor-core TTM's conditions, when an FP32 tensor-core policy bit
- * is set (see tucker_set_kernel_policy; otherwise the two run as separate
- * TTMs), one tensor-core kernel computes both, running through T block by
- * block of mode a + 1 (each block read from HBM once and found in L2 by the
- * second mode's tiles).  The second child's buffer then sits after the first
+ * along a and along b); when the plan is made under the kernel-policy bits
+ * for the tensor-core pairs (see tucker_set_kernel_policy) and b = a + 2,
+ * one tensor-core kernel computes both children of an FP32 or BF16 tensor,
+ * running through T block by block of mode a + 1 (each block read from HBM
+ * once and found in L2 by the second mode's tiles).  The second child's buffer then sits after the first
  * child's subtree (see ws_offset), which can enlarge the workspace.  Results
  * are those of the two separate TTMs (the same bits). */
 #define TUCKER_PLAN_NO_FUSED_ROOT 1
@@ -371,8 +370,14 @@ size_t tucker_bf16_split_lo_offset(int64_t n);
  *              zero, which biases every output by ~1e-7 relative and the
  *              fit identity by ~1e-5 on the 1e-2-noise workloads);
  *   bit 7 (128): with bit 6, one accumulator per tile instead of one per
- *              64-l chunk summed in registers.
- * Used to compare the paths.  TUCKER_ERR_INVALID_ARG outside 0..255. */
+ *              64-l chunk summed in registers;
+ *   bit 8 (256): BF16 plans made while it is set compute their two root
+ *              children (modes a, a + 2) with the L2-blocked tensor-core pair
+ *              (see TUCKER_PLAN_NO_FUSED_ROOT; FP32 plans do so under bits 5
+ *              or 6).  Off by default: measured slower than two separate
+ *              tensor-core TTMs on the 64^5 workload.
+ * Bits 5, 6 and 8 are read by tucker_plan (the pair changes the plan's
+ * buffer layout) and by the calls.  TUCKER_ERR_INVALID_ARG outside 0..511. */
 int tucker_set_kernel_policy(int policy);
 
 /* Device error word of the tensor-core kernels: 0, or TUCKER_ERR_TIMEOUT if a

@@ -228,10 +228,17 @@ int launch_ttm_fused_root(int dtype, const void* X, const int64_t* L, int N, int
   return TUCKER_OK;
 }
 
+// The tensor-core pairs are opt-in (kernel policy read when the plan is
+// made): measured slower than two separate TTMs on the 64^5 (BF16) and 200^4
+// (FP32 tensor-core kernels) workloads.
 bool root_pair_fits(int dtype, int N, const int64_t* L, const int64_t* K, int a, int b) {
   if (fused_root_fits(dtype, N, L, K, a, b)) return true;
-  if (dtype == TUCKER_BF16) return ttm_tc_pair_supported(L, N, a, b, K[a], K[b], nullptr);
-  return dtype == TUCKER_F32 && ttm_x3_pair_supported(L, N, a, b, K[a], K[b], nullptr);
+  if (dtype == TUCKER_BF16)
+    return (kernel_policy() & 256) && ttm_tc_pair_supported(L, N, a, b, K[a], K[b], nullptr);
+  if (dtype == TUCKER_F32 && (kernel_policy() & (32 | 64)))
+    return ttm_x3_pair_supported(L, N, a, b, K[a], K[b], nullptr) ||
+           ttm_tf32_pair_supported(L, N, a, b, K[a], K[b], nullptr);
+  return false;
 }
 
 }  // namespace tk

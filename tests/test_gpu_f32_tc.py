@@ -279,7 +279,7 @@ BF16_PAIR_CASES = [
 @pytest.mark.parametrize("shape,a,Ka,Kb", BF16_PAIR_CASES)
 @pytest.mark.parametrize("ydt", [torch.bfloat16, torch.float32])
 def test_bf16_tensor_core_pair_equals_single_ttms(tk, orc, shape, a, Ka, Kb, ydt):
-    """The BF16 root pair from one pass over T blocked by mode a + 1 gives the
+    """The BF16 root pair (policy bit 256) from one pass over T blocked by mode a + 1 gives the
     bits of the two single tensor-core TTMs (policy 16: tensor cores wherever
     the shape allows; each output position is summed by the same MMAs in the
     same order whichever tile holds it), and those are within the BF16
@@ -294,7 +294,11 @@ def test_bf16_tensor_core_pair_equals_single_ttms(tk, orc, shape, a, Ka, Kb, ydt
     oa[a], ob[b] = Ka, Kb
     Ya, Yb = torch.empty(oa, dtype=ydt, device="cuda"), torch.empty(ob, dtype=ydt, device="cuda")
     Ya1, Yb1 = torch.empty(oa, dtype=torch.float32, device="cuda"), torch.empty(ob, dtype=torch.float32, device="cuda")
-    tk.tucker_ttm_pair(X, a, Fa, Ya, b, Fb, Yb)
+    assert tk.lib().tucker_set_kernel_policy(256) == 0  # the BF16 pair is opt-in
+    try:
+        tk.tucker_ttm_pair(X, a, Fa, Ya, b, Fb, Yb)
+    finally:
+        tk.lib().tucker_set_kernel_policy(0)
     assert tk.lib().tucker_set_kernel_policy(16) == 0
     try:
         tk.tucker_ttm(X, a, Fa, Ya1)

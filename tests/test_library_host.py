@@ -304,18 +304,29 @@ def test_plan_flags_validated(tk):
     opts = tk.PlanOpts(tk.TUCKER_F32, tk.TREE_OPTIMAL, tk.COST_MACS, 4)
     assert tk.lib().tucker_plan(3, L, K, ctypes.byref(opts), ctypes.byref(h)) == -1
     # the trailing block of 200^4 (64 MB) is too large for the fused kernel:
-    # its FP32 and BF16 plans take the L2-blocked tensor-core pair (modes 0
-    # and 2, blocked by mode 1); FP8 plans keep the root children apart
-    assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (20,) * 4, tk.TUCKER_FP8_E4M3)) is None
-    for dt in (tk.TUCKER_F32, tk.TUCKER_BF16):
-        p = tk.tucker_plan((200,) * 4, (20,) * 4, dt)
-        f = tk.tucker_plan_fused_root(p)
-        assert f is not None
-        nodes = tk.tucker_plan_nodes(p)
-        assert sorted(nodes[u]["label"] for u in f) == [0, 2]
-    # the pair needs one mode between its two modes, a 16-byte row stride and K <= 32
-    assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (40,) * 4)) is None
-    assert tk.tucker_plan_fused_root(tk.tucker_plan((200, 200, 200, 201), (20,) * 4)) is None
+    # by default its plans keep the root children apart; made under the
+    # tensor-core pair policy bits (32 for FP32, 256 for BF16) they take the
+    # L2-blocked pair (modes 0 and 2, blocked by mode 1); FP8 plans never do
+    for dt in (tk.TUCKER_F32, tk.TUCKER_BF16, tk.TUCKER_FP8_E4M3):
+        assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (20,) * 4, dt)) is None
+    for dt, pol in ((tk.TUCKER_F32, 32), (tk.TUCKER_BF16, 256), (tk.TUCKER_FP8_E4M3, 32 | 256)):
+        assert tk.lib().tucker_set_kernel_policy(pol) == 0
+        try:
+            p = tk.tucker_plan((200,) * 4, (20,) * 4, dt)
+            f = tk.tucker_plan_fused_root(p)
+            if dt == tk.TUCKER_FP8_E4M3:
+                assert f is None
+                continue
+            assert f is not None
+            nodes = tk.tucker_plan_nodes(p)
+            assert sorted(nodes[u]["label"] for u in f) == [0, 2]
+            # the pair needs a 16-byte row stride and K within the kernel's
+            # accumulators (32 for FP32, 64 for BF16)
+            kbig = 40 if dt == tk.TUCKER_F32 else 80
+            assert tk.tucker_plan_fused_root(tk.tucker_plan((200,) * 4, (kbig,) * 4, dt)) is None
+            assert tk.tucker_plan_fused_root(tk.tucker_plan((200, 200, 200, 201), (20,) * 4, dt)) is None
+        finally:
+            tk.lib().tucker_set_kernel_policy(0)
 
 
 def test_elems_cost_model(tk, orc):
