@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--unfused", action="store_true",
                     help="time hooi_sweep + a separate core chain + fit per step")
     ap.add_argument("--kernel-policy", type=int, default=0,
-                    help="0: tensor cores where supported (default); 1: CUDA cores only")
+                    help="kernel selection bits of tucker_set_kernel_policy (0: the defaults; "
+                         "1: CUDA cores only; 256: the BF16 tensor-core root pair, ...)")
     ap.add_argument("--planner", action="store_true",
                     help="host only: TTM-tree loads of the optimal tree vs the prior trees over the "
                          "paper's metadata benchmark (5-D and 6-D) and its real-tensor metadata")
@@ -150,6 +151,7 @@ def run_ttm_pair_only(args):
     sa[a], sb[b] = Ka, Kb
     Ya = torch.empty(sa, dtype=dt, device="cuda")
     Yb = torch.empty(sb, dtype=dt, device="cuda")
+    tk.lib().tucker_set_kernel_policy(args.kernel_policy)
     for _ in range(args.warmup):
         tk.tucker_ttm_pair(X, a, Fa, Ya, b, Fb, Yb)
     torch.cuda.synchronize()

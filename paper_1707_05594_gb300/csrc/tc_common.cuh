@@ -95,6 +95,12 @@ __device__ __noinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, vol
   }
 }
 
+// Brings a tensor map (a kernel parameter) into the TMA unit's descriptor
+// cache ahead of its first use.
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {
   asm volatile(

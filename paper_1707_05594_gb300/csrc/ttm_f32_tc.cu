@@ -150,6 +150,9 @@ struct Tile {
   int64_t g;       // block
 };
 
+// The work list runs block after block (value of the block mode), each
+// block's job-0 tiles and then its job-1 tiles (an interleaved order measured
+// slower, as for the BF16 pair).
 __device__ __forceinline__ Tile decode(const Tf32Params& P, int64_t w) {
   Tile t;
   t.g = w / P.per_block;
