@@ -577,32 +577,39 @@ __global__ void __launch_bounds__(kF32Threads, 1)
 
 // ---------------------------------------------------------------------------
 // FP8 E4M3 tensors (one FP32 scale per 64 consecutive elements) on the tensor
-// cores (column case, C % 64 == 0).  TMA brings 128 c x 64 l tiles of codes
-// (8 KB) into a staging ring (no swizzle); a converter of eight warps decodes
-// eight codes at a time, multiplies them by their block's scale (exact in
-// FP32: a 4-bit significand times a 24-bit one) and writes the value rounded
-// to BF16 (relative 2^-9, a 32nd of the E4M3 step) in the 128-byte-swizzled
-// MN-major layout; per k-step the MMA warp issues A [F_hi | F_lo], so F keeps
-// ~16 bits.  Warp roles: warp 0 TMA producer, warp 1 TMEM + MMA issuer,
-// warps 2-9 converter, warps 10-17 two epilogue groups.
+// cores (column case, C % 256 == 0).  TMA brings 128 c x 64 l tiles of codes
+// (8 KB) into a staging ring (no swizzle) and, on the same barrier, the
+// tile's scales: the scale array read as [R L][C / 64] rows, a 4 x 64 box
+// from the 16-byte-aligned column at or below c0 / 64 (the tile's two scale
+// columns sit at 0 or 2 within it).  A converter of eight warps decodes eight
+// codes at a time, multiplies them by their block's scale (exact in FP32: a
+// 4-bit significand times a 24-bit one) and writes the value rounded to BF16
+// (relative 2^-9, a 32nd of the E4M3 step) in the 128-byte-swizzled MN-major
+// layout; per k-step the MMA warp issues A [F_hi | F_lo], so F keeps ~16
+// bits.  The converter issues no global loads (earlier versions read the
+// scales with per-thread loads six stages ahead).  Warp roles: warp 0 TMA
+// producer, warp 1 TMEM + MMA issuer, warps 2-9 converter, warps 10-17 two
+// epilogue groups.
 // ---------------------------------------------------------------------------
 constexpr int kF8St = 12;                         // staging stages (codes): 96 KB in flight
 constexpr int kF8Cv = 3;                          // converted stages (BF16)
 constexpr int kF8Warps = 8;                       // converter warps
 constexpr int kF8StageBytes = kTileM * kBoxL;     // 8 KB
+constexpr int kF8ScaleBytes = 4 * kBoxL * 4;       // 4 scale columns x 64 rows (1 KB)
 constexpr int kF8CvBytes = kStageBytes;           // 16 KB
 constexpr int kF8Threads = 64 + kF8Warps * 32 + kEpiGroups * 128;
 
 template <typename TOut>
 __global__ void __launch_bounds__(kF8Threads, 1)
-    ttm_tc_fp8_kernel(const __grid_constant__ CUtensorMap map_q, const float* __restrict__ scales,
+    ttm_tc_fp8_kernel(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_s,
                       TOut* __restrict__ Y, const TcParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* stage = smem;                                        // kF8St x 8 KB
   unsigned char* conv = stage + (size_t)kF8St * kF8StageBytes;        // kF8Cv x 16 KB
-  unsigned char* bsm = conv + (size_t)kF8Cv * kF8CvBytes;
+  unsigned char* ssm = conv + (size_t)kF8Cv * kF8CvBytes;             // kF8St x 1 KB scales
+  unsigned char* bsm = ssm + (size_t)kF8St * kF8ScaleBytes;
   const int N2 = 2 * P.Np;
   const size_t b_bytes = (size_t)P.nk * N2 * 128;
   uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + ((b_bytes + 15) & ~size_t(15)));
@@ -676,8 +683,10 @@ __global__ void __launch_bounds__(kF8Threads, 1)
             ok = false;
             break;
           }
-          mbar_expect_tx(&st_full[st], (uint32_t)kF8StageBytes);
+          mbar_expect_tx(&st_full[st], (uint32_t)(kF8StageBytes + kF8ScaleBytes));
           tma_load_3d(stage + (size_t)st * kF8StageBytes, &map_q, &st_full[st], c0, kc * kBoxL, (int)r);
+          tma_load_2d(ssm + (size_t)st * kF8ScaleBytes, &map_s, &st_full[st], (c0 >> 6) & ~3,
+                      (int)(r * P.L + kc * kBoxL));
         }
       }
       const uint32_t issued = it;
@@ -724,51 +733,15 @@ __global__ void __launch_bounds__(kF8Threads, 1)
   } else if (warp < 2 + kF8Warps) {
     // ------------------------------------------------------------ converter
     // Thread ct converts groups g = ct + 256 i (i < 4) of a stage: row
-    // l = 2 wq + (lane >> 4) + 16 i, columns c = 8 (lane & 15) .. + 7.  The 16
-    // (row, 64-column half) scales a warp needs per stage are loaded six
-    // stages ahead, one per lane (slot j = lane & 15: row 2 wq + ((j >> 1) & 1)
-    // + 16 (j >> 2), half j & 1), and handed to the groups by warp shuffles.
+    // l = g >> 4, columns c = 8 (g & 15) .. + 7; the scale of (l, c) is the
+    // stage's scale row l, column ((c0 / 64) & 3) + (c >> 6).
     const int ct = threadIdx.x - 64;  // 0 .. 255
-    const int wq = ct >> 5;
-    const int js = lane & 15;
-    auto scale_slot = [&](int64_t t, int kc) -> float {
-      if (t >= P.tiles) return 0.f;
-      const int64_t r = t / P.ctiles;
-      const int64_t lg = (int64_t)kc * kBoxL + 2 * wq + ((js >> 1) & 1) + 16 * (js >> 2);
-      const int64_t cg = (t - r * P.ctiles) * kTileM + 64 * (js & 1);
-      return (lg < P.L && cg < P.C) ? __ldg(scales + (((r * P.L + lg) * P.C + cg) >> 6)) : 0.f;
-    };
-    // (tile, chunk) of the stage after (t, kc)
-    auto advance = [&](int64_t& t, int& kc) {
-      if (++kc == P.nk) {
-        kc = 0;
-        t += gridDim.x;
-      }
-    };
-    // scale slots of the next kAhead stages: slot a holds stage it's scale for
-    // it % kAhead == a; the stage loop is unrolled by kAhead so that a slot is
-    // read and refilled in place (moving a register whose load is still in
-    // flight would wait for that load)
-    constexpr int kAhead = 6;
-    float ahead[kAhead];
-    int64_t tp = blockIdx.x;
-    int kcp = 0;
-#pragma unroll
-    for (int a = 0; a < kAhead; ++a) {
-      ahead[a] = scale_slot(tp, kcp);
-      advance(tp, kcp);
-    }
     uint32_t it = 0;
     bool ok = true;
-    int64_t t = blockIdx.x;
-    int kc = 0;
-    while (ok && t < P.tiles) {
-#pragma unroll
-      for (int a = 0; a < kAhead; ++a) {
-        if (!ok || t >= P.tiles) break;
-        const float cur = ahead[a];
-        ahead[a] = scale_slot(tp, kcp);
-        advance(tp, kcp);
+    for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+      const int64_t r = t / P.ctiles;
+      const int sx = (int)((((t - r * P.ctiles) * kTileM) >> 6) & 3);
+      for (int kc = 0; kc < P.nk; ++kc, ++it) {
         const uint32_t ss = it % kF8St, sph = (it / kF8St) & 1u;
         const uint32_t cs = it % kF8Cv, cph = (it / kF8Cv) & 1u;
         if (!mbar_wait(&st_full[ss], sph, abort_flag) || !mbar_wait(&cv_empty[cs], cph ^ 1u, abort_flag)) {
@@ -776,14 +749,15 @@ __global__ void __launch_bounds__(kF8Threads, 1)
           break;
         }
         const unsigned char* src = stage + (size_t)ss * kF8StageBytes;
+        const float* scl = reinterpret_cast<const float*>(ssm + (size_t)ss * kF8ScaleBytes);
         unsigned char* dst = conv + (size_t)cs * kF8CvBytes;
 #pragma unroll
         for (int i = 0; i < (kTileM * kBoxL / 8) / (kF8Warps * 32); ++i) {
           const int g = ct + kF8Warps * 32 * i;   // eight consecutive c of one l
           const int l = g >> 4, c = (g & 15) << 3;
           // with C % 64 == 0 the 64-column half of row l is one scale block;
-          // rows and columns past the tensor were zero-filled by TMA (scale 0)
-          const float sc = __shfl_sync(0xffffffffu, cur, (i << 2) | ((lane >> 4) << 1) | ((lane & 15) >> 3));
+          // codes past the tensor were zero-filled by TMA
+          const float sc = scl[l * 4 + sx + (c >> 6)];
           const uint2 w = *reinterpret_cast<const uint2*>(src + l * kTileM + c);
           const uint32_t words[2] = {w.x, w.y};
           uint32_t hw[4];
@@ -805,8 +779,6 @@ __global__ void __launch_bounds__(kF8Threads, 1)
           mbar_arrive(&cv_full[cs]);
           mbar_arrive(&st_empty[ss]);
         }
-        ++it;
-        advance(t, kc);
       }
     }
   } else {
@@ -1395,16 +1367,17 @@ int launch_ttm_tc_f32(const float* X, int64_t R, int64_t L, int64_t C, const flo
 }
 
 size_t smem_bytes_fp8(int Np, int nk) {
-  return 1024 + (size_t)kF8St * kF8StageBytes + (size_t)kF8Cv * kF8CvBytes +
+  return 1024 + (size_t)kF8St * kF8StageBytes + (size_t)kF8Cv * kF8CvBytes + (size_t)kF8St * kF8ScaleBytes +
          (((size_t)nk * 2 * Np * 128 + 15) & ~size_t(15)) + (2 * kF8St + 2 * kF8Cv + 2 * kAccBufs) * 8 + 16;
 }
 
-// FP8 column-case TTM on the tensor cores: C % 64 == 0 (each 64-column half
-// of a tile row is one scale block; 16-byte TMA strides), C >= 64, K <= 32,
-// codes 16-byte aligned, B and the rings within shared memory.
+// FP8 column-case TTM on the tensor cores: C % 256 == 0 (each 64-column half
+// of a tile row is one scale block, and a scale row of C / 64 floats has a
+// 16-byte TMA stride), K <= 32, codes 16-byte aligned, R * L within 32-bit
+// TMA coordinates, B and the rings within shared memory.
 bool ttm_tc_fp8_supported(int64_t R, int64_t L, int64_t C, int64_t K, const void* X) {
-  if (K < 1 || K > 32 || L < 1 || L > 1024 || C < 64 || C % 64 != 0) return false;
-  if ((uintptr_t)X % 16 != 0 || R > INT32_MAX || C > INT32_MAX) return false;
+  if (K < 1 || K > 32 || L < 1 || L > 1024 || C < 256 || C % 256 != 0) return false;
+  if ((uintptr_t)X % 16 != 0 || R > INT32_MAX || C > INT32_MAX || R * L + kBoxL > INT32_MAX) return false;
   const int Np = (int)((K + 15) / 16 * 16), nk = (int)((L + kBoxL - 1) / kBoxL);
   return smem_bytes_fp8(Np, nk) <= 227 * 1024;
 }
@@ -1429,16 +1402,23 @@ int launch_ttm_tc_fp8(const void* Xq, const float* scales, int64_t R, int64_t L,
   const cuuint32_t box[3] = {(cuuint32_t)kTileM, (cuuint32_t)kBoxL, 1u};
   int rc = make_map(&mq, Xq, 3, dims, str, box, CU_TENSOR_MAP_DATA_TYPE_UINT8, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (rc) return rc;
+  // the scales as [R L] rows of C / 64 floats; a box of 4 columns x 64 rows
+  CUtensorMap ms;
+  const cuuint64_t sdims[2] = {(cuuint64_t)(C / 64), (cuuint64_t)(R * L)};
+  const cuuint64_t sstr[1] = {(cuuint64_t)(C / 64) * 4};
+  const cuuint32_t sbox[2] = {4u, (cuuint32_t)kBoxL};
+  rc = make_map(&ms, scales, 2, sdims, sstr, sbox, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (rc) return rc;
   const size_t smem = smem_bytes_fp8(P.Np, P.nk);
   const int64_t grid = std::min<int64_t>(P.tiles, sm_count());
   if (y_bf16) {
     auto kern = ttm_tc_fp8_kernel<bf16_t>;
     TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)grid, kF8Threads, smem, s>>>(mq, scales, static_cast<bf16_t*>(Y), P);
+    kern<<<(unsigned)grid, kF8Threads, smem, s>>>(mq, ms, static_cast<bf16_t*>(Y), P);
   } else {
     auto kern = ttm_tc_fp8_kernel<float>;
     TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)grid, kF8Threads, smem, s>>>(mq, scales, static_cast<float*>(Y), P);
+    kern<<<(unsigned)grid, kF8Threads, smem, s>>>(mq, ms, static_cast<float*>(Y), P);
   }
   TK_LAUNCH_CHECK("ttm_tc_fp8");
   return TUCKER_OK;

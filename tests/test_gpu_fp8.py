@@ -58,14 +58,17 @@ def test_convert_fp8_matches_oracle_bit_for_bit(tk, orc, n):
 
 
 TTM_CASES = [
-    ((64, 48, 40), 0, 16),      # column case, C % 16 == 0 and C >= 64: tensor cores
+    ((64, 48, 40), 0, 16),      # column case, C % 256 != 0: CUDA-core columns kernel
     ((64, 48, 40), 1, 9),       # C = 40 < 64: CUDA-core columns kernel (C % 4 == 0)
     ((30, 20, 64), 2, 16),      # last mode, L % 4 == 0: rows kernel
     ((30, 20, 63), 2, 7),       # last mode, L odd: any-shape kernel
     ((13, 7, 9), 1, 5),         # C odd: any-shape kernel
     ((40, 36, 32, 30), 2, 20),  # C = 30: two K blocks on the CUDA cores
-    ((30, 70, 192), 1, 16),     # tensor cores: C = 192 leaves half a 128-position tile
-    ((5, 130, 320), 1, 32),     # tensor cores: three l chunks (last ragged), K = 32
+    ((30, 70, 192), 1, 16),     # C % 256 != 0: CUDA cores
+    ((30, 70, 256), 1, 16),     # tensor cores: C = 256, two tiles per row, L ragged past 64
+    ((5, 130, 768), 1, 32),     # tensor cores: three l chunks (last ragged, its scale rows
+                                # run into the next row's), tiles at scale columns 0 and 2 of a box
+    ((2, 100, 512), 1, 20),     # tensor cores: two l chunks, K = 20 (two 16-column groups)
     ((30, 70, 80), 1, 16),      # C % 64 != 0 (scale blocks straddle tile halves): CUDA cores
     ((3, 40, 2048), 1, 1),      # tensor cores: K = 1
     ((2, 64, 64, 16), 1, 20),   # tensor cores: C = 1024, K = 20 (two 16-column groups)
