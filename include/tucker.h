@@ -77,7 +77,17 @@ typedef struct {
   int32_t tree;       /* tucker_tree_t                                   */
   int32_t cost_model; /* tucker_cost_t (only for TUCKER_TREE_OPTIMAL)    */
   int32_t flags;      /* TUCKER_PLAN_* bits, 0 by default                */
+  uint64_t ws_cap;    /* workspace cap in bytes, 0 for none (see below)  */
 } tucker_plan_opts_t;
+/* Workspace cap: when ws_cap > 0 and the plan's workspace would exceed it,
+ * tucker_plan gives up, in this order, the fused root (the second root
+ * child's buffer, live through the first child's subtree) and then the
+ * least-cost STHOSVD order (TUCKER_PLAN_STHOSVD_ORDER; its ping-pong buffers
+ * can be larger than the natural order's) -- tucker_plan_fused_root and
+ * tucker_plan_sthosvd report what the plan kept -- and returns
+ * TUCKER_ERR_WORKSPACE, with the smallest size it reached in the error text,
+ * when the cap still cannot be met.  The tree itself (and so every sweep's
+ * result) never changes with the cap.  Zero-initialise the whole struct. */
 
 /* Plan flag: never fuse the root.  By default, when the first two root
  * children of the tree (modes a < b) are both TTM nodes, T is FP32 or BF16,
@@ -125,7 +135,7 @@ typedef struct {
  * (Sec. 5: the planner needs only this metadata; the plan is reused by every
  * sweep).  Host only, no device work.  Validation: 2 <= N <= 8,
  * 1 <= K_n <= L_n, K_n <= prod_{j != n} K_j (else Z_(n) has rank < K_n),
- * prod L_n < 2^40.  opts may be NULL (F32, optimal tree, MAC cost). */
+ * prod L_n < 2^40.  opts may be NULL (F32, optimal tree, MAC cost, no cap). */
 int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opts_t* opts,
                 tucker_plan_t* out);
 

@@ -41,7 +41,8 @@ class TuckerError(RuntimeError):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("tree", ctypes.c_int32),
-                ("cost_model", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("cost_model", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("ws_cap", ctypes.c_uint64)]
 
 
 class Node(ctypes.Structure):
@@ -224,10 +225,12 @@ class Plan:
 
 def tucker_plan(L: Sequence[int], K: Sequence[int], dtype: int = TUCKER_F32,
                 tree: int = TREE_OPTIMAL, cost_model: int = COST_MACS,
-                fuse_root: bool = True, sthosvd_order: bool = False) -> Plan:
+                fuse_root: bool = True, sthosvd_order: bool = False, ws_cap: int = 0) -> Plan:
+    """ws_cap: workspace cap in bytes (0: none); the plan gives up the fused
+    root, then the STHOSVD order, to meet it (see include/tucker.h)."""
     h = ctypes.c_void_p()
     flags = (0 if fuse_root else PLAN_NO_FUSED_ROOT) | (PLAN_STHOSVD_ORDER if sthosvd_order else 0)
-    opts = PlanOpts(dtype, tree, cost_model, flags)
+    opts = PlanOpts(dtype, tree, cost_model, flags, int(ws_cap))
     _check(lib().tucker_plan(len(L), _i64(L), _i64(K), ctypes.byref(opts), ctypes.byref(h)),
            "tucker_plan")
     return Plan(h, tuple(int(x) for x in L), tuple(int(x) for x in K), dtype, tree)

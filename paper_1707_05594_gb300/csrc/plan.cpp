@@ -339,6 +339,32 @@ size_t eig_ws_bytes(int batch, const int64_t* L, const int64_t* K) {
   return total;
 }
 
+// Buffer placement of a built tree: the fused root (when asked for and the
+// kernel takes it), the stack memory plan, the core chain, the Gauss-Seidel
+// chains and STHOSVD buffers, then the workspace layout.
+void layout(Plan& p, bool fuse, bool sth_opt) {
+  p.fused_u1 = p.fused_u2 = -1;
+  p.bytes_scratch = 0;
+  if (fuse) choose_fused_root(p);
+  memory_plan(p);
+  core_chain(p);
+  gs_buffers(p);
+  sthosvd_order(p, sth_opt);
+  size_t off = 0;
+  p.off_scratch = off;
+  off += align_up(p.bytes_scratch);
+  for (int n = 0; n < p.N; ++n) {
+    p.off_gram[n] = off;
+    off += align_up((size_t)p.L[n] * (size_t)p.L[n] * 8);
+  }
+  p.off_eig = off;
+  p.bytes_eig = eig_ws_bytes(p.N, p.L, p.K);
+  off += align_up(p.bytes_eig);
+  p.off_misc = off;
+  off += align_up(64 * 8);
+  p.ws_total = off;
+}
+
 }  // namespace tk
 
 using namespace tk;
@@ -356,7 +382,7 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
   if (N < 2 || N > kMaxModes)
     return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: N must be in [2, 8]");
   if (!L || !K) return fail(TUCKER_ERR_INVALID_ARG, "tucker_plan: L or K is NULL");
-  tucker_plan_opts_t o{TUCKER_F32, TUCKER_TREE_OPTIMAL, TUCKER_COST_MACS, 0};
+  tucker_plan_opts_t o{TUCKER_F32, TUCKER_TREE_OPTIMAL, TUCKER_COST_MACS, 0, 0};
   if (opts) o = *opts;
   if (o.dtype != TUCKER_F32 && o.dtype != TUCKER_F64 && o.dtype != TUCKER_BF16 &&
       o.dtype != TUCKER_FP8_E4M3 && o.dtype != TUCKER_BF16_SPLIT)
@@ -438,26 +464,18 @@ int tucker_plan(int N, const int64_t* L, const int64_t* K, const tucker_plan_opt
       p.tree_elems += nd.in_elems + nd.out_elems;
     }
   }
-  if (!(o.flags & TUCKER_PLAN_NO_FUSED_ROOT)) choose_fused_root(p);
-  memory_plan(p);
-  core_chain(p);
-  gs_buffers(p);
-  sthosvd_order(p, (o.flags & TUCKER_PLAN_STHOSVD_ORDER) != 0);
-
-  // workspace layout
-  size_t off = 0;
-  p.off_scratch = off;
-  off += align_up(p.bytes_scratch);
-  for (int n = 0; n < N; ++n) {
-    p.off_gram[n] = off;
-    off += align_up((size_t)L[n] * (size_t)L[n] * 8);
+  bool fuse = !(o.flags & TUCKER_PLAN_NO_FUSED_ROOT);
+  bool sth_opt = (o.flags & TUCKER_PLAN_STHOSVD_ORDER) != 0;
+  layout(p, fuse, sth_opt);
+  // a workspace cap trades the fused root first, then the STHOSVD order
+  if (o.ws_cap > 0 && p.ws_total > o.ws_cap && p.fused_u1 >= 0) layout(p, fuse = false, sth_opt);
+  if (o.ws_cap > 0 && p.ws_total > o.ws_cap && sth_opt) layout(p, fuse, sth_opt = false);
+  if (o.ws_cap > 0 && p.ws_total > o.ws_cap) {
+    const std::string msg = "tucker_plan: the workspace needs " + std::to_string(p.ws_total) +
+                            " bytes at least, above the cap of " + std::to_string(o.ws_cap);
+    delete h;
+    return fail(TUCKER_ERR_WORKSPACE, msg);
   }
-  p.off_eig = off;
-  p.bytes_eig = eig_ws_bytes(N, p.L, p.K);
-  off += align_up(p.bytes_eig);
-  p.off_misc = off;
-  off += align_up(64 * 8);
-  p.ws_total = off;
   *out = h;
   return TUCKER_OK;
 }

@@ -540,3 +540,50 @@ def test_eig_entry_points_reject_unknown_factor_dtype(tk):
         assert b"f_dtype" in L.tucker_last_error()
         rc = L.tucker_eig_topk_noalloc(1, Ls, Ks, ptrs, ptrs, code, None)
         assert rc == -1
+
+
+def test_workspace_cap_trades_fused_root_then_sthosvd_order(tk):
+    """A workspace cap gives up the fused root first (the 6-way workload's
+    plan fuses its root and needs more workspace for it), then the least-cost
+    STHOSVD order, and otherwise fails with TUCKER_ERR_WORKSPACE; the tree
+    and its cost never change."""
+    L, K = (64, 56, 48, 40, 32, 24), (16, 14, 12, 10, 8, 6)
+    full = tk.tucker_plan(L, K, sthosvd_order=True)
+    nofuse = tk.tucker_plan(L, K, fuse_root=False, sthosvd_order=True)
+    natural = tk.tucker_plan(L, K, fuse_root=False)
+    w_full, w_nf, w_nat = (tk.tucker_plan_cost(p)["ws_bytes"] for p in (full, nofuse, natural))
+    assert tk.tucker_plan_fused_root(full) is not None and w_full > w_nf
+    # a cap at or above the full plan's need changes nothing
+    p = tk.tucker_plan(L, K, sthosvd_order=True, ws_cap=w_full)
+    assert tk.tucker_plan_fused_root(p) is not None
+    assert tk.tucker_plan_cost(p)["ws_bytes"] == w_full
+    # just below: the fused root goes, the STHOSVD order stays
+    p = tk.tucker_plan(L, K, sthosvd_order=True, ws_cap=w_full - 1)
+    assert tk.tucker_plan_fused_root(p) is None
+    assert tk.tucker_plan_cost(p)["ws_bytes"] == w_nf
+    assert tk.tucker_plan_sthosvd(p)[0] == tk.tucker_plan_sthosvd(nofuse)[0]
+    assert tk.tucker_plan_cost(p)["tree_macs"] == tk.tucker_plan_cost(full)["tree_macs"]
+    # the STHOSVD order is given up when only that meets the cap
+    if w_nat < w_nf:
+        p = tk.tucker_plan(L, K, sthosvd_order=True, ws_cap=w_nf - 1)
+        assert tk.tucker_plan_sthosvd(p)[0] == list(range(len(L)))
+        assert tk.tucker_plan_cost(p)["ws_bytes"] == w_nat
+    # below every layout: TUCKER_ERR_WORKSPACE naming the smallest size
+    with pytest.raises(tk.TuckerError) as e:
+        tk.tucker_plan(L, K, sthosvd_order=True, ws_cap=min(w_nf, w_nat) - 1)
+    assert e.value.code == -3
+    assert str(min(w_nf, w_nat)) in str(e.value)
+
+
+def test_workspace_cap_gives_up_the_sthosvd_order(tk):
+    """On 64 x 64 x 32 with ranks 16 the least-cost STHOSVD order takes mode 2
+    first, whose ping-pong buffers are larger than the natural order's: a cap
+    between the two sizes keeps the plan with the natural order."""
+    L, K = (64, 64, 32), (16, 16, 16)
+    opt = tk.tucker_plan(L, K, sthosvd_order=True)
+    nat = tk.tucker_plan(L, K)
+    w_opt, w_nat = tk.tucker_plan_cost(opt)["ws_bytes"], tk.tucker_plan_cost(nat)["ws_bytes"]
+    assert w_nat < w_opt and tk.tucker_plan_sthosvd(opt)[0] != [0, 1, 2]
+    p = tk.tucker_plan(L, K, sthosvd_order=True, ws_cap=w_opt - 1)
+    assert tk.tucker_plan_sthosvd(p)[0] == [0, 1, 2]
+    assert tk.tucker_plan_cost(p)["ws_bytes"] == w_nat <= w_opt - 1
