@@ -386,8 +386,14 @@ size_t tucker_bf16_split_lo_offset(int64_t n);
  *              (see TUCKER_PLAN_NO_FUSED_ROOT; FP32 plans do so under bits 5
  *              or 6).  Off by default: measured slower than two separate
  *              tensor-core TTMs on the 64^5 workload.
+ *   bit 9 (512): FP32 Grams on the CUDA cores (otherwise Grams of FP32
+ *              unfoldings with C % 4 == 0, C >= 16 and L <= 512 run on the
+ *              tensor cores: TF32 with split operands, x_hi y_hi + x_hi y_lo +
+ *              x_lo y_hi, one 32-column stage per accumulator, the stage sums
+ *              added in FP32 registers and the block sums in FP64 -- as
+ *              accurate as FP32 arithmetic; bit 0 also selects the CUDA cores).
  * Bits 5, 6 and 8 are read by tucker_plan (the pair changes the plan's
- * buffer layout) and by the calls.  TUCKER_ERR_INVALID_ARG outside 0..511. */
+ * buffer layout) and by the calls.  TUCKER_ERR_INVALID_ARG outside 0..1023. */
 int tucker_set_kernel_policy(int policy);
 
 /* Device error word of the tensor-core kernels: 0, or TUCKER_ERR_TIMEOUT if a

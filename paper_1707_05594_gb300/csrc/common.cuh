@@ -349,6 +349,9 @@ int kernel_policy();
 // W += Z_(n) Z_(n)^T for Z viewed as [R][L][C] (W must be zeroed first).
 int launch_gram(int z_dtype, const void* Z, int64_t R, int64_t L, int64_t C, double* W,
                 cudaStream_t s);
+// the same for FP32 Z on the tensor cores (gram_tc.cu)
+bool gram_tc_supported(int64_t R, int64_t L, int64_t C, const void* Z);
+int launch_gram_tc(const float* Z, int64_t R, int64_t L, int64_t C, double* W, cudaStream_t s);
 // out[0] += sum x^2 (out must be zeroed first)
 int launch_norm2(int dtype, const void* X, int64_t n, double* out, cudaStream_t s);
 // fit from G (factor type) and normT2

@@ -152,6 +152,8 @@ int launch_gram(int z_dtype, const void* Z, int64_t R, int64_t L, int64_t C, dou
   dim3 grid((unsigned)tiles, (unsigned)splits);
   switch (z_dtype) {
     case TUCKER_F32:
+      if (!(kernel_policy() & (1 | 512)) && gram_tc_supported(R, L, C, Z))
+        return launch_gram_tc(static_cast<const float*>(Z), R, L, C, W, s);
       gram_kernel<float><<<grid, kGramThreads, 0, s>>>(static_cast<const float*>(Z), R, L, C, W,
                                                        tiles, mpb);
       break;

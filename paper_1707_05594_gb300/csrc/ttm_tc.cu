@@ -1435,8 +1435,8 @@ int kernel_policy() { return g_policy.load(std::memory_order_relaxed); }
 }  // namespace tk
 
 extern "C" int tucker_set_kernel_policy(int policy) {
-  if (policy < 0 || policy > 511)
-    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 511]");
+  if (policy < 0 || policy > 1023)
+    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 1023]");
   tk::g_policy.store(policy, std::memory_order_relaxed);
   return TUCKER_OK;
 }
