@@ -396,6 +396,28 @@ size_t tucker_bf16_split_lo_offset(int64_t n);
  * buffer layout) and by the calls.  TUCKER_ERR_INVALID_ARG outside 0..1023. */
 int tucker_set_kernel_policy(int policy);
 
+/* Debug build: the library compiled with -DTUCKER_DEBUG
+ * (paper_1707_05594_gb300/build.py, build(debug=True), which writes
+ * libtucker_gb300_debug.so).  There every kernel that forms global indices
+ * from tensor shapes -- the TTMs on CUDA and tensor cores (their epilogue
+ * stores), the CUDA-core Gram, the FP8 TTMs, the fused root, the short-row
+ * kernels and the batched form's tree, Gram and expansion kernels -- checks,
+ * per thread and per array, the first and last element it will touch (the
+ * accesses are affine in the loop indices, so the two ends bound all of
+ * them) against the array's length; a range outside it is recorded (the
+ * first: offending index, length, source file and line) and its accesses are
+ * skipped.  Kernels whose every access is guarded by `i < n` in its own loop
+ * (norms, conversions, the eigensolver's L x L work) carry no check.
+ * tucker_debug_build returns 1 in the debug build and 0 otherwise. */
+int tucker_debug_build(void);
+
+/* Synchronous (waits for the device): the number of out-of-range ranges
+ * recorded since the last reset -- always 0 in the normal build -- and the
+ * first one's index, length, source line and file (file: file_len bytes,
+ * NUL-terminated).  Any pointer may be NULL; reset != 0 clears the records.
+ * TUCKER_ERR_CUDA when a record cannot be read. */
+int tucker_debug_check(int64_t* index, int64_t* bound, int* line, char* file, int file_len, int reset);
+
 /* Device error word of the tensor-core kernels: 0, or TUCKER_ERR_TIMEOUT if a
  * pipeline wait gave up (the kernel then returned early and its output is not
  * valid).  Synchronous; reset != 0 clears the word. */

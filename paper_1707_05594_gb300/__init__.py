@@ -17,7 +17,10 @@ from dataclasses import dataclass
 from typing import List, Sequence
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtucker_gb300.so")
+# TUCKER_LIB_VARIANT=debug loads the debug build (index-checked kernels, see
+# build.build(debug=True) and tucker_debug_check)
+DEBUG_VARIANT = os.environ.get("TUCKER_LIB_VARIANT", "") == "debug"
+LIB_PATH = os.path.join(_HERE, "libtucker_gb300_debug.so" if DEBUG_VARIANT else "libtucker_gb300.so")
 
 TUCKER_F32, TUCKER_F64, TUCKER_BF16, TUCKER_FP8_E4M3, TUCKER_BF16_SPLIT = 0, 1, 2, 3, 4
 TREE_OPTIMAL, TREE_CHAIN, TREE_CHAIN_K, TREE_CHAIN_H, TREE_BALANCED = 0, 1, 2, 3, 4
@@ -61,7 +64,8 @@ def lib():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1707_05594_gb300.build.build()")
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1707_05594_gb300.build.build("
+                          f"{'debug=True' if DEBUG_VARIANT else ''})")
     L = ctypes.CDLL(LIB_PATH)
     L.tucker_plan.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.POINTER(PlanOpts),
                               ctypes.POINTER(ctypes.c_void_p)]
@@ -110,6 +114,9 @@ def lib():
     L.tucker_bf16_split_lo_offset.argtypes = [ctypes.c_int64]
     L.tucker_bf16_split_lo_offset.restype = ctypes.c_size_t
     L.tucker_device_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.tucker_debug_build.argtypes = []
+    L.tucker_debug_check.argtypes = [_i64p, _i64p, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p,
+                                     ctypes.c_int, ctypes.c_int]
     L.tucker_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
     L.tucker_check_finite.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
     L.tucker_eig_topk_noalloc.argtypes = [ctypes.c_int, _i64p, _i64p, _vpp, _vpp, ctypes.c_int,
@@ -518,6 +525,26 @@ def tucker_device_status(reset: bool = True) -> int:
     st = ctypes.c_int(0)
     _check(lib().tucker_device_status(ctypes.byref(st), 1 if reset else 0), "tucker_device_status")
     return st.value
+
+
+def tucker_debug_build() -> bool:
+    """True when the loaded library is the index-checked debug build."""
+    return bool(lib().tucker_debug_build())
+
+
+def tucker_debug_check(reset: bool = True) -> dict:
+    """Out-of-range index ranges recorded by the debug build's kernels since
+    the last reset: {"count", "index", "bound", "line", "file"} (count 0 in
+    the normal build).  Synchronous."""
+    idx, bnd = ctypes.c_int64(0), ctypes.c_int64(0)
+    line = ctypes.c_int(0)
+    buf = ctypes.create_string_buffer(256)
+    n = lib().tucker_debug_check(ctypes.byref(idx), ctypes.byref(bnd), ctypes.byref(line), buf, 256,
+                                 1 if reset else 0)
+    if n < 0:
+        _check(n, "tucker_debug_check")
+    return {"count": n, "index": idx.value, "bound": bnd.value, "line": line.value,
+            "file": os.path.basename(buf.value.decode())}
 
 
 def tucker_check_finite(X, stream=None) -> None:

@@ -94,7 +94,13 @@ __device__ __forceinline__ void bttm_staged(const BNode& nd, int64_t t, const fl
   const int C = (int)nd.C;
   const int rt = kBThreads / C;
   const int64_t r0 = t * rt;
-  const int nrows = (int)min((int64_t)rt, nd.R - r0);
+  // the tile's rows of the node's input and output views (block-uniform
+  // check: a failed one skips the tile's accesses and keeps its barriers)
+  const int64_t r1 = r0 + min((int64_t)rt, nd.R - r0);
+  const int nrows = TK_DBG_IN(r0 * nd.L * C, r1 * nd.L * C - 1, nd.R * nd.L * C) &&
+                            TK_DBG_IN(r0 * nd.K * C, r1 * nd.K * C - 1, nd.R * nd.K * C)
+                        ? (int)(r1 - r0)
+                        : 0;
   const bool active = tid < nrows * C;
   float acc[KB];
 #pragma unroll
@@ -159,8 +165,11 @@ __device__ __forceinline__ void bttm_async(const BNode& nd, int64_t t, const flo
                                            float* Fs /* [32][KB] */, float (*Ts)[kBThreads + 1]) {
   const int tid = threadIdx.x;
   const int64_t p = t * kBThreads + tid;
-  const bool act = p < nd.R * nd.C;
+  bool act = p < nd.R * nd.C;
   const int64_t r = act ? p / nd.C : 0, c = act ? p - r * nd.C : 0;
+  // input fibre In[r, :, c] and outputs Out[r, :, c] of the node's views
+  act = act && TK_DBG_IN((r * nd.L) * nd.C + c, (r * nd.L + nd.L - 1) * nd.C + c, nd.R * nd.L * nd.C) &&
+        TK_DBG_IN((r * nd.K) * nd.C + c, (r * nd.K + nd.K - 1) * nd.C + c, nd.R * nd.K * nd.C);
   const float* in = src + (r * nd.L) * nd.C + c;
   float acc[KB];
 #pragma unroll
@@ -205,6 +214,9 @@ __device__ __forceinline__ void bttm_direct(const BNode& nd, int64_t t, const fl
     const int64_t p = (t * PPT + j) * kBThreads + tid;
     act[j] = p < M;
     const int64_t r = act[j] ? p / nd.C : 0, c = act[j] ? p - r * nd.C : 0;
+    // input fibre In[r, :, c] and outputs Out[r, :, c] of the node's views
+    act[j] = act[j] && TK_DBG_IN((r * nd.L) * nd.C + c, (r * nd.L + nd.L - 1) * nd.C + c, nd.R * nd.L * nd.C) &&
+             TK_DBG_IN((r * nd.K) * nd.C + c, (r * nd.K + nd.K - 1) * nd.C + c, nd.R * nd.K * nd.C);
     in[j] = src + (r * nd.L) * nd.C + c;
     ob[j] = (r * nd.K) * nd.C + c;
   }
@@ -310,8 +322,9 @@ __global__ void __launch_bounds__(kBThreads)
       if (m < M) {
         const int64_t r = m / g.C, c = m - (m / g.C) * g.C;
         const int la = g.ti * 32 + a, lb = g.tj * 32 + a;
-        if (la < g.L) va = Z[(r * g.L + la) * g.C + c];
-        if (lb < g.L) vb = Z[(r * g.L + lb) * g.C + c];
+        const int64_t ea = (r * g.L + la) * g.C + c, eb = (r * g.L + lb) * g.C + c;
+        if (la < g.L && TK_DBG_IN(ea, ea, M * g.L)) va = Z[ea];
+        if (lb < g.L && TK_DBG_IN(eb, eb, M * g.L)) vb = Z[eb];
       }
       As[a][mm] = va;
       Bs[a][mm] = vb;
@@ -414,6 +427,9 @@ __global__ void __launch_bounds__(kBThreads)
     const int64_t p = ((tile - st.tile0) * PPT + j) * kBThreads + threadIdx.x;
     act[j] = p < M;
     const int64_t r = act[j] ? p / st.C : 0, c = act[j] ? p - r * st.C : 0;
+    // inputs In[r, :, c] ([R][K][C]) and outputs Out[r, :, c] ([R][L][C])
+    act[j] = act[j] && TK_DBG_IN((r * st.K) * st.C + c, (r * st.K + st.K - 1) * st.C + c, M * st.K) &&
+             TK_DBG_IN((r * st.L) * st.C + c, (r * st.L + st.L - 1) * st.C + c, M * st.L);
     const float* in = (st.in_src ? inter : G) + st.in_off + (r * st.K) * st.C + c;
 #pragma unroll
     for (int k = 0; k < KB; ++k) y[j][k] = (act[j] && k < st.K) ? in[(int64_t)k * st.C] : 0.f;

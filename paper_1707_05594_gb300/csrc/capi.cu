@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "nvtx3/nvToolsExt.h"
 
@@ -110,6 +111,25 @@ int launch_root_pair(int dtype, const void* X, const int64_t* L, int N, int a, i
 
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+#ifdef TUCKER_DEBUG
+namespace dbg {
+namespace {
+struct Entry {
+  Reader read;
+  const char* file;
+};
+std::vector<Entry>& readers() {
+  static std::vector<Entry> v;  // filled while the library loads
+  return v;
+}
+}  // namespace
+int add_reader(Reader r, const char* file) {
+  readers().push_back({r, file});
+  return (int)readers().size();
+}
+}  // namespace dbg
+#endif
+
 void destroy_profile(Plan& p) {
   for (void* e : p.prof_events)
     if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
@@ -124,6 +144,43 @@ void destroy_profile(Plan& p) {
 using namespace tk;
 
 extern "C" {
+
+int tucker_debug_build(void) {
+#ifdef TUCKER_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int tucker_debug_check(int64_t* index, int64_t* bound, int* line, char* file, int file_len, int reset) {
+  if (index) *index = 0;
+  if (bound) *bound = 0;
+  if (line) *line = 0;
+  if (file && file_len > 0) file[0] = 0;
+#ifdef TUCKER_DEBUG
+  TK_CUDA_TRY(cudaDeviceSynchronize());
+  unsigned long long total = 0;
+  for (const auto& e : dbg::readers()) {
+    dbg::Record r{};
+    if (e.read(&r, reset) != 0) return fail(TUCKER_ERR_CUDA, "tucker_debug_check: record not readable");
+    if (r.count && !total) {
+      if (index) *index = r.index;
+      if (bound) *bound = r.bound;
+      if (line) *line = r.line;
+      if (file && file_len > 0) {
+        std::strncpy(file, e.file, (size_t)file_len - 1);
+        file[file_len - 1] = 0;
+      }
+    }
+    total += r.count;
+  }
+  return total > (unsigned long long)INT32_MAX ? INT32_MAX : (int)total;
+#else
+  (void)reset;
+  return 0;
+#endif
+}
 
 int tucker_ttm(int N, const int64_t* dims, const void* X, int x_dtype, int n, const void* F,
                int64_t K, void* Y, void* stream) {

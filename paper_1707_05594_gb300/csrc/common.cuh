@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 
+#include "debug_check.cuh"
 #include "internal.h"
 
 #define TK_CUDA_TRY(expr)                                                                \

@@ -66,11 +66,14 @@ __global__ void __launch_bounds__(kF8Threads)
   const int kb0 = blockIdx.y * KB;
   const int64_t C4 = C / 4;
   const int64_t g = (int64_t)blockIdx.x * kF8Threads + threadIdx.x;
-  const bool active = g < R * C4;
+  bool active = g < R * C4;
   int64_t r = 0, c = 0;
   if (active) {
     r = g / C4;
     c = (g - r * C4) * 4;
+    // codes X[r, 0 .. L-1, c .. c+3] (their scales follow), outputs Y[r, kb0 .., c .. c+3]
+    active = TK_DBG_IN(r * L * C + c, (r * L + L - 1) * C + c + 3, R * L * C) &&
+             TK_DBG_IN((r * K + kb0) * C + c, (r * K + min(K, kb0 + KB) - 1) * C + c + 3, R * K * C);
   }
   const int64_t e0 = r * L * C + c;
   float acc[4][KB];
@@ -123,7 +126,9 @@ __global__ void __launch_bounds__(kF8Threads)
   __shared__ __align__(16) float Fs[64][KB];
   const int kb0 = blockIdx.y * KB;
   const int64_t r = (int64_t)blockIdx.x * kF8Threads + threadIdx.x;
-  const bool active = r < R;
+  // codes of row r, outputs Y[r, kb0 ..]
+  const bool active = r < R && TK_DBG_IN(r * L, r * L + L - 1, R * L) &&
+                      TK_DBG_IN(r * K + kb0, r * K + min(K, kb0 + KB) - 1, R * K);
   float acc[KB];
 #pragma unroll
   for (int k = 0; k < KB; ++k) acc[k] = 0.f;
@@ -165,11 +170,14 @@ __global__ void __launch_bounds__(kF8Threads)
   __shared__ __align__(16) float Fs[64][KB];
   const int kb0 = blockIdx.y * KB;
   const int64_t p = (int64_t)blockIdx.x * kF8Threads + threadIdx.x;
-  const bool active = p < R * C;
+  bool active = p < R * C;
   int64_t r = 0, c = 0;
   if (active) {
     r = p / C;
     c = p - r * C;
+    // codes X[r, 0 .. L-1, c], outputs Y[r, kb0 .., c]
+    active = TK_DBG_IN(r * L * C + c, (r * L + L - 1) * C + c, R * L * C) &&
+             TK_DBG_IN((r * K + kb0) * C + c, (r * K + min(K, kb0 + KB) - 1) * C + c, R * K * C);
   }
   float acc[KB];
 #pragma unroll

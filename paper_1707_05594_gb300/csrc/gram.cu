@@ -34,7 +34,8 @@ __device__ __forceinline__ void load_panel(const TIn* __restrict__ Z, int64_t L,
     for (int i = threadIdx.x; i < kTile * kMStep; i += kGramThreads) {
       const int a = i % kTile, mm = i / kTile;
       const int64_t l = row0 + a, m = m0 + mm;
-      S[mm][a] = (l < L && m < M) ? load_one<TIn>(Z + m * L + l) : A(0);
+      S[mm][a] = (l < L && m < M && TK_DBG_IN(m * L + l, m * L + l, M * L)) ? load_one<TIn>(Z + m * L + l)
+                                                                          : A(0);
     }
   } else {
     // element (l, m) at r*L*C + l*C + c: consecutive threads take consecutive m
@@ -81,7 +82,9 @@ __global__ void __launch_bounds__(kGramThreads)
       const int64_t m = m0 + threadIdx.x % kMStep;
       if (m < mend) {
         const int64_t r = m / C;
-        base = Z + r * L * C + (m - r * C);
+        // this column's fibre Z[r, 0 .. L-1, c]
+        if (TK_DBG_IN(r * L * C + (m - r * C), r * L * C + (L - 1) * C + (m - r * C), R * L * C))
+          base = Z + r * L * C + (m - r * C);
       }
     }
     __syncthreads();

@@ -96,6 +96,14 @@ struct Tf32Params {
   int* status;         // the library's device error word
 };
 
+// Values of a job's Y: R * K * S (plain), R * K * G * S (block-C: rows of
+// G * S positions) or R * G * Rl * K * S (block-R: the block mode between
+// the row indices).
+__device__ __forceinline__ int64_t y_total(const Tf32Job& J, int64_t G) {
+  const int64_t base = J.R * (int64_t)J.K * J.S;
+  return J.type == kJobPlain ? base : J.type == kJobBlockC ? base * G : base * G * J.Rl;
+}
+
 // idesc for kind::tf32: D FP32, A and B TF32, both K-major, M = 128.
 __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
@@ -423,6 +431,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
           ystride = J.S;
           yp = J.Y + (t.r * J.K) * ystride + c;
         }
+        if (!TK_DBG_IN(yp - J.Y, (yp - J.Y) + (int64_t)(J.K - 1) * ystride, y_total(J, P.G))) continue;
         // columns [0, Kp): x_hi f_hi + x_lo f_hi; [Kp, 2 Kp): x_hi f_lo
         if (J.Kp == 16) {
 #pragma unroll
@@ -876,9 +885,10 @@ __global__ void __launch_bounds__(kT32Threads, 1)
           ystride = J.S;
           yp = J.Y + (t.r * J.K) * ystride + c;
         }
+        if (TK_DBG_IN(yp - J.Y, (yp - J.Y) + (int64_t)(J.K - 1) * ystride, y_total(J, P.G)))
 #pragma unroll
-        for (int k = 0; k < 32; ++k)
-          if (k < J.K) yp[(int64_t)k * ystride] = y[k];
+          for (int k = 0; k < 32; ++k)
+            if (k < J.K) yp[(int64_t)k * ystride] = y[k];
       }
     }
   }

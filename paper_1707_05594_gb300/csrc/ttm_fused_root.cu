@@ -38,7 +38,17 @@ __global__ void __launch_bounds__(kSlabThreads)
   const int QA = M * Lb * B;           // positions of the first child per block
   const int SAB = La * QA;             // elements per block X[alpha]
   const int64_t a0 = (int64_t)blockIdx.x * S;
-  const int ns = (int)min((int64_t)S, A - a0);
+  // the tile's blocks of X, Ya and Yb (block-uniform check: a failed one
+  // skips the block's accesses and keeps its barrier)
+  const int64_t a1 = a0 + min((int64_t)S, A - a0);
+  const int64_t ya_per = (int64_t)Ka * M * Lb * B, yb_per = (int64_t)La * M * Kb * B;
+  const int ns = TK_DBG_IN(a0 * La * M * Lb * B, a1 * La * M * Lb * B - 1, A * La * M * Lb * B) &&
+                         TK_DBG_IN(a0 * ya_per, a1 * ya_per - 1, A * ya_per) &&
+                         TK_DBG_IN(a0 * yb_per, a1 * yb_per - 1, A * yb_per)
+                     ? (int)(a1 - a0)
+                     : 0;
+  (void)ya_per;
+  (void)yb_per;
   constexpr int per = 16 / (int)sizeof(TIn);
   const bool vecB = B == 1 && (Lb * (int)sizeof(TIn)) % 16 == 0;
   for (int i = tid; i < La * KBA; i += kSlabThreads) {

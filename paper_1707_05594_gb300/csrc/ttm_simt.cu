@@ -30,11 +30,14 @@ __global__ void __launch_bounds__(kColsThreads)
   const int kb0 = blockIdx.y * KB;
   const int64_t total = R * C;
   const int64_t m0 = ((int64_t)blockIdx.x * kColsThreads + threadIdx.x) * VEC;
-  const bool active = m0 < total;
+  bool active = m0 < total;
   int64_t r = 0, c = 0;
   if (active) {
     r = m0 / C;
     c = m0 - r * C;
+    // this thread reads X[r, 0 .. L-1, c .. c+VEC-1], writes Y[r, kb0 .., c ..]
+    active = TK_DBG_IN(r * L * C + c, (r * L + L - 1) * C + c + VEC - 1, R * L * C) &&
+             TK_DBG_IN((r * K + kb0) * C + c, (r * K + min(K, kb0 + KB) - 1) * C + c + VEC - 1, R * K * C);
   }
   const TIn* xp = X + (r * L) * C + c;
   A acc[KB][VEC];
@@ -48,7 +51,8 @@ __global__ void __launch_bounds__(kColsThreads)
     __syncthreads();
     for (int i = threadIdx.x; i < kColsLChunk * KB; i += kColsThreads) {
       const int l = i / KB, k = i - (i / KB) * KB;
-      Fs[l][k] = (l < lc && kb0 + k < K) ? F[(int64_t)(l0 + l) * K + kb0 + k] : A(0);
+      const int64_t e = (int64_t)(l0 + l) * K + kb0 + k;
+      Fs[l][k] = (l < lc && kb0 + k < K && TK_DBG_IN(e, e, (int64_t)L * K)) ? F[e] : A(0);
     }
     __syncthreads();
     if (active) {
@@ -145,11 +149,14 @@ __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccO
   const int kb0 = blockIdx.y * KB;
   const int64_t total = R * C;
   const int64_t m0 = ((int64_t)blockIdx.x * kColsThreads + tid) * VEC;
-  const bool active = m0 < total;
+  bool active = m0 < total;
   int64_t r = 0, c = 0;
   if (active) {
     r = m0 / C;
     c = m0 - r * C;
+    // this thread reads X[r, 0 .. L-1, c .. c+VEC-1], writes Y[r, kb0 .., c ..]
+    active = TK_DBG_IN(r * L * C + c, (r * L + L - 1) * C + c + VEC - 1, R * L * C) &&
+             TK_DBG_IN((r * K + kb0) * C + c, (r * K + min(K, kb0 + KB) - 1) * C + c + VEC - 1, R * K * C);
   }
   const TIn* xp = X + (r * L) * C + c;
 #pragma unroll
@@ -168,7 +175,8 @@ __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccO
     __syncthreads();
     for (int i = tid; i < kColsLChunk * KB; i += kColsThreads) {
       const int l = i / KB, k = i - (i / KB) * KB;
-      Fs[l][k] = (l < lc && kb0 + k < K) ? F[(int64_t)(l0 + l) * K + kb0 + k] : A(0);
+      const int64_t e = (int64_t)(l0 + l) * K + kb0 + k;
+      Fs[l][k] = (l < lc && kb0 + k < K && TK_DBG_IN(e, e, (int64_t)L * K)) ? F[e] : A(0);
     }
     __syncthreads();
     for (int ll = 0; ll < lc; ++ll) {
@@ -239,7 +247,9 @@ __global__ void __launch_bounds__(kColsThreads, (KB * sizeof(typename AccOf<TIn>
   const int tid = threadIdx.x;
   const int kb0 = blockIdx.y * KB;
   const int64_t r = (int64_t)blockIdx.x * kColsThreads + tid;
-  const bool active = r < R;
+  // this thread reads row r of X (L elements) and writes Y[r, kb0 ..]
+  const bool active = r < R && TK_DBG_IN(r * L, r * L + L - 1, R * L) &&
+                      TK_DBG_IN(r * K + kb0, r * K + min(K, kb0 + KB) - 1, R * K);
   const TIn* xp = X + (active ? r : 0) * L;
   const int nsteps = L / VEC;
 #pragma unroll
@@ -255,7 +265,8 @@ __global__ void __launch_bounds__(kColsThreads, (KB * sizeof(typename AccOf<TIn>
     __syncthreads();
     for (int i = tid; i < kColsLChunk * KB; i += kColsThreads) {
       const int l = i / KB, k = i - (i / KB) * KB;
-      Fs[l][k] = (l < lc && kb0 + k < K) ? F[(int64_t)(l0 + l) * K + kb0 + k] : A(0);
+      const int64_t e = (int64_t)(l0 + l) * K + kb0 + k;
+      Fs[l][k] = (l < lc && kb0 + k < K && TK_DBG_IN(e, e, (int64_t)L * K)) ? F[e] : A(0);
     }
     __syncthreads();
     for (int ll = 0; ll < lc; ll += VEC) {
@@ -313,11 +324,13 @@ __global__ void __launch_bounds__(kRowsThreads)
     for (int i = threadIdx.x; i < kRowsThreads * kRowsLChunk; i += kRowsThreads) {
       const int rr = i / kRowsLChunk, ll = i - rr * kRowsLChunk;
       const int64_t r = r0 + rr;
-      Xs[rr][ll] = (r < R && ll < lc) ? load_one<TIn>(X + r * L + l0 + ll) : A(0);
+      const int64_t e = r * L + l0 + ll;
+      Xs[rr][ll] = (r < R && ll < lc && TK_DBG_IN(e, e, R * L)) ? load_one<TIn>(X + e) : A(0);
     }
     for (int i = threadIdx.x; i < kRowsLChunk * KB; i += kRowsThreads) {
       const int l = i / KB, k = i - (i / KB) * KB;
-      Fs[l][k] = (l < lc && kb0 + k < K) ? F[(int64_t)(l0 + l) * K + kb0 + k] : A(0);
+      const int64_t e = (int64_t)(l0 + l) * K + kb0 + k;
+      Fs[l][k] = (l < lc && kb0 + k < K && TK_DBG_IN(e, e, (int64_t)L * K)) ? F[e] : A(0);
     }
     __syncthreads();
 #pragma unroll 4
@@ -328,7 +341,7 @@ __global__ void __launch_bounds__(kRowsThreads)
     }
   }
   const int64_t r = r0 + threadIdx.x;
-  if (r >= R) return;
+  if (r >= R || !TK_DBG_IN(r * K + kb0, r * K + min(K, kb0 + KB) - 1, R * K)) return;
   TOut* yp = Y + r * K + kb0;
 #pragma unroll
   for (int k = 0; k < KB; ++k)

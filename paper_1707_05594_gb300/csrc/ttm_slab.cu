@@ -58,7 +58,12 @@ __global__ void __launch_bounds__(kSlabThreads)
   const int tid = threadIdx.x;
   constexpr int kTile = kSlabThreads * RPT;
   const int64_t r0 = (int64_t)blockIdx.x * kTile;
-  const int nrows = (int)min((int64_t)kTile, R - r0);
+  // the tile's rows of X and of Y (the same range for every thread, so that
+  // a failed check skips the block's accesses but keeps its barriers)
+  const int nrows = TK_DBG_IN(r0 * L, (r0 + min((int64_t)kTile, R - r0)) * L - 1, R * L) &&
+                            TK_DBG_IN(r0 * K, (r0 + min((int64_t)kTile, R - r0)) * K - 1, R * K)
+                        ? (int)min((int64_t)kTile, R - r0)
+                        : 0;
   for (int i = tid; i < KB * Lp; i += kSlabThreads) {
     const int k = i / Lp, l = i - (i / Lp) * Lp;
     Ft[i] = (k < K && l < L) ? F[(int64_t)l * K + k] : 0.f;
@@ -156,7 +161,11 @@ __global__ void __launch_bounds__(kSlabThreads)
   float* Os = Xs;
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * kSlabThreads;
-  const int nrows = (int)min((int64_t)kSlabThreads, R - r0);
+  // the tile's rows of X and of Y (block-uniform check, as above)
+  const int nrows = TK_DBG_IN(r0 * L, (r0 + min((int64_t)kSlabThreads, R - r0)) * L - 1, R * L) &&
+                            TK_DBG_IN(r0 * K, (r0 + min((int64_t)kSlabThreads, R - r0)) * K - 1, R * K)
+                        ? (int)min((int64_t)kSlabThreads, R - r0)
+                        : 0;
   load_f<KB>(Fs, F, L, K);
   stage_issue(Xs, X + r0 * L, nrows * L);
   cp_wait_all();
@@ -206,8 +215,12 @@ __global__ void __launch_bounds__(kSlabThreads)
   TIn* Xs = reinterpret_cast<TIn*>(slab_smem + align16((size_t)L * KB * 4));
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * S;
-  const int ns = (int)min((int64_t)S, R - r0);
   const int LC = L * C;
+  // the tile's slabs of X and of Y (block-uniform check)
+  const int ns = TK_DBG_IN(r0 * LC, (r0 + min((int64_t)S, R - r0)) * LC - 1, R * LC) &&
+                         TK_DBG_IN(r0 * K * C, (r0 + min((int64_t)S, R - r0)) * K * C - 1, R * K * C)
+                     ? (int)min((int64_t)S, R - r0)
+                     : 0;
   load_f<KB>(Fs, F, L, K);
   stage_issue(Xs, X + r0 * LC, ns * LC);
   cp_wait_all();

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (kRows) {
           const int64_t r = t * kTileM + row;
-          if (r < P.R) {
+          if (r < P.R && TK_DBG_IN(r * P.K + k0, r * P.K + min(P.K, k0 + 16) - 1, P.R * P.K)) {
             TOut* yp = Y + r * P.K + k0;
             if (P.vec_rows && k0 + 16 <= P.K) {
               // 16 consecutive outputs of this row: 16-byte vector stores
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else if (P.pack2) {
           const int64_t r = 2 * t + (row >> 6);
           const int64_t c = row & 63;
-          if (r < P.R) {
+          if (r < P.R && TK_DBG_IN((r * P.K) * P.C + c, (r * P.K + P.K - 1) * P.C + c, P.R * P.K * P.C)) {
             TOut* yp = Y + (r * P.K) * P.C + c;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else {
           const int64_t r = t / P.ctiles;
           const int64_t c = (t - r * P.ctiles) * kTileM + row;
-          if (c < P.C) {
+          if (c < P.C && TK_DBG_IN((r * P.K) * P.C + c, (r * P.K + P.K - 1) * P.C + c, P.R * P.K * P.C)) {
             TOut* yp = Y + (r * P.K) * P.C + c;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[buf]);
         }
-        if (c < P.C) {
+        if (c < P.C && TK_DBG_IN((r * P.K) * P.C + c, (r * P.K + P.K - 1) * P.C + c, P.R * P.K * P.C)) {
           TOut* yp = Y + (r * P.K) * P.C + c;
 #pragma unroll
           for (int j = 0; j < 16; ++j)
@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(kF8Threads, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[buf]);
         }
-        if (c < P.C) {
+        if (c < P.C && TK_DBG_IN((r * P.K) * P.C + c, (r * P.K + P.K - 1) * P.C + c, P.R * P.K * P.C)) {
           TOut* yp = Y + (r * P.K) * P.C + c;
 #pragma unroll
           for (int j = 0; j < 16; ++j)
@@ -1047,7 +1047,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[buf]);
         }
-        if (c < J.S) {
+        // Y of either job holds R * G * K * S values (mode a: [R][K][G * S];
+        // mode b: [R * G][K][S])
+        const int64_t yo = yp - static_cast<TOut*>(J.Y);
+        if (c < J.S && TK_DBG_IN(yo, yo + (int64_t)(J.K - 1) * ystride, J.R * P.G * J.K * J.S)) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
             if (k0 + j < J.K) yp[(int64_t)(k0 + j) * ystride] = to_out<TOut>(hi[j] + lo[j]);
