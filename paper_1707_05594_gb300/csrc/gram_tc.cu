@@ -23,10 +23,12 @@
 // TMEM every 16 stages, and add both levels to W with FP64 atomics at the
 // end.
 //
-// Units: the R * ceil(C / 32) column chunks of every job are split into
-// contiguous ranges, about as many CTAs in all as the GPU has SMs, weighted
-// by the job's MMA width and the rows it loads.  One CTA per SM (~190 KB of
-// shared memory, 512 TMEM columns).
+// Units: the R * ceil(C / 32) column chunks of every job are cut into the
+// same number of contiguous ranges per job (about as many CTAs in all as the
+// GPU has SMs, at least 32 chunks each: fewer CTAs, and fewer atomics, for
+// small Grams), so that the jobs that share a block read the same columns at
+// about the same time and the second read of a block is served by L2.  One
+// CTA per SM (~200 KB of shared memory, 512 TMEM columns).
 //
 // Warp roles (576 threads): warp 0 TMA producer (one lane); warp 1 TMEM
 // allocation and MMA issuer (one lane); warps 2-17 split each landed stage in
@@ -56,6 +58,7 @@ constexpr int kGLag = 2;                    // stage s is drained after stage s 
 constexpr int kGFold = 16;                  // stage sums per level-1 run
 constexpr int kGMaxStages = 16;
 constexpr int kGMaxJobs = 10;               // block pairs for L <= 512
+constexpr int kGMinChunks = 32;             // chunks per unit at least
 constexpr uint32_t kGSum2 = kGAcc * kGB;     // TMEM column of the second-level sums
 constexpr uint32_t kGTmemCols = 512;
 constexpr size_t kGSmemBudget = 200 * 1024;  // ring
@@ -69,8 +72,8 @@ struct GramParams {
   int two;            // two blocks per stage (some job has I != J)
   int stages;
   int njobs;
+  int units;          // units per job
   int bi[kGMaxJobs], bj[kGMaxJobs], n[kGMaxJobs];
-  int first_unit[kGMaxJobs + 1];
   double* W;
   int* status;
 };
@@ -154,12 +157,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   // this CTA's unit: job j, chunk range [q0, q1)
-  const int u = blockIdx.x;
-  int j = 0;
-  while (j + 1 < P.njobs && u >= P.first_unit[j + 1]) ++j;
-  const int64_t nsplit = P.first_unit[j + 1] - P.first_unit[j];
-  const int64_t sidx = u - P.first_unit[j];
-  const int64_t q0 = P.Q * sidx / nsplit, q1 = P.Q * (sidx + 1) / nsplit;
+  const int j = (int)blockIdx.x / P.units;
+  const int64_t sidx = (int64_t)blockIdx.x - (int64_t)j * P.units;
+  const int64_t q0 = P.Q * sidx / P.units, q1 = P.Q * (sidx + 1) / P.units;
   const uint32_t nq = (uint32_t)(q1 - q0);
   const int I = P.bi[j], J = P.bj[j], N = P.n[j];
   const bool diag = I == J;
@@ -396,28 +396,19 @@ int launch_gram_tc(const float* Z, int64_t R, int64_t L, int64_t C, double* W, c
   const int nb = (int)((L + kGB - 1) / kGB);
   P.rows = nb == 1 ? (int)((L + 15) / 16 * 16) : kGB;
   P.two = nb > 1 ? 1 : 0;
-  // jobs and their weights: MMA width N plus the valid rows the job loads
-  double w[kGMaxJobs], wsum = 0;
   P.njobs = 0;
   for (int I = 0; I < nb; ++I)
     for (int J = I; J < nb; ++J) {
       const int k = P.njobs++;
       const int64_t rowsJ = std::min<int64_t>(kGB, L - (int64_t)J * kGB);
-      const int64_t rowsI = std::min<int64_t>(kGB, L - (int64_t)I * kGB);
       P.bi[k] = I;
       P.bj[k] = J;
       P.n[k] = (int)((rowsJ + 15) / 16 * 16);
-      w[k] = (double)P.n[k] + 0.6 * (double)(rowsI + (I == J ? 0 : rowsJ));
-      wsum += w[k];
     }
-  // units: about one per SM in all, at least 4 chunks each
-  const int64_t sms = sm_count();
-  P.first_unit[0] = 0;
-  for (int k = 0; k < P.njobs; ++k) {
-    int64_t u = (int64_t)(sms * w[k] / wsum + 0.5);
-    u = std::max<int64_t>(1, std::min<int64_t>(u, std::max<int64_t>(1, P.Q / 4)));
-    P.first_unit[k + 1] = P.first_unit[k] + (int)u;
-  }
+  // the same number of units per job, about one CTA per SM in all, at least
+  // kGMinChunks chunks per unit
+  const int64_t per_job = std::max<int64_t>(1, sm_count() / P.njobs);
+  P.units = (int)std::max<int64_t>(1, std::min<int64_t>(per_job, P.Q / kGMinChunks));
   const size_t stage = (size_t)2 * (P.two ? 2 : 1) * (size_t)P.rows * 128;
   P.stages = (int)std::min<size_t>(kGMaxStages, kGSmemBudget / stage);
   if (P.stages < 2) return fail(TUCKER_ERR_UNSUPPORTED, "gram_tc: stage does not fit");
@@ -438,7 +429,7 @@ int launch_gram_tc(const float* Z, int64_t R, int64_t L, int64_t C, double* W, c
   size_t smem = 1024 + kGBarBytes + (size_t)P.stages * stage + (size_t)(kGB - P.rows) * 128;
   smem = std::max<size_t>(smem, 120 * 1024);
   TK_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  gram_tc_kernel<<<(unsigned)P.first_unit[P.njobs], kGThreads, smem, s>>>(m, P);
+  gram_tc_kernel<<<(unsigned)(P.njobs * P.units), kGThreads, smem, s>>>(m, P);
   TK_LAUNCH_CHECK("gram_tc");
   return TUCKER_OK;
 }

@@ -171,3 +171,25 @@ def test_tc_gram_in_sthosvd_matches_oracle(tk, orc):
         Qa, _ = np.linalg.qr(Fo[n])
         s = np.linalg.norm(Fg - Qa @ (Qa.T @ Fg), 2)
         assert s <= 1e-4, (n, s)
+
+
+def test_tc_gram_scaled_rows(tk, orc):
+    """Rows whose magnitudes span 1e-10 .. 1e10, zero rows, and values
+    spread over 2^10 inside a row (every product stays in FP32's normal
+    range, as both FP32 Gram paths need): within the bound of the module
+    docstring, and exactly zero for the zero rows."""
+    L, C = 40, 1000
+    rng = np.random.default_rng(17)
+    Z = rng.standard_normal((L, C)) * np.exp2(rng.uniform(-10, 0, (L, C)))
+    Z *= (10.0 ** np.linspace(-10, 10, L))[:, None]
+    Z[[3, 17, 29]] = 0.0
+    Z = Z.astype(np.float32)
+    Zd = Z.astype(np.float64)
+    ref = orc.gram(Zd, 0)
+    mag = orc.gram(np.abs(Zd), 0)
+    W = gram_gpu(tk, torch.from_numpy(Z).cuda(), 0)
+    assert np.all(np.isfinite(W))
+    err = np.abs(W - ref)
+    bound = tc_bound((L, C), 0) * mag
+    assert np.all(err <= bound + 1e-300), np.max(err / (mag + 1e-300))
+    assert np.all(W[[3, 17, 29]] == 0.0) and np.all(W[:, [3, 17, 29]] == 0.0)
