@@ -1109,10 +1109,14 @@ def run_batch_form(args):
     """Batched form on the 4096-tensor workload (3-way FP32, lengths on
     [16, 96], ranks on [4, min(16, L)], rho 1e-3): STHOSVD, then 5 HOOI sweeps
     as replays of a recorded CUDA graph (one graph launch per sweep, each sweep
-    with the fit of the factors it starts from), against the plain FP32 GPU
-    form: tucker_hooi_sweep_core + tucker_fit called tensor by tensor from the
-    same STHOSVD factors.  Both are timed with CUDA events over the 5 sweeps;
-    the fit of each tensor's final factors is compared."""
+    with the fit of the factors it starts from).  Headline: the fused sweep
+    (tucker_batch_sweep_fused: one persistent launch over a work queue of
+    tensors); beside it, the per-site form (about 20 kernels per sweep, one
+    per tree level, Gram, eigensolver stage and fit step, launch
+    configurations autotuned).  Against the plain FP32 GPU form:
+    tucker_hooi_sweep_core + tucker_fit called tensor by tensor from the same
+    STHOSVD factors.  All are timed with CUDA events over the 5 sweeps; the
+    fit of each tensor's final factors is compared."""
     import torch
 
     import paper_1707_05594_gb300 as tk
@@ -1141,19 +1145,29 @@ def run_batch_form(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), tk.tucker_launch_count() - n0
 
+    # the per-site form: default launch configurations, then autotuned ones
+    # (the graphs are recorded again with the chosen configurations)
+    d.fused = False
+    tk.tucker_batch_set_fused(b, False)
+    d._graphs = None
     run_batched()  # records the two graphs, warms up
     ms_def, _ = run_batched()
     F_def = d.factors().clone()
-    # autotune the launch configurations on the STHOSVD factors; the graphs
-    # are recorded again with the chosen configurations
     d.cur = 0
     d.Fbuf[0].copy_(F_sth)
     t0 = time.perf_counter()
     sites = d.autotune(reps=5)
     tune_s = time.perf_counter() - t0
     run_batched()
-    ms_b, launches_b = run_batched()
+    ms_site, launches_site = run_batched()
     same_bits = bool(torch.equal(d.factors(), F_def))
+    # the fused form (the default of BatchDecomposition)
+    d.fused = True
+    tk.tucker_batch_set_fused(b, True)
+    d._graphs = None
+    run_batched()
+    ms_b, launches_b = run_batched()
+    fused_same_bits = bool(torch.equal(d.factors(), F_def))
     # fit of the final factors: one more direct sweep yields their core
     Fb = d.factors().clone()
     Fjunk = torch.empty_like(Fb)
@@ -1183,11 +1197,16 @@ def run_batch_form(args):
                        "sweeps_per_s": round(S * 1e3 / ms_b, 2),
                        "graph_launches_per_sweep": 1,
                        "kernels_per_sweep": round(launches_b / S, 1),
-                       "min_fit": float(fit_b.min()), "mean_fit": float(fit_b.mean()),
-                       "launch_configs": "autotuned (tucker_batch_autotune)"},
+                       "form": "fused: one persistent launch per sweep (work queue of tensors), then the "
+                               "full eigensolver path's launches over the matrices its check listed",
+                       "same_bits_as_per_site": fused_same_bits,
+                       "min_fit": float(fit_b.min()), "mean_fit": float(fit_b.mean())},
+           "per_site": {"ms_per_sweep": round(ms_site / S, 4), "kernels_per_sweep": round(launches_site / S, 1),
+                        "launch_configs": "autotuned (tucker_batch_autotune)",
+                        "fused_speedup": round(ms_site / ms_b, 3)},
            "autotune": {"seconds": round(tune_s, 3),
                         "ms_per_sweep_default_configs": round(ms_def / S, 4),
-                        "speedup_tuned_vs_default": round(ms_def / ms_b, 3),
+                        "speedup_tuned_vs_default": round(ms_def / ms_site, 3),
                         "same_bits_as_default": same_bits, "sites": len(sites)},
            "vs_oracle": orc,
            "roofline": {"bound": "hbm", "bytes_per_sweep": int(step_b), "tree_bytes": int(tree_b),

@@ -42,6 +42,7 @@ extern "C" {
 #define TUCKER_ERR_CUDA (-4)
 #define TUCKER_ERR_TIMEOUT (-5)
 #define TUCKER_ERR_NONFINITE (-6)
+#define TUCKER_ERR_INCOMPLETE (-7) /* device error word: a fused batched sweep ended with tensors untaken */
 
 #define TUCKER_MAX_MODES 8
 
@@ -473,8 +474,33 @@ int tucker_batch_norm2(tucker_batch_t b, const float* T, double* normT2, void* w
  * residual is below about 1e-2 of ||T||.)  normT2 from tucker_batch_norm2. */
 int tucker_batch_fit(tucker_batch_t b, const float* T, const float* F, const float* G,
                      const double* normT2, double* fit, void* ws, size_t ws_bytes, void* stream);
+/* The same sweep and fit as one persistent, fused launch (Fig. 2 per
+ * tensor): each CTA takes tensors from a device work queue (an atomic
+ * counter, largest tensors first) and runs, for each, its TTM tree, leaf
+ * Grams, the core of the input factors (G_in), the fit of F_in and G_in
+ * (as tucker_batch_fit) and the eigensolver warm-started from F_in (F_out);
+ * no CTA waits for another.  Matrices whose warm-start check fails are
+ * listed and finished by the full eigensolver path in launches after it,
+ * which do no work when the list is empty.  The results equal those of
+ * tucker_batch_sweep + tucker_batch_fit (the fit's per-tensor sum of
+ * squares is added in another order).  The last CTA verifies that every
+ * tensor was taken, else it records TUCKER_ERR_INCOMPLETE in the device
+ * error word (tucker_device_status), and resets the queue for the next
+ * launch.  TUCKER_ERR_UNSUPPORTED under kernel policy bit 1 (full
+ * eigensolver path). */
+int tucker_batch_sweep_fused(tucker_batch_t b, const float* T, const float* F_in, float* F_out,
+                             float* G_in, const double* normT2, double* fit, void* ws, size_t ws_bytes,
+                             void* stream);
+/* Byte offset in the workspace of the fused sweep's work queue (three ints:
+ * next tensor, CTAs done, tensors done; all zero between launches).  Host
+ * only; for tests that corrupt the queue to check the detection above. */
+int tucker_batch_queue_offset(tucker_batch_t b, size_t* off);
+/* on = 1: tucker_batch_graph_create records tucker_batch_sweep_fused (when
+ * G_in, normT2 and fit are all non-NULL); on = 0: the per-site launches. */
+int tucker_batch_set_fused(tucker_batch_t b, int on);
 /* Records tucker_batch_sweep (and, when G_in, normT2 and fit are all non-NULL,
- * tucker_batch_fit of F_in and G_in) with these buffers into an executable CUDA graph
+ * tucker_batch_fit of F_in and G_in; or the two as tucker_batch_sweep_fused
+ * after tucker_batch_set_fused(b, 1)) with these buffers into an executable CUDA graph
  * (*graph_exec, a cudaGraphExec_t).  Nothing runs until
  * tucker_batch_graph_launch; each launch is one sweep of the whole batch on
  * the given stream.  The buffers must stay valid while the graph is used. */

@@ -28,7 +28,8 @@ COST_MACS, COST_ELEMS = 0, 1
 PLAN_NO_FUSED_ROOT = 1
 PLAN_STHOSVD_ORDER = 2
 ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "WORKSPACE", -4: "CUDA", -5: "TIMEOUT",
-          -6: "NONFINITE"}
+          -6: "NONFINITE", -7: "INCOMPLETE"}
+TUCKER_ERR_INCOMPLETE = -7
 
 _lib = None
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -138,6 +139,9 @@ def lib():
     L.tucker_batch_sweep.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
     L.tucker_batch_norm2.argtypes = [vp, vp, vp, vp, sz, vp]
     L.tucker_batch_fit.argtypes = [vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.tucker_batch_sweep_fused.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.tucker_batch_set_fused.argtypes = [vp, ctypes.c_int]
+    L.tucker_batch_queue_offset.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.tucker_batch_graph_create.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, sz, ctypes.POINTER(vp)]
     L.tucker_batch_graph_launch.argtypes = [vp, vp, vp]
     L.tucker_batch_graph_destroy.argtypes = [vp]
@@ -721,6 +725,24 @@ def tucker_batch_sweep(b: BatchPlan, T, F_in, F_out, G_in, ws, stream=None):
            "tucker_batch_sweep")
 
 
+def tucker_batch_sweep_fused(b: BatchPlan, T, F_in, F_out, G_in, normT2, fit, ws, stream=None):
+    """tucker_batch_sweep + tucker_batch_fit of (F_in, G_in) as one
+    persistent launch (plus the gated full eigensolver path)."""
+    _check(lib().tucker_batch_sweep_fused(b.handle, _vp(T), _vp(F_in), _vp(F_out), _vp(G_in), _vp(normT2),
+                                          _vp(fit), _vp(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "tucker_batch_sweep_fused")
+
+
+def tucker_batch_queue_offset(b: BatchPlan) -> int:
+    off = ctypes.c_size_t(0)
+    _check(lib().tucker_batch_queue_offset(b.handle, ctypes.byref(off)), "tucker_batch_queue_offset")
+    return off.value
+
+
+def tucker_batch_set_fused(b: BatchPlan, on: bool):
+    _check(lib().tucker_batch_set_fused(b.handle, 1 if on else 0), "tucker_batch_set_fused")
+
+
 def tucker_batch_norm2(b: BatchPlan, T, normT2, ws, stream=None):
     _check(lib().tucker_batch_norm2(b.handle, _vp(T), _vp(normT2), _vp(ws),
                                     ws.numel() * ws.element_size(), _stream(stream)),
@@ -803,10 +825,14 @@ class BatchDecomposition:
     After each sweep G and fit describe the factors the sweep started from;
     factors() is the newest factor buffer."""
 
-    def __init__(self, T, dims, ranks):
+    def __init__(self, T, dims, ranks, fused: bool = True):
         import torch
         self.T = T
         self.b = BatchPlan(dims, ranks)
+        # fused: each sweep (and its fit) is one persistent launch
+        # (tucker_batch_sweep_fused); else the per-site launches
+        self.fused = bool(fused)
+        tucker_batch_set_fused(self.b, self.fused)
         if T.numel() != self.b.t_elems or T.dtype != torch.float32:
             raise ValueError("T must hold the packed FP32 tensors of the batch")
         dev = T.device
@@ -843,6 +869,8 @@ class BatchDecomposition:
                     BatchGraph(self.b, self.T, A, B, self.G, self.normT2, self.fit_out, self.ws),
                     BatchGraph(self.b, self.T, B, A, self.G, self.normT2, self.fit_out, self.ws))
             self._graphs[self.cur].launch()
+        elif self.fused:
+            tucker_batch_sweep_fused(self.b, self.T, src, dst, self.G, self.normT2, self.fit_out, self.ws)
         else:
             tucker_batch_sweep(self.b, self.T, src, dst, self.G, self.ws)
             tucker_batch_fit(self.b, self.T, src, self.G, self.normT2, self.fit_out, self.ws)

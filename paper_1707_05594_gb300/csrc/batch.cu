@@ -24,265 +24,13 @@
 #include <unordered_map>
 #include <vector>
 
-#include "common.cuh"
+#include "batch_bodies.cuh"
+#include "batch_fused.h"
 
 namespace tk {
 namespace {
 
-constexpr int kBThreads = 256;
-
-// One TTM work unit (a tree node of one tensor, or one STHOSVD step, or the
-// core step).  Offsets are in elements.
-struct BNode {
-  int64_t in_off;    // into T (in_src 0) or the intermediate region (1)
-  int64_t out_off;   // into the intermediate region (out_dst 0) or G (1)
-  int64_t f_off;     // into F (L x K factor, applied transposed)
-  int64_t R, C;      // view [R][L][C] of the input
-  int32_t L, K;
-  int64_t tile0;     // first tile of this node
-  int8_t in_src, out_dst;
-  int8_t staged;     // rows staged through shared memory (set with the tile map)
-  int8_t pad[5];
-};
-
-// One 32 x 32 tile of a leaf Gram W = Z_(n) Z_(n)^T (lower triangle, ti >= tj).
-struct BGram {
-  int64_t z_off;     // into T (z_src 0) or intermediates (1)
-  int64_t w_off;     // into the Gram region (doubles)
-  int64_t R, C;
-  int32_t L, ti, tj, z_src;
-};
-
-// Launch configuration of one batched launch site (a tree level, the core
-// step, an STHOSVD step or a fit step), picked by tucker_batch_autotune.
-// None of the knobs changes the order in which any output's terms are summed.
-//   ppt:     positions per thread of the direct (long-row) tiles: a tile is
-//            256 * ppt consecutive (r, c) positions
-//   stage_c: nodes with rows shorter than stage_c (C < stage_c) take whole
-//            rows per tile, staged through shared memory (0: never)
-//   order:   0 = nodes in plan order (tensor by tensor), 1 = nodes with the
-//            most tiles first (longest-processing-time order)
-//   async:   direct tiles copy each chunk of 32 input rows into shared memory
-//            with cp.async before the multiply-adds (one position per thread)
-struct BCfg {
-  int ppt = 1, stage_c = 32, order = 0, async = 0;
-};
-
-// Tiles of a node under a configuration.  Staged tiles take 256 / C whole
-// rows; direct tiles take 256 * ppt consecutive positions and read along c.
-inline bool node_staged(int64_t C, const BCfg& cfg) { return C < cfg.stage_c; }
-inline int64_t node_tiles(int64_t R, int64_t C, const BCfg& cfg) {
-  if (node_staged(C, cfg)) {
-    const int64_t rt = kBThreads / C;
-    return (R + rt - 1) / rt;
-  }
-  const int64_t tp = (int64_t)kBThreads * cfg.ppt;
-  return (R * C + tp - 1) / tp;
-}
-
-// Out[r, k, c] = sum_l F[l, k] In[r, l, c] for one tile of one node, F in
-// chunks of 32 l through shared memory.  Each thread accumulates the K
-// outputs of each of its positions (KB >= K registers per position), l in
-// increasing order.  Staged tiles (short rows) copy the rows of the chunk
-// into shared memory transposed, Ts[l][position], with coalesced loads, and
-// write their outputs back the same way; they take one position per thread.
-template <int KB>
-__device__ __forceinline__ void bttm_staged(const BNode& nd, int64_t t, const float* __restrict__ src,
-                                            float* __restrict__ dst, const float* __restrict__ f,
-                                            float* Fs /* [32][KB] */, float (*Ts)[kBThreads + 1]) {
-  const int tid = threadIdx.x;
-  const int C = (int)nd.C;
-  const int rt = kBThreads / C;
-  const int64_t r0 = t * rt;
-  // the tile's rows of the node's input and output views (block-uniform
-  // check: a failed one skips the tile's accesses and keeps its barriers)
-  const int64_t r1 = r0 + min((int64_t)rt, nd.R - r0);
-  const int nrows = TK_DBG_IN(r0 * nd.L * C, r1 * nd.L * C - 1, nd.R * nd.L * C) &&
-                            TK_DBG_IN(r0 * nd.K * C, r1 * nd.K * C - 1, nd.R * nd.K * C)
-                        ? (int)(r1 - r0)
-                        : 0;
-  const bool active = tid < nrows * C;
-  float acc[KB];
-#pragma unroll
-  for (int k = 0; k < KB; ++k) acc[k] = 0.f;
-  for (int l0 = 0; l0 < nd.L; l0 += 32) {
-    const int lc = min(32, nd.L - l0);
-    __syncthreads();
-    for (int i = tid; i < 32 * KB; i += kBThreads) {
-      const int l = i / KB, k = i - (i / KB) * KB;
-      Fs[i] = (l < lc && k < nd.K) ? f[(int64_t)(l0 + l) * nd.K + k] : 0.f;
-    }
-    // row rr of the chunk: lc * C contiguous elements
-    const int seg = lc * C;
-    const SmallDiv dseg(seg), dc(C);
-    for (int i = tid; i < nrows * seg; i += kBThreads) {
-      const int rr = dseg.div(i), o = i - rr * seg;
-      const int l = dc.div(o), cc = o - l * C;
-      Ts[l][rr * C + cc] = src[((r0 + rr) * nd.L + l0) * C + o];
-    }
-    __syncthreads();
-    if (active) {
-      for (int l = 0; l < lc; ++l) {
-        const float x = Ts[l][tid];
-#pragma unroll
-        for (int k = 0; k < KB; ++k) acc[k] = fmaf(Fs[l * KB + k], x, acc[k]);
-      }
-    }
-  }
-  // outputs through shared memory: row rr owns K * C contiguous elements
-  __syncthreads();
-  if (active) {
-#pragma unroll
-    for (int k = 0; k < KB; ++k)
-      if (k < nd.K) Ts[k][tid] = acc[k];
-  }
-  __syncthreads();
-  const int seg = nd.K * C;
-  const SmallDiv dseg(seg), dc(C);
-  for (int i = tid; i < nrows * seg; i += kBThreads) {
-    const int rr = dseg.div(i), o = i - rr * seg;
-    const int k = dc.div(o), cc = o - k * C;
-    dst[(r0 + rr) * seg + o] = Ts[k][rr * C + cc];
-  }
-}
-
-constexpr int kDepth = 8;  // rows of a chunk loaded ahead by the direct TTM tiles
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// Direct tile, one position per thread, each chunk of up to 32 input rows
-// copied into Ts[l][thread] by cp.async (32 copies per thread in flight, no
-// registers held while they travel), then multiplied from shared memory.
-template <int KB>
-__device__ __forceinline__ void bttm_async(const BNode& nd, int64_t t, const float* __restrict__ src,
-                                           float* __restrict__ dst, const float* __restrict__ f,
-                                           float* Fs /* [32][KB] */, float (*Ts)[kBThreads + 1]) {
-  const int tid = threadIdx.x;
-  const int64_t p = t * kBThreads + tid;
-  bool act = p < nd.R * nd.C;
-  const int64_t r = act ? p / nd.C : 0, c = act ? p - r * nd.C : 0;
-  // input fibre In[r, :, c] and outputs Out[r, :, c] of the node's views
-  act = act && TK_DBG_IN((r * nd.L) * nd.C + c, (r * nd.L + nd.L - 1) * nd.C + c, nd.R * nd.L * nd.C) &&
-        TK_DBG_IN((r * nd.K) * nd.C + c, (r * nd.K + nd.K - 1) * nd.C + c, nd.R * nd.K * nd.C);
-  const float* in = src + (r * nd.L) * nd.C + c;
-  float acc[KB];
-#pragma unroll
-  for (int k = 0; k < KB; ++k) acc[k] = 0.f;
-  for (int l0 = 0; l0 < nd.L; l0 += 32) {
-    const int lc = min(32, nd.L - l0);
-    __syncthreads();  // the previous chunk's reads of Ts and Fs are done
-    if (act)
-      for (int l = 0; l < lc; ++l) cp_async4(&Ts[l][tid], in + (int64_t)(l0 + l) * nd.C);
-    for (int i = tid; i < 32 * KB; i += kBThreads) {
-      const int l = i / KB, k = i - (i / KB) * KB;
-      Fs[i] = (l < lc && k < nd.K) ? f[(int64_t)(l0 + l) * nd.K + k] : 0.f;
-    }
-    cp_async_commit_wait_all();
-    __syncthreads();
-    if (act) {
-      for (int l = 0; l < lc; ++l) {
-        const float x = Ts[l][tid];
-#pragma unroll
-        for (int k = 0; k < KB; ++k) acc[k] = fmaf(Fs[l * KB + k], x, acc[k]);
-      }
-    }
-  }
-  if (!act) return;
-  float* out = dst + (r * nd.K) * nd.C + c;
-#pragma unroll
-  for (int k = 0; k < KB; ++k)
-    if (k < nd.K) out[(int64_t)k * nd.C] = acc[k];
-}
-
-template <int KB, int PPT>
-__device__ __forceinline__ void bttm_direct(const BNode& nd, int64_t t, const float* __restrict__ src,
-                                            float* __restrict__ dst, const float* __restrict__ f,
-                                            float* Fs /* [32][KB] */) {
-  const int tid = threadIdx.x;
-  const int64_t M = nd.R * nd.C;
-  const float* in[PPT];
-  int64_t ob[PPT];
-  bool act[PPT];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    const int64_t p = (t * PPT + j) * kBThreads + tid;
-    act[j] = p < M;
-    const int64_t r = act[j] ? p / nd.C : 0, c = act[j] ? p - r * nd.C : 0;
-    // input fibre In[r, :, c] and outputs Out[r, :, c] of the node's views
-    act[j] = act[j] && TK_DBG_IN((r * nd.L) * nd.C + c, (r * nd.L + nd.L - 1) * nd.C + c, nd.R * nd.L * nd.C) &&
-             TK_DBG_IN((r * nd.K) * nd.C + c, (r * nd.K + nd.K - 1) * nd.C + c, nd.R * nd.K * nd.C);
-    in[j] = src + (r * nd.L) * nd.C + c;
-    ob[j] = (r * nd.K) * nd.C + c;
-  }
-  float acc[PPT][KB];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j)
-#pragma unroll
-    for (int k = 0; k < KB; ++k) acc[j][k] = 0.f;
-  for (int l0 = 0; l0 < nd.L; l0 += 32) {
-    const int lc = min(32, nd.L - l0);
-    __syncthreads();
-    for (int i = tid; i < 32 * KB; i += kBThreads) {
-      const int l = i / KB, k = i - (i / KB) * KB;
-      Fs[i] = (l < lc && k < nd.K) ? f[(int64_t)(l0 + l) * nd.K + k] : 0.f;
-    }
-    __syncthreads();
-    if (act[0]) {
-      // kDepth rows of the chunk are loaded before their multiply-adds, so
-      // that each thread has kDepth * PPT loads in flight
-      for (int lb = 0; lb < lc; lb += kDepth) {
-        float x[kDepth][PPT];
-#pragma unroll
-        for (int u = 0; u < kDepth; ++u)
-#pragma unroll
-          for (int j = 0; j < PPT; ++j)
-            x[u][j] = (lb + u < lc && act[j]) ? __ldg(in[j] + (int64_t)(l0 + lb + u) * nd.C) : 0.f;
-#pragma unroll
-        for (int u = 0; u < kDepth; ++u) {
-          if (lb + u < lc) {
-#pragma unroll
-            for (int k = 0; k < KB; ++k) {
-              const float fk = Fs[(lb + u) * KB + k];
-#pragma unroll
-              for (int j = 0; j < PPT; ++j) acc[j][k] = fmaf(fk, x[u][j], acc[j][k]);
-            }
-          }
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    if (!act[j]) continue;
-    float* out = dst + ob[j];
-#pragma unroll
-    for (int k = 0; k < KB; ++k)
-      if (k < nd.K) out[(int64_t)k * nd.C] = acc[j][k];
-  }
-}
-
-template <int KB, int PPT, bool ASYNC>
-__device__ __forceinline__ void bttm_tile(const BNode& nd, int64_t t, const float* __restrict__ T,
-                                          const float* __restrict__ F, float* __restrict__ inter,
-                                          float* __restrict__ G, float* Fs,
-                                          float (*Ts)[kBThreads + 1]) {
-  const float* src = (nd.in_src ? inter : T) + nd.in_off;
-  float* dst = (nd.out_dst ? G : inter) + nd.out_off;
-  const float* f = F + nd.f_off;
-  if (nd.staged) bttm_staged<KB>(nd, t, src, dst, f, Fs, Ts);
-  else if (ASYNC) bttm_async<KB>(nd, t, src, dst, f, Fs, Ts);
-  else bttm_direct<KB, PPT>(nd, t, src, dst, f, Fs);
-}
-
-// One block per tile; the block runs the variant whose KB is the smallest of
-// 4, 8, 12, 16, 24, 32 that holds its node's K (KMAX bounds the variants so
-// that the kernel's register count follows the batch's largest rank).
+// One block per tile.
 template <int KMAX, int PPT, bool ASYNC>
 __global__ void __launch_bounds__(kBThreads)
     bttm_kernel(const BNode* __restrict__ nodes, const int* __restrict__ tile_node,
@@ -292,71 +40,15 @@ __global__ void __launch_bounds__(kBThreads)
   __shared__ float Ts[32][kBThreads + 1];
   const int64_t tile = blockIdx.x;
   const BNode nd = nodes[tile_node[tile]];
-  const int64_t t = tile - nd.tile0;
-  if (nd.K <= 4) bttm_tile<4, PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
-  else if (nd.K <= 8 || KMAX <= 8) bttm_tile<(KMAX < 8 ? KMAX : 8), PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
-  else if (nd.K <= 12 || KMAX <= 12) bttm_tile<(KMAX < 12 ? KMAX : 12), PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
-  else if (nd.K <= 16 || KMAX <= 16) bttm_tile<(KMAX < 16 ? KMAX : 16), PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
-  else if (nd.K <= 24 || KMAX <= 24) bttm_tile<(KMAX < 24 ? KMAX : 24), PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
-  else bttm_tile<KMAX, PPT, ASYNC>(nd, t, T, F, inter, G, Fs, Ts);
+  bttm_dispatch<KMAX, PPT, ASYNC>(nd, tile - nd.tile0, T, F, inter, G, Fs, Ts);
 }
 
-// 32 x 32 Gram tile over all M = R*C columns: FP32 products summed in runs of
-// 32 columns, runs added in FP64.  The tile (and its mirror) is written whole.
 __global__ void __launch_bounds__(kBThreads)
     bgram_kernel(const BGram* __restrict__ tiles, const float* __restrict__ T,
                  const float* __restrict__ inter, double* __restrict__ gram) {
-  const BGram g = tiles[blockIdx.x];
   __shared__ float As[32][33];
   __shared__ float Bs[32][33];
-  const float* Z = (g.z_src ? inter : T) + g.z_off;
-  const int64_t M = g.R * g.C;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 2 x 2 entries each
-  double acc64[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-  for (int64_t m0 = 0; m0 < M; m0 += 32) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < 32 * 32; i += kBThreads) {
-      const int mm = i % 32, a = i / 32;
-      const int64_t m = m0 + mm;
-      float va = 0.f, vb = 0.f;
-      if (m < M) {
-        const int64_t r = m / g.C, c = m - (m / g.C) * g.C;
-        const int la = g.ti * 32 + a, lb = g.tj * 32 + a;
-        const int64_t ea = (r * g.L + la) * g.C + c, eb = (r * g.L + lb) * g.C + c;
-        if (la < g.L && TK_DBG_IN(ea, ea, M * g.L)) va = Z[ea];
-        if (lb < g.L && TK_DBG_IN(eb, eb, M * g.L)) vb = Z[eb];
-      }
-      As[a][mm] = va;
-      Bs[a][mm] = vb;
-    }
-    __syncthreads();
-    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 8
-    for (int mm = 0; mm < 32; ++mm) {
-      const float a0 = As[ty * 2][mm], a1 = As[ty * 2 + 1][mm];
-      const float b0 = Bs[tx * 2][mm], b1 = Bs[tx * 2 + 1][mm];
-      acc[0][0] = fmaf(a0, b0, acc[0][0]);
-      acc[0][1] = fmaf(a0, b1, acc[0][1]);
-      acc[1][0] = fmaf(a1, b0, acc[1][0]);
-      acc[1][1] = fmaf(a1, b1, acc[1][1]);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) acc64[i][j] += (double)acc[i][j];
-  }
-  double* W = gram + g.w_off;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int a = g.ti * 32 + ty * 2 + i, b = g.tj * 32 + tx * 2 + j;
-      if (a < g.L && b < g.L) {
-        W[(int64_t)a * g.L + b] = acc64[i][j];
-        if (g.ti != g.tj) W[(int64_t)b * g.L + a] = acc64[i][j];
-      }
-    }
-  }
+  bgram_tile(tiles[blockIdx.x], T, inter, gram, As, Bs);
 }
 
 // ||X_i||^2 per tensor (one block per tensor), FP64 accumulation.
@@ -381,27 +73,6 @@ __global__ void __launch_bounds__(kBThreads)
   }
 }
 
-// One step of the reconstruction G x_0 F_0 ... x_{N-1} F_{N-1} of one tensor
-// (the expansion of mode m): In is viewed as [R][K][C], Out as [R][L][C] with
-// Out[r, l, c] = sum_k F[l, k] In[r, k, c].  The last step of a tensor is not
-// written: it is compared with T and the squared differences are summed.
-struct BExp {
-  int64_t in_off;   // into G (in_src 0) or the intermediate region (1)
-  int64_t out_off;  // into the intermediate region, or T offset for the last step
-  int64_t f_off;
-  int64_t R, C;
-  int32_t K, L;     // contracted length (rank) and output length
-  int64_t tile0;
-  int32_t in_src, last, tensor, pad;
-};
-
-constexpr int kExpMaxL = 200;
-
-// Each thread owns PPT (r, c) positions, 256 apart: it keeps the K inputs
-// In[r, :, c] of each in registers and produces the L outputs one after
-// another (F from shared memory, broadcast).  In the last step the FP32
-// differences T - Out are squared and summed in FP32 per position, then
-// reduced in FP64 per block and added to res2[tensor].
 template <int KB, int PPT>
 __global__ void __launch_bounds__(kBThreads)
     bexpand_kernel(const BExp* __restrict__ steps, const int* __restrict__ tile_step,
@@ -412,84 +83,8 @@ __global__ void __launch_bounds__(kBThreads)
   __shared__ double red[kBThreads / 32];
   const int64_t tile = blockIdx.x;
   const BExp st = steps[tile_step[tile]];
-  const float* f = F + st.f_off;
-  for (int i = threadIdx.x; i < st.L * KB; i += kBThreads) {
-    const int l = i / KB, k = i - (i / KB) * KB;
-    Fs[l][k] = k < st.K ? f[(int64_t)l * st.K + k] : 0.f;
-  }
-  __syncthreads();
-  const int64_t M = st.R * st.C;
-  float y[PPT][KB];
-  int64_t ob[PPT];
-  bool act[PPT];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    const int64_t p = ((tile - st.tile0) * PPT + j) * kBThreads + threadIdx.x;
-    act[j] = p < M;
-    const int64_t r = act[j] ? p / st.C : 0, c = act[j] ? p - r * st.C : 0;
-    // inputs In[r, :, c] ([R][K][C]) and outputs Out[r, :, c] ([R][L][C])
-    act[j] = act[j] && TK_DBG_IN((r * st.K) * st.C + c, (r * st.K + st.K - 1) * st.C + c, M * st.K) &&
-             TK_DBG_IN((r * st.L) * st.C + c, (r * st.L + st.L - 1) * st.C + c, M * st.L);
-    const float* in = (st.in_src ? inter : G) + st.in_off + (r * st.K) * st.C + c;
-#pragma unroll
-    for (int k = 0; k < KB; ++k) y[j][k] = (act[j] && k < st.K) ? in[(int64_t)k * st.C] : 0.f;
-    ob[j] = (r * st.L) * st.C + c;
-  }
-  float part[PPT];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) part[j] = 0.f;
-  if (act[0]) {
-    if (st.last) {
-      // kDepth rows of T are loaded ahead of their comparisons
-      const float* t = T + st.out_off;
-      for (int lb = 0; lb < st.L; lb += kDepth) {
-        float tv[kDepth][PPT];
-#pragma unroll
-        for (int u = 0; u < kDepth; ++u)
-#pragma unroll
-          for (int j = 0; j < PPT; ++j)
-            tv[u][j] = (lb + u < st.L && act[j]) ? __ldg(t + ob[j] + (int64_t)(lb + u) * st.C) : 0.f;
-#pragma unroll
-        for (int u = 0; u < kDepth; ++u) {
-          if (lb + u >= st.L) break;
-#pragma unroll
-          for (int j = 0; j < PPT; ++j) {
-            float v = 0.f;
-#pragma unroll
-            for (int k = 0; k < KB; ++k) v = fmaf(Fs[lb + u][k], y[j][k], v);
-            if (act[j]) {
-              const float d = tv[u][j] - v;
-              part[j] = fmaf(d, d, part[j]);
-            }
-          }
-        }
-      }
-    } else {
-      float* o = inter + st.out_off;
-      for (int l = 0; l < st.L; ++l) {
-#pragma unroll
-        for (int j = 0; j < PPT; ++j) {
-          float v = 0.f;
-#pragma unroll
-          for (int k = 0; k < KB; ++k) v = fmaf(Fs[l][k], y[j][k], v);
-          if (act[j]) o[ob[j] + (int64_t)l * st.C] = v;
-        }
-      }
-    }
-  }
-  if (!st.last) return;
-  double s = 0.0;
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) s += (double)part[j];
-#pragma unroll
-  for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kBThreads / 32; ++w) t += red[w];
-    atomicAdd(res2 + st.tensor, t);
-  }
+  const double s = bexpand_tile<KB, PPT>(st, tile - st.tile0, T, F, G, inter, Fs, red);
+  if (st.last && threadIdx.x == 0) atomicAdd(res2 + st.tensor, s);
 }
 
 // fit_i = 1 - ||T_i - G_i x F||_F / ||T_i||_F (Sec. 2.2), from the residual.
@@ -534,12 +129,20 @@ struct tucker_batch_s {
   std::vector<std::vector<BGram>> sth_gram;   // STHOSVD Gram of step n
   std::vector<EigDesc> eig;                   // [mode][tensor]
   std::vector<std::vector<BExp>> fit_steps;   // reconstruction step s of every tensor
+  // the fused sweep (batch_fused.cu): the same work, tensor by tensor
+  std::vector<BNode> fz_nodes;                // tree nodes, tensor after tensor, parents first
+  std::vector<BNode> fz_cores;                // core node of each tensor
+  std::vector<BFusedTensor> fz_work;          // per tensor: its nodes and leaf Gram tiles
+  std::vector<int> fz_order;                  // tensors by decreasing size (queue order)
+  std::vector<BExp> fz_steps;                 // reconstruction steps [N][count]
   // workspace layout (bytes)
   size_t off_inter = 0, bytes_inter = 0;      // floats
   size_t off_gram = 0, bytes_gram = 0;        // doubles
   size_t off_eig = 0, bytes_eig = 0;
   size_t off_res = 0;                         // count doubles: residuals
   size_t off_cold = 0;                        // 1 + count * N ints: full-path list
+  size_t off_fzfit = 0, bytes_fzfit = 0;      // floats: the fused sweep's reconstruction intermediates
+  size_t off_queue = 0;                       // 4 ints: the fused sweep's work queue
   size_t off_tables = 0, bytes_tables = 0;
   size_t ws_total = 0;
   // device table addresses (valid after prepare)
@@ -553,6 +156,12 @@ struct tucker_batch_s {
   std::vector<DevSite<BExp>> d_fit;           // reconstruction step s
   const int64_t* d_t_off = nullptr;
   const int64_t* d_t_size = nullptr;
+  const BNode* d_fz_nodes = nullptr;
+  const BNode* d_fz_cores = nullptr;
+  const BFusedTensor* d_fz_work = nullptr;
+  const int* d_fz_order = nullptr;
+  const BExp* d_fz_steps = nullptr;
+  int fused = 0;                              // graphs record the fused sweep
   // launch configurations per site (defaults until tucker_batch_autotune)
   std::vector<BCfg> lvl_cfg;                  // per tree level
   BCfg core_cfg;
@@ -766,6 +375,9 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
     b->g_size[(size_t)i] = prod64(K, 0, N);
     b->g_total += b->g_size[(size_t)i];
     // tree nodes: every internal node gets its own intermediate buffer
+    BFusedTensor fw{};
+    fw.node0 = (int32_t)b->fz_nodes.size();
+    fw.gram0 = (int32_t)b->gram_tiles.size();
     std::vector<int64_t> out_off(pl.nodes.size(), 0);
     std::vector<int> depth(pl.nodes.size(), 0);
     int best_leaf = -1;
@@ -793,6 +405,9 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
         bn.L = (int)Ln;
         bn.K = (int)K[mode];
         b->levels[(size_t)depth[j] - 1].push_back(bn);
+        BNode fz = bn;
+        fz.staged = node_staged(bn.C, BCfg()) ? 1 : 0;
+        b->fz_nodes.push_back(fz);
       } else {
         // leaf of mode `mode`: Gram of its parent's output
         const int64_t w_off = (int64_t)gram;
@@ -830,6 +445,12 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
       bn.C = prod64(par.out_dims, mode + 1, N);
       bn.K = (int)K[mode];
       b->core_nodes.push_back(bn);
+      BNode fz = bn;
+      fz.staged = node_staged(bn.C, BCfg()) ? 1 : 0;
+      b->fz_cores.push_back(fz);
+      fw.nnodes = (int32_t)b->fz_nodes.size() - fw.node0;
+      fw.ngram = (int32_t)b->gram_tiles.size() - fw.gram0;
+      b->fz_work.push_back(fw);
     }
     // STHOSVD, natural mode order: Y_0 = T, Y_{n+1} = Y_n x_n F_n^T, G = Y_N
     {
@@ -911,6 +532,16 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
     }
     tucker_plan_destroy(p);
   }
+  // the fused sweep: reconstruction steps [N][count] (their intermediates get
+  // a region of their own: tensors are in different phases at once), queue
+  // order by decreasing size
+  for (size_t st = 0; st < b->fit_steps.size(); ++st)
+    b->fz_steps.insert(b->fz_steps.end(), b->fit_steps[st].begin(), b->fit_steps[st].end());
+  b->fz_order.resize((size_t)count);
+  std::iota(b->fz_order.begin(), b->fz_order.end(), 0);
+  std::stable_sort(b->fz_order.begin(), b->fz_order.end(),
+                   [&](int a, int c) { return b->t_size[(size_t)a] > b->t_size[(size_t)c]; });
+  b->bytes_fzfit = align_up(fit_inter * sizeof(float));
   inter = std::max(inter, fit_inter);
   while (!b->levels.empty() && b->levels.back().empty()) b->levels.pop_back();
   b->lvl_cfg.assign(b->levels.size(), BCfg());
@@ -931,6 +562,10 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
   off += align_up((size_t)count * sizeof(double));
   b->off_cold = off;
   off += align_up((size_t)(1 + (size_t)count * N) * sizeof(int));
+  b->off_fzfit = off;
+  off += b->bytes_fzfit;
+  b->off_queue = off;
+  off += align_up(4 * sizeof(int));
   b->off_tables = off;
   // work tables: each TTM / reconstruction site holds its items and a tile
   // map sized for the configuration with the most tiles
@@ -950,6 +585,9 @@ int tucker_batch_plan(int count, int N, const int64_t* dims, const int64_t* rank
   for (auto& v : b->sth_gram) tb += align_up(v.size() * sizeof(BGram));
   tb += align_up(b->eig.size() * sizeof(EigDesc));
   tb += 2 * align_up((size_t)count * sizeof(int64_t));
+  tb += align_up(b->fz_nodes.size() * sizeof(BNode)) + align_up(b->fz_cores.size() * sizeof(BNode)) +
+        align_up(b->fz_work.size() * sizeof(BFusedTensor)) + align_up(b->fz_order.size() * sizeof(int)) +
+        align_up(b->fz_steps.size() * sizeof(BExp));
   b->bytes_tables = tb;
   off += align_up(tb);
   b->ws_total = off;
@@ -1030,8 +668,16 @@ int tucker_batch_prepare(tucker_batch_t b, void* ws, size_t ws_bytes, void* stre
   b->d_eig = reinterpret_cast<const EigDesc*>(upload(ed.data(), ed.size() * sizeof(EigDesc)));
   b->d_t_off = reinterpret_cast<const int64_t*>(upload(b->t_off.data(), b->t_off.size() * sizeof(int64_t)));
   b->d_t_size = reinterpret_cast<const int64_t*>(upload(b->t_size.data(), b->t_size.size() * sizeof(int64_t)));
-  if (!b->d_core.items || !b->d_gram || !b->d_eig || !b->d_t_size)
+  b->d_fz_nodes = reinterpret_cast<const BNode*>(upload(b->fz_nodes.data(), b->fz_nodes.size() * sizeof(BNode)));
+  b->d_fz_cores = reinterpret_cast<const BNode*>(upload(b->fz_cores.data(), b->fz_cores.size() * sizeof(BNode)));
+  b->d_fz_work = reinterpret_cast<const BFusedTensor*>(
+      upload(b->fz_work.data(), b->fz_work.size() * sizeof(BFusedTensor)));
+  b->d_fz_order = reinterpret_cast<const int*>(upload(b->fz_order.data(), b->fz_order.size() * sizeof(int)));
+  b->d_fz_steps = reinterpret_cast<const BExp*>(upload(b->fz_steps.data(), b->fz_steps.size() * sizeof(BExp)));
+  if (!b->d_core.items || !b->d_gram || !b->d_eig || !b->d_t_size || !b->d_fz_nodes || !b->d_fz_cores ||
+      !b->d_fz_work || !b->d_fz_order || !b->d_fz_steps)
     return fail(TUCKER_ERR_CUDA, "tucker_batch_prepare: table upload failed");
+  TK_CUDA_TRY(cudaMemsetAsync(base + b->off_queue, 0, 4 * sizeof(int), s));
   TK_CUDA_TRY(cudaStreamSynchronize(s));  // the host tables above go out of scope
   b->prepared_ws = ws;
   return TUCKER_OK;
@@ -1062,6 +708,64 @@ int tucker_batch_sweep(tucker_batch_t b, const float* T, const float* F_in, floa
   return launch_eig_batched(b->d_eig, b->count * b->N, b->maxL, b->maxK, TUCKER_F32,
                             reinterpret_cast<char*>(F_out), reinterpret_cast<const char*>(F_in),
                             reinterpret_cast<int*>(base + b->off_cold), s);
+}
+
+int tucker_batch_sweep_fused(tucker_batch_t b, const float* T, const float* F_in, float* F_out,
+                             float* G_in, const double* normT2, double* fit, void* ws, size_t ws_bytes,
+                             void* stream) {
+  if (!b || !T || !F_in || !F_out || !G_in || !normT2 || !fit)
+    return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_sweep_fused: NULL argument");
+  if (F_in == F_out) return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_sweep_fused: F_out aliases F_in");
+  int rc = check_batch_ws(b, ws, ws_bytes, "tucker_batch_sweep_fused");
+  if (rc) return rc;
+  if ((kernel_policy() & 2) != 0)
+    return fail(TUCKER_ERR_UNSUPPORTED, "tucker_batch_sweep_fused: the fused sweep starts from the input factors "
+                                        "(kernel policy bit 1 asks for the full eigensolver path)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  int* cold = reinterpret_cast<int*>(base + b->off_cold);
+  TK_CUDA_TRY(cudaMemsetAsync(cold, 0, sizeof(int), s));
+  BFusedArgs a{};
+  a.work = b->d_fz_work;
+  a.order = b->d_fz_order;
+  a.count = b->count;
+  a.N = b->N;
+  a.KB = b->KB;
+  a.nodes = b->d_fz_nodes;
+  a.cores = b->d_fz_cores;
+  a.grams = b->d_gram;
+  a.steps = b->d_fz_steps;
+  a.eigs = b->d_eig;
+  a.f_base = reinterpret_cast<char*>(F_out);
+  a.f0_base = reinterpret_cast<const char*>(F_in);
+  a.T = T;
+  a.F = F_in;
+  a.inter = reinterpret_cast<float*>(base + b->off_inter);
+  a.fit_inter = reinterpret_cast<float*>(base + b->off_fzfit);
+  a.G = G_in;
+  a.gram = reinterpret_cast<double*>(base + b->off_gram);
+  a.normT2 = normT2;
+  a.fit = fit;
+  a.cold = cold;
+  a.queue = reinterpret_cast<int*>(base + b->off_queue);
+  a.status = device_status_ptr();
+  if (!a.status) return fail(TUCKER_ERR_CUDA, "tucker_batch_sweep_fused: device error word unavailable");
+  a.tol = 1e-12;
+  rc = launch_batch_fused(a, b->maxL, b->maxK, s);
+  if (rc) return rc;
+  return launch_eig_cold_path(b->d_eig, b->count * b->N, b->maxL, b->maxK, a.f_base, a.f0_base, cold, s);
+}
+
+int tucker_batch_queue_offset(tucker_batch_t b, size_t* off) {
+  if (!b || !off) return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_queue_offset: NULL argument");
+  *off = b->off_queue;
+  return TUCKER_OK;
+}
+
+int tucker_batch_set_fused(tucker_batch_t b, int on) {
+  if (!b || (on != 0 && on != 1)) return fail(TUCKER_ERR_INVALID_ARG, "tucker_batch_set_fused: invalid argument");
+  b->fused = on;
+  return TUCKER_OK;
 }
 
 int tucker_batch_sthosvd(tucker_batch_t b, const float* T, float* F, float* G, void* ws,
@@ -1131,9 +835,14 @@ int tucker_batch_graph_create(tucker_batch_t b, const float* T, const float* F_i
     cudaStreamDestroy(cs);
     return fail(TUCKER_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
   }
-  int rc = tucker_batch_sweep(b, T, F_in, F_out, G_in, ws, ws_bytes, cs);
-  if (rc == TUCKER_OK && G_in && normT2 && fit)
-    rc = tucker_batch_fit(b, T, F_in, G_in, normT2, fit, ws, ws_bytes, cs);
+  int rc;
+  if (b->fused && G_in && normT2 && fit) {
+    rc = tucker_batch_sweep_fused(b, T, F_in, F_out, G_in, normT2, fit, ws, ws_bytes, cs);
+  } else {
+    rc = tucker_batch_sweep(b, T, F_in, F_out, G_in, ws, ws_bytes, cs);
+    if (rc == TUCKER_OK && G_in && normT2 && fit)
+      rc = tucker_batch_fit(b, T, F_in, G_in, normT2, fit, ws, ws_bytes, cs);
+  }
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(cs, &g);
   cudaStreamDestroy(cs);

@@ -347,6 +347,8 @@ int launch_ttm_tc_f32(const float* X, int64_t R, int64_t L, int64_t C, const flo
                       float* Y, cudaStream_t s);
 // kernel-selection policy (tucker_set_kernel_policy): 0 = auto, 1 = CUDA cores only
 int kernel_policy();
+// device address of the library's device error word (tucker_device_status)
+int* device_status_ptr();
 // W += Z_(n) Z_(n)^T for Z viewed as [R][L][C] (W must be zeroed first).
 int launch_gram(int z_dtype, const void* Z, int64_t R, int64_t L, int64_t C, double* W,
                 cudaStream_t s);

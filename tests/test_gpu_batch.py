@@ -220,3 +220,87 @@ def test_batch_workspace_errors(tk):
     with pytest.raises(tk.TuckerError) as e:
         tk.tucker_batch_sweep(b, T, F, F, G, ws)
     assert "alias" in str(e.value)
+
+
+def _sthosvd_start(tk, dims, ranks, T):
+    d = tk.BatchDecomposition(T.cuda(), dims, ranks, fused=False)
+    d.sthosvd()
+    torch.cuda.synchronize()
+    return d
+
+
+def test_fused_sweep_equals_per_site_launches(tk):
+    """The persistent fused sweep runs the per-site kernels' tile and matrix
+    code tensor by tensor: from the same factors its new factors and cores
+    are bit-identical to tucker_batch_sweep's, and its fits equal
+    tucker_batch_fit's up to the order of the per-tensor FP64 sum."""
+    wb = workloads.planted_batch(96, 4, rho=1e-3)
+    dims, ranks = wb["dims"], wb["ranks"]
+    d = _sthosvd_start(tk, dims, ranks, wb["T"])
+    F0 = d.factors().clone()
+    T = d.T
+    Fa, Fb = torch.empty_like(F0), torch.empty_like(F0)
+    Ga, Gb = torch.empty_like(d.G), torch.empty_like(d.G)
+    fa, fb = torch.empty_like(d.fit_out), torch.empty_like(d.fit_out)
+    tk.tucker_batch_sweep(d.b, T, F0, Fa, Ga, d.ws)
+    tk.tucker_batch_fit(d.b, T, F0, Ga, d.normT2, fa, d.ws)
+    tk.tucker_batch_sweep_fused(d.b, T, F0, Fb, Gb, d.normT2, fb, d.ws)
+    torch.cuda.synchronize()
+    assert tk.tucker_device_status() == 0
+    assert torch.equal(Fa, Fb)
+    assert torch.equal(Ga, Gb)
+    assert torch.allclose(fa, fb, rtol=0, atol=1e-12)
+    # a second fused sweep from the new factors (the queue was reset)
+    Fc = torch.empty_like(F0)
+    tk.tucker_batch_sweep(d.b, T, Fa, Fc, Ga, d.ws)
+    tk.tucker_batch_sweep_fused(d.b, T, Fb, Fa, Gb, d.normT2, fb, d.ws)
+    torch.cuda.synchronize()
+    assert tk.tucker_device_status() == 0
+    assert torch.equal(Fc, Fa)
+
+
+def test_fused_sweep_edge_shapes_and_graph(tk):
+    """Edge shapes (length 200 with rank 32, ragged tails, a rank-1 mode, the
+    staged short-row tiles): the fused sweep recorded in a graph equals the
+    per-site launches."""
+    dims, ranks = edge_batch()
+    T = pack(dims, ranks, 5, 1e-2)
+    d = _sthosvd_start(tk, dims, ranks, T)
+    F0 = d.factors().clone()
+    Fa, Fb = torch.empty_like(F0), torch.empty_like(F0)
+    Ga = torch.empty_like(d.G)
+    tk.tucker_batch_sweep(d.b, d.T, F0, Fa, Ga, d.ws)
+    tk.tucker_batch_set_fused(d.b, True)
+    g = tk.BatchGraph(d.b, d.T, F0, Fb, d.G, d.normT2, d.fit_out, d.ws)
+    g.launch()
+    torch.cuda.synchronize()
+    assert tk.tucker_device_status() == 0
+    assert torch.equal(Fa, Fb)
+    assert torch.equal(Ga, d.G)
+
+
+def test_fused_sweep_detects_a_corrupted_queue(tk):
+    """Failure detection without a GPU fault: the host poisons the fused
+    sweep's work queue (the 'next tensor' counter already at the end), so no
+    CTA takes a tensor; the last CTA sees that fewer tensors than the batch
+    were taken, records TUCKER_ERR_INCOMPLETE in the device error word and
+    resets the queue, and the next sweep runs normally."""
+    wb = workloads.planted_batch(40, 4, rho=1e-3)
+    dims, ranks = wb["dims"], wb["ranks"]
+    d = _sthosvd_start(tk, dims, ranks, wb["T"])
+    F0 = d.factors().clone()
+    off = tk.tucker_batch_queue_offset(d.b)
+    q = d.ws[off:off + 12].view(torch.int32)
+    q[0] = d.b.count
+    Fb = torch.full_like(F0, float("nan"))
+    tk.tucker_batch_sweep_fused(d.b, d.T, F0, Fb, d.G, d.normT2, d.fit_out, d.ws)
+    torch.cuda.synchronize()
+    assert tk.tucker_device_status() == tk.TUCKER_ERR_INCOMPLETE
+    assert bool(torch.isnan(Fb).all())  # no tensor was processed
+    assert q.tolist() == [0, 0, 0]
+    tk.tucker_batch_sweep_fused(d.b, d.T, F0, Fb, d.G, d.normT2, d.fit_out, d.ws)
+    Fa = torch.empty_like(F0)
+    tk.tucker_batch_sweep(d.b, d.T, F0, Fa, None, d.ws)
+    torch.cuda.synchronize()
+    assert tk.tucker_device_status() == 0
+    assert torch.equal(Fa, Fb)
