@@ -28,7 +28,10 @@
 namespace tk {
 namespace {
 
-constexpr int kFusedBlocksPerSM = 2;
+// CTAs per SM the registers allow (64 each); every phase is latency-bound,
+// so more tensors in flight per SM pay: measured 17.7, 14.8 and 14.0 ms per
+// sweep of the 4096-tensor batch with 2, 3 and 4
+constexpr int kFusedBlocksPerSM = 4;
 
 template <typename TIn>
 __device__ __forceinline__ void wmul_all(const EigDesc& P, int use_v0, double (*Ws)[kMulJ + 1],
@@ -136,33 +139,37 @@ __global__ void __launch_bounds__(kBThreads, kFusedBlocksPerSM) bfused_kernel(co
   }
 }
 
-}  // namespace
-
-size_t batch_fused_smem(int maxL, int maxK) {
+size_t batch_fused_smem_impl(int maxL, int maxK) {
   // dynamic shared memory of the orthonormalisation and of Rayleigh-Ritz
   const size_t smo = ((size_t)maxK * (maxL + 1) + (size_t)maxK * maxK) * 8;
   const size_t sm3 = ((size_t)2 * maxK * maxK + (size_t)maxL * maxK) * 8 + (size_t)2 * maxK * maxK * 4;
   return std::max(smo, sm3);
 }
 
+template <int KB>
+int launch_kb(const BFusedArgs& a, size_t smem, cudaStream_t s) {
+  auto kern = bfused_kernel<KB>;
+  TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // a persistent grid: as many CTAs as fit at once (shared memory may allow
+  // fewer than the registers)
+  int per_sm = 0;
+  TK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem));
+  const int64_t grid = std::min<int64_t>(a.count, (int64_t)std::max(1, per_sm) * sm_count());
+  kern<<<(unsigned)grid, kBThreads, smem, s>>>(a);
+  return TUCKER_OK;
+}
+
+}  // namespace
+
+size_t batch_fused_smem(int maxL, int maxK) { return batch_fused_smem_impl(maxL, maxK); }
+
 int launch_batch_fused(const BFusedArgs& a, int maxL, int maxK, cudaStream_t s) {
   if (a.count <= 0) return TUCKER_OK;
   const size_t smem = batch_fused_smem(maxL, maxK);
-  const int64_t grid = std::min<int64_t>(a.count, (int64_t)kFusedBlocksPerSM * sm_count());
-  switch (a.KB) {
-    case 8:
-      TK_CUDA_TRY(cudaFuncSetAttribute(bfused_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      bfused_kernel<8><<<(unsigned)grid, kBThreads, smem, s>>>(a);
-      break;
-    case 16:
-      TK_CUDA_TRY(cudaFuncSetAttribute(bfused_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      bfused_kernel<16><<<(unsigned)grid, kBThreads, smem, s>>>(a);
-      break;
-    default:
-      TK_CUDA_TRY(cudaFuncSetAttribute(bfused_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      bfused_kernel<32><<<(unsigned)grid, kBThreads, smem, s>>>(a);
-      break;
-  }
+  const int rc = a.KB == 8    ? launch_kb<8>(a, smem, s)
+                 : a.KB == 16 ? launch_kb<16>(a, smem, s)
+                              : launch_kb<32>(a, smem, s);
+  if (rc) return rc;
   TK_LAUNCH_CHECK("batch_fused");
   return TUCKER_OK;
 }
