@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--ttm-pair", default=None,
                     help="time the fused root kernel (tucker_ttm_pair) alone: "
                          "'L0,L1,...:a:Ka:b:Kb[:f32|bf16]' (kernel studies and small ncu captures)")
+    ap.add_argument("--gram", default=None,
+                    help="time one Gram alone (tucker_gram, FP32): 'L0,L1,...:mode' "
+                         "(kernel studies and small ncu captures)")
     ap.add_argument("--ttm", default=None,
                     help="time one TTM kernel alone: 'L0,L1,...:mode:K[:f32|bf16|f64|fp8]' "
                          "(kernel studies and small ncu captures)")
@@ -128,6 +131,45 @@ def run_ttm_only(args):
             "K": K,
             "dtype": "fp8_e4m3" if fp8 else str(dt).replace("torch.", ""), "ms": round(ms, 5),
             "gbs": round(byts / ms / 1e6, 1), "frac_of_hbm": round(byts / ms / 1e6 / pk["hbm_gbs"], 4),
+            "steps": args.steps, "warmup": args.warmup}
+
+
+def run_gram_only(args):
+    """Times tucker_gram, W = Z_(n) Z_(n)^T, on one FP32 shape (the tensor-core
+    Gram where the shape allows, else the CUDA-core one; --kernel-policy 512
+    forces the latter).  Bytes: Z read once, W written once; work: L^2 M
+    multiply-adds (M = |Z| / L)."""
+    import torch
+
+    import paper_1707_05594_gb300 as tk
+    import workloads
+    from paper_1707_05594_gb300 import build as tkbuild
+    tkbuild.build()
+    tk.lib().tucker_set_kernel_policy(args.kernel_policy)
+    parts = args.gram.split(":")
+    dims = tuple(int(x) for x in parts[0].split(","))
+    n = int(parts[1])
+    Z = workloads.random_tensor(dims, seed=1, dtype=torch.float32, device="cuda")
+    L = dims[n]
+    W = torch.empty(L, L, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        tk.tucker_gram(Z, n, W)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        tk.tucker_gram(Z, n, W)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    byts = Z.numel() * 4 + L * L * 8
+    macs = L * Z.numel()
+    pk = peaks()
+    return {"kernel": "tucker_gram", "policy": args.kernel_policy, "shape": list(dims), "mode": n,
+            "ms": round(ms, 5), "gbs": round(byts / ms / 1e6, 1),
+            "frac_of_hbm": round(byts / ms / 1e6 / pk["hbm_gbs"], 4),
+            "tflops": round(2 * macs / ms / 1e9, 2), "status": tk.tucker_device_status(),
             "steps": args.steps, "warmup": args.warmup}
 
 
@@ -1109,11 +1151,13 @@ def run_batch_form(args):
     """Batched form on the 4096-tensor workload (3-way FP32, lengths on
     [16, 96], ranks on [4, min(16, L)], rho 1e-3): STHOSVD, then 5 HOOI sweeps
     as replays of a recorded CUDA graph (one graph launch per sweep, each sweep
-    with the fit of the factors it starts from).  Headline: the fused sweep
-    (tucker_batch_sweep_fused: one persistent launch over a work queue of
-    tensors); beside it, the per-site form (about 20 kernels per sweep, one
-    per tree level, Gram, eigensolver stage and fit step, launch
-    configurations autotuned).  Against the plain FP32 GPU form:
+    with the fit of the factors it starts from).  Two forms of the sweep:
+    fused (tucker_batch_sweep_fused: one persistent launch over a work queue
+    of tensors) and per-site (about 20 kernels per sweep, one per tree level,
+    Gram, eigensolver stage and fit step, launch configurations autotuned);
+    BatchDecomposition.autotune() times both and keeps the faster, which is
+    the headline, the other is reported beside it.  Against the plain FP32
+    GPU form:
     tucker_hooi_sweep_core + tucker_fit called tensor by tensor from the same
     STHOSVD factors.  All are timed with CUDA events over the 5 sweeps; the
     fit of each tensor's final factors is compared."""
@@ -1146,10 +1190,9 @@ def run_batch_form(args):
         return e0.elapsed_time(e1), tk.tucker_launch_count() - n0
 
     # the per-site form: default launch configurations, then autotuned ones
-    # (the graphs are recorded again with the chosen configurations)
-    d.fused = False
-    tk.tucker_batch_set_fused(b, False)
-    d._graphs = None
+    # (autotune() also picks the faster form; the graphs are recorded again)
+    fused_before = d.fused
+    d.set_fused(False)
     run_batched()  # records the two graphs, warms up
     ms_def, _ = run_batched()
     F_def = d.factors().clone()
@@ -1158,16 +1201,21 @@ def run_batch_form(args):
     t0 = time.perf_counter()
     sites = d.autotune(reps=5)
     tune_s = time.perf_counter() - t0
-    run_batched()
-    ms_site, launches_site = run_batched()
-    same_bits = bool(torch.equal(d.factors(), F_def))
-    # the fused form (the default of BatchDecomposition)
-    d.fused = True
-    tk.tucker_batch_set_fused(b, True)
-    d._graphs = None
-    run_batched()
-    ms_b, launches_b = run_batched()
-    fused_same_bits = bool(torch.equal(d.factors(), F_def))
+    chosen = d.fused
+    # both forms timed again, the same way, from the STHOSVD factors
+    timed = {}
+    for on in (False, True):
+        d.set_fused(on)
+        run_batched()
+        ms, nl = run_batched()
+        timed[on] = (ms, nl, bool(torch.equal(d.factors(), F_def)))
+    d.set_fused(chosen)
+    ms_site, launches_site, same_bits = timed[False]
+    ms_b, launches_b, fused_same_bits = timed[chosen]
+    ms_other, launches_other, _ = timed[not chosen]
+    d.cur = 0
+    d.Fbuf[0].copy_(F_sth)
+    run_batched()  # the chosen form's factors for the fit below
     # fit of the final factors: one more direct sweep yields their core
     Fb = d.factors().clone()
     Fjunk = torch.empty_like(Fb)
@@ -1197,14 +1245,20 @@ def run_batch_form(args):
                        "sweeps_per_s": round(S * 1e3 / ms_b, 2),
                        "graph_launches_per_sweep": 1,
                        "kernels_per_sweep": round(launches_b / S, 1),
-                       "form": "fused: one persistent launch per sweep (work queue of tensors), then the "
-                               "full eigensolver path's launches over the matrices its check listed",
+                       "form": ("fused: one persistent launch per sweep (work queue of tensors), then the "
+                                "full eigensolver path's launches over the matrices its check listed"
+                                if chosen else "per-site launches, autotuned configurations"),
+                       "chosen_by": "BatchDecomposition.autotune (the faster of both forms)",
+                       "size_heuristic_form": "fused" if fused_before else "per_site",
                        "same_bits_as_per_site": fused_same_bits,
                        "min_fit": float(fit_b.min()), "mean_fit": float(fit_b.mean())},
+           "other_form": {"form": "per_site" if chosen else "fused",
+                          "ms_per_sweep": round(ms_other / S, 4),
+                          "kernels_per_sweep": round(launches_other / S, 1),
+                          "chosen_speedup": round(ms_other / ms_b, 3)},
            "per_site": {"ms_per_sweep": round(ms_site / S, 4), "kernels_per_sweep": round(launches_site / S, 1),
-                        "launch_configs": "autotuned (tucker_batch_autotune)",
-                        "fused_speedup": round(ms_site / ms_b, 3)},
-           "autotune": {"seconds": round(tune_s, 3),
+                        "launch_configs": "autotuned (tucker_batch_autotune)"},
+           "autotune": {"seconds": round(tune_s, 3), "form_ms_per_sweep": d.form_ms,
                         "ms_per_sweep_default_configs": round(ms_def / S, 4),
                         "speedup_tuned_vs_default": round(ms_def / ms_site, 3),
                         "same_bits_as_default": same_bits, "sites": len(sites)},
@@ -1333,6 +1387,9 @@ def main():
     ws_size, rank, local = dist_setup()
     if args.ttm:
         print(json.dumps(run_ttm_only(args)), flush=True)
+        return 0
+    if args.gram:
+        print(json.dumps(run_gram_only(args)), flush=True)
         return 0
     if args.ttm_pair:
         print(json.dumps(run_ttm_pair_only(args)), flush=True)

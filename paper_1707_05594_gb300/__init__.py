@@ -825,14 +825,25 @@ class BatchDecomposition:
     After each sweep G and fit describe the factors the sweep started from;
     factors() is the newest factor buffer."""
 
-    def __init__(self, T, dims, ranks, fused: bool = True):
+    # Below this many tensors per SM the per-site launches are taken before
+    # autotune() times both forms: the fused sweep's CTAs need several tensors
+    # each to hide their latency (measured on GB300: per-site faster with 1024
+    # tensors, fused faster with 4096).
+    FUSED_MIN_TENSORS_PER_SM = 16
+
+    def __init__(self, T, dims, ranks, fused=None):
         import torch
         self.T = T
         self.b = BatchPlan(dims, ranks)
         # fused: each sweep (and its fit) is one persistent launch
-        # (tucker_batch_sweep_fused); else the per-site launches
+        # (tucker_batch_sweep_fused); else the per-site launches; None: by
+        # the batch's size until autotune() times both
+        if fused is None:
+            sms = torch.cuda.get_device_properties(T.device).multi_processor_count
+            fused = self.b.count >= self.FUSED_MIN_TENSORS_PER_SM * sms
         self.fused = bool(fused)
         tucker_batch_set_fused(self.b, self.fused)
+        self.form_ms = None  # ms per sweep of each form, from the last autotune()
         if T.numel() != self.b.t_elems or T.dtype != torch.float32:
             raise ValueError("T must hold the packed FP32 tensors of the batch")
         dev = T.device
@@ -851,13 +862,39 @@ class BatchDecomposition:
         tucker_batch_fit(self.b, self.T, self.Fbuf[self.cur], self.G, self.normT2, self.fit_out,
                          self.ws)
 
+    def set_fused(self, on: bool):
+        """Sweeps by the fused persistent launch (True) or the per-site
+        launches (False); recorded graphs are dropped."""
+        self.fused = bool(on)
+        tucker_batch_set_fused(self.b, self.fused)
+        self._graphs = None
+
     def autotune(self, reps: int = 5):
         """Tunes the batch's launch configurations on the current factors
-        (tucker_batch_autotune); the recorded graphs are dropped and recorded
-        again at the next graph sweep.  G is overwritten with the core of the
-        current factors."""
+        (tucker_batch_autotune), then times `reps` graph sweeps of each form
+        (per-site with the tuned configurations, and fused) from the current
+        factors and keeps the faster (form_ms holds both times).  The factors
+        are restored afterwards; G and fit are overwritten.  Both forms give
+        the same factors and cores."""
+        import torch
         self._graphs = None
         tucker_batch_autotune(self.b, self.T, self.Fbuf[self.cur], self.G, self.ws, reps)
+        F0, cur0 = self.Fbuf[self.cur].clone(), self.cur
+        ms = {}
+        for on in (False, True):
+            self.set_fused(on)
+            self.sweep(graph=True)  # records the graphs
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(max(1, reps)):
+                self.sweep(graph=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ms["fused" if on else "per_site"] = e0.elapsed_time(e1) / max(1, reps)
+            self.cur = cur0
+            self.Fbuf[cur0].copy_(F0)
+        self.form_ms = ms
+        self.set_fused(ms["fused"] < ms["per_site"])
         return tucker_batch_tuning(self.b)
 
     def sweep(self, graph: bool = True):

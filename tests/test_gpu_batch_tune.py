@@ -145,10 +145,37 @@ def test_decomposition_autotune_then_graph_sweeps(tk):
     c.sweep(graph=True)
     sites = a.autotune(reps=2)
     assert len(sites) == len(tk.tucker_batch_tuning(c.b))
+    # both forms were timed; the faster is kept
+    assert set(a.form_ms) == {"fused", "per_site"}
+    assert a.fused == (a.form_ms["fused"] < a.form_ms["per_site"])
+    # 23 tensors: the size heuristic takes the per-site launches
+    assert c.fused is False
     for _ in range(3):
         a.sweep(graph=True)
         c.sweep(graph=True)
     torch.cuda.synchronize()
+    assert torch.equal(a.factors(), c.factors())
+    assert torch.equal(a.G, c.G)
+    assert torch.allclose(a.fit_out, c.fit_out, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_decomposition_either_form_after_autotune(tk, fused):
+    """Whichever form a decomposition sweeps by, after autotune() (which
+    switches forms while it times them and restores the factors) its sweeps
+    equal those of one that never tuned, set to the same form."""
+    dims, ranks, T = mixed_batch(29)
+    a = tk.BatchDecomposition(T, dims, ranks, fused=fused)
+    c = tk.BatchDecomposition(T, dims, ranks, fused=fused)
+    a.sthosvd()
+    c.sthosvd()
+    a.autotune(reps=1)
+    a.set_fused(fused)
+    for _ in range(2):
+        a.sweep(graph=True)
+        c.sweep(graph=False)
+    torch.cuda.synchronize()
+    assert tk.tucker_device_status() == 0
     assert torch.equal(a.factors(), c.factors())
     assert torch.equal(a.G, c.G)
     assert torch.allclose(a.fit_out, c.fit_out, rtol=0, atol=1e-12)
