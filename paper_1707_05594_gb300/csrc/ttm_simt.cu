@@ -13,6 +13,8 @@
 //             stages 128 rows x 32 columns in shared memory with coalesced
 //             loads and each thread reduces its own row.
 // Accumulation is FP32 for FP32/BF16 inputs and FP64 for FP64 inputs.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace tk {
@@ -136,6 +138,17 @@ struct Slot {
   }
 };
 
+// Slots in flight per thread of ttm_cols_pipe (the ring lives in dynamic
+// shared memory so that the depth is free of the 48 KB static limit; on the
+// 200^4 root, 12, 16 and 24 slots measured 7 %, 1 % and 14 % slower than 8).
+template <int SB>
+__host__ __device__ constexpr int pipe_depth() { return 8; }
+// Rows l of F staged per chunk of ttm_cols_pipe (every chunk ends with a
+// block barrier and a reload of F; 128 rows measured 1.7 % faster than 64 on
+// the 200^4 root, 256 no better)
+template <typename A>
+__host__ __device__ constexpr int pipe_lchunk() { return sizeof(A) == 4 ? 128 : kColsLChunk; }
+
 template <typename TIn, typename TOut, int KB, int VEC>
 __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccOf<TIn>::type) <= 384) ? 2 : 1)
     ttm_cols_pipe_kernel(const TIn* __restrict__ X, const typename AccOf<TIn>::type* __restrict__ F,
@@ -143,8 +156,12 @@ __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccO
   using A = typename AccOf<TIn>::type;
   constexpr int SB = Slot<TIn, VEC>::kBytes;
   static_assert(SB == 8 || SB == 16, "slot size");
-  __shared__ __align__(16) A Fs[kColsLChunk][KB];
-  __shared__ __align__(16) unsigned char ring[kDepth][kColsThreads][SB];
+  constexpr int kDepth = pipe_depth<SB>();
+  constexpr int kLChunk = pipe_lchunk<A>();
+  __shared__ __align__(16) A Fs[kLChunk][KB];
+  // the ring, [kDepth][kColsThreads][SB] bytes of dynamic shared memory
+  extern __shared__ __align__(16) unsigned char ring_mem[];
+  unsigned char(*ring)[kColsThreads][SB] = reinterpret_cast<unsigned char(*)[kColsThreads][SB]>(ring_mem);
   const int tid = threadIdx.x;
   const int kb0 = blockIdx.y * KB;
   const int64_t total = R * C;
@@ -164,16 +181,28 @@ __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccO
     if (active && s < L) Slot<TIn, VEC>::copy(&ring[s][tid][0], xp + (int64_t)s * C);
     cp_async_commit();
   }
-  A acc[KB][VEC];
+  // FP32 accumulators in pairs of consecutive k: one packed FP32x2 FMA
+  // (two IEEE FMAs, each rounded as fmaf) per pair and position, which halves
+  // the issued multiply-add instructions; FP64 accumulators one by one
+  constexpr bool kPacked = std::is_same<A, float>::value;
+  static_assert(KB % 2 == 0, "k pairs");
+  A acc[kPacked ? 1 : KB][VEC];
+  float2 accp[kPacked ? KB / 2 : 1][VEC];
 #pragma unroll
-  for (int k = 0; k < KB; ++k)
+  for (int v = 0; v < VEC; ++v) {
+    if constexpr (kPacked) {
 #pragma unroll
-    for (int v = 0; v < VEC; ++v) acc[k][v] = A(0);
+      for (int kp = 0; kp < KB / 2; ++kp) accp[kp][v] = make_float2(0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int k = 0; k < KB; ++k) acc[k][v] = A(0);
+    }
+  }
 
-  for (int l0 = 0; l0 < L; l0 += kColsLChunk) {
-    const int lc = min(kColsLChunk, L - l0);
+  for (int l0 = 0; l0 < L; l0 += kLChunk) {
+    const int lc = min(kLChunk, L - l0);
     __syncthreads();
-    for (int i = tid; i < kColsLChunk * KB; i += kColsThreads) {
+    for (int i = tid; i < kLChunk * KB; i += kColsThreads) {
       const int l = i / KB, k = i - (i / KB) * KB;
       const int64_t e = (int64_t)(l0 + l) * K + kb0 + k;
       Fs[l][k] = (l < lc && kb0 + k < K && TK_DBG_IN(e, e, (int64_t)L * K)) ? F[e] : A(0);
@@ -206,11 +235,21 @@ __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccO
       if (active && l + kDepth < L)
         Slot<TIn, VEC>::copy(&ring[l % kDepth][tid][0], xp + (int64_t)(l + kDepth) * C);
       cp_async_commit();
+      if constexpr (kPacked) {
+        const float2* f2 = reinterpret_cast<const float2*>(&Fs[ll][0]);
 #pragma unroll
-      for (int k = 0; k < KB; ++k) {
-        const A f = Fs[ll][k];
+        for (int v = 0; v < VEC; ++v) {
+          const float2 xx = make_float2(x[v], x[v]);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[k][v] = fma(f, x[v], acc[k][v]);
+          for (int kp = 0; kp < KB / 2; ++kp) accp[kp][v] = __ffma2_rn(f2[kp], xx, accp[kp][v]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const A f = Fs[ll][k];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) acc[k][v] = fma(f, x[v], acc[k][v]);
+        }
       }
     }
   }
@@ -222,7 +261,10 @@ __global__ void __launch_bounds__(kColsThreads, (KB * VEC * sizeof(typename AccO
     if (kb0 + k < K) {
       TOut o[VEC];
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) o[v] = OutCvt<TOut>::run(acc[k][v]);
+      for (int v = 0; v < VEC; ++v) {
+        if constexpr (kPacked) o[v] = OutCvt<TOut>::run((k & 1) ? accp[k / 2][v].y : accp[k / 2][v].x);
+        else o[v] = OutCvt<TOut>::run(acc[k][v]);
+      }
       VecStore<TOut, VEC>::run(yp + (int64_t)k * C, o);
     }
   }
@@ -366,6 +408,18 @@ struct LoadBF16 {
   __device__ __forceinline__ float operator()(int64_t e) const { return bf16_to_float(__ldg(p + e)); }
 };
 
+template <typename TIn, typename TOut, int KB, int VEC>
+int launch_cols_pipe(dim3 grid, const TIn* X, const typename AccOf<TIn>::type* F, TOut* Y, int64_t R,
+                     int64_t L, int64_t C, int64_t K, cudaStream_t s) {
+  constexpr int SB = Slot<TIn, VEC>::kBytes;
+  constexpr size_t ring = (size_t)pipe_depth<SB>() * kColsThreads * SB;
+  auto kern = ttm_cols_pipe_kernel<TIn, TOut, KB, VEC>;
+  // (the static F chunk counts against the default 48 KB too)
+  TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
+  kern<<<grid, kColsThreads, ring, s>>>(X, F, Y, R, (int)L, C, (int)K);
+  return TUCKER_OK;
+}
+
 template <typename TIn, typename TOut, int KB>
 int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccOf<TIn>::type* F,
               int64_t K, TOut* Y, cudaStream_t s) {
@@ -404,8 +458,8 @@ int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccO
   const int64_t total = R * C;
   if (Vc != V && C % Vc == 0 && (uintptr_t)X % (Vc * sizeof(TIn)) == 0) {
     const int64_t gx = (total / Vc + kColsThreads - 1) / kColsThreads;
-    ttm_cols_pipe_kernel<TIn, TOut, KB, Vc><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
-        X, F, Y, R, (int)L, C, (int)K);
+    const int rc = launch_cols_pipe<TIn, TOut, KB, Vc>(dim3((unsigned)gx, gy), X, F, Y, R, L, C, K, s);
+    if (rc) return rc;
     TK_LAUNCH_CHECK("ttm_cols");
     return TUCKER_OK;
   }
@@ -413,8 +467,8 @@ int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccO
                       ((uintptr_t)Y % (V * sizeof(TOut)) == 0);
   if (vec_ok) {
     const int64_t gx = (total / V + kColsThreads - 1) / kColsThreads;
-    ttm_cols_pipe_kernel<TIn, TOut, KB, V><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
-        X, F, Y, R, (int)L, C, (int)K);
+    const int rc = launch_cols_pipe<TIn, TOut, KB, V>(dim3((unsigned)gx, gy), X, F, Y, R, L, C, K, s);
+    if (rc) return rc;
   } else {
     const int64_t gx = (total + kColsThreads - 1) / kColsThreads;
     ttm_cols_kernel<TIn, TOut, KB, 1><<<dim3((unsigned)gx, gy), kColsThreads, 0, s>>>(
