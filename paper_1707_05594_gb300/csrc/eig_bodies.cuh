@@ -532,6 +532,18 @@ __device__ __forceinline__ void eig_wmul_block(const EigDesc& P, int use_v0, int
   }
 }
 
+// 1 / sqrt(d) for d > 0: an FP32 estimate refined by two Newton steps
+// r <- r (3 - d r^2) / 2 in FP64 (each step squares the relative error:
+// ~2^-22 -> 2^-43 -> FP64 rounding), which on GB300 costs far less than the
+// FP64 square root and divide; d outside FP32's normal range takes those.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  if (!(d >= 1e-37 && d <= 1e37)) return 1.0 / sqrt(d);
+  double r = (double)rsqrtf((float)d);
+  r = r * fma(-0.5 * d, r * r, 1.5);
+  r = r * fma(-0.5 * d, r * r, 1.5);
+  return r;
+}
+
 // Block sum in FP64 for 256 threads; every thread receives the result.
 __device__ __forceinline__ double block_sum256(double v, double* red) {
   __syncthreads();
@@ -600,7 +612,7 @@ __device__ __forceinline__ int chol_qr_pass(double* Qs, int ld, double* S, int n
         fail = 1;
         break;
       }
-      const double rjj = sqrt(d), rinv = 1.0 / rjj;
+      const double rinv = rsqrt_nr(d), rjj = d * rinv;
       __syncwarp();
       for (int b = j + 1 + lane; b < K; b += 32) {
         double v = S[j * K + b];
@@ -724,12 +736,17 @@ __device__ __forceinline__ void eig_orth_body(const EigDesc& P, int mode, double
       th[t] = (fabsf(v) > 1e-20f * tmax && v != 0.f) ? (double)v : 0.0;
     }
   } else {
-    for (int t = tid; t < K; t += 256) {
+    // a warp per column, its lanes along the rows: the K dot products of
+    // length n as short chains (a thread per column would run n dependent
+    // FP64 multiply-adds)
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int t = warp; t < K; t += 8) {
       const double* a = P.Qp + (int64_t)t * n;
       const double* y = P.Y + (int64_t)t * n;
       double s = 0.0;
-      for (int r = 0; r < n; ++r) s = fma(a[r], y[r], s);
-      th[t] = s;
+      for (int r = lane; r < n; r += 32) s = fma(a[r], y[r], s);
+      s = warp_sum(s);
+      if (lane == 0) th[t] = s;
     }
   }
   __syncthreads();
@@ -784,7 +801,7 @@ __device__ __forceinline__ void eig_orth_body(const EigDesc& P, int mode, double
 // Rayleigh-Ritz: H = Q^T Y (Y = W Q) in FP64; the K x K eigenproblem of H by
 // cyclic Jacobi in FP32 (one warp; H is nearly diagonal here, since Q already
 // approximates the eigenvectors), its eigenvector matrix re-orthonormalised
-// in FP64 (Gram-Schmidt, twice) so that F = Q U stays orthonormal to FP64
+// in FP64 (two Newton-Schulz steps) so that F = Q U stays orthonormal to FP64
 // accuracy; columns sorted by decreasing eigenvalue, signs fixed, F written as
 // L x K row-major.
 // ---------------------------------------------------------------------------
@@ -800,21 +817,22 @@ __device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
   float* Uf = Hf + K * K;                            // K x K
   __shared__ int order[kMaxEigK];
   __shared__ int flip[kMaxEigK];
-  __shared__ double dots[kMaxEigK];
-  // H = sym(Q^T Y), a thread per entry (no warp reductions on the FP64 pipe)
+  // H = Q^T Y, a thread per entry of the upper triangle (no warp reductions
+  // on the FP64 pipe), mirrored: Q^T W Q is symmetric, and H is rounded to
+  // FP32 for the Jacobi step, far above the FP64 asymmetry of Q^T Y
   for (int idx = tid; idx < K * K; idx += 256) {
     const int a = idx / K, b = idx - (idx / K) * K;
     if (a > b) continue;
     const double* qa = P.Q + (int64_t)a * n;
     const double* yb = P.Y + (int64_t)b * n;
-    const double* qb = P.Q + (int64_t)b * n;
-    const double* ya = P.Y + (int64_t)a * n;
     double s0 = 0.0, s1 = 0.0;
-    for (int r = 0; r < n; ++r) {
+    int r = 0;
+    for (; r + 1 < n; r += 2) {
       s0 = fma(qa[r], yb[r], s0);
-      s1 = fma(qb[r], ya[r], s1);
+      s1 = fma(qa[r + 1], yb[r + 1], s1);
     }
-    Hf[a * K + b] = Hf[b * K + a] = (float)(0.5 * (s0 + s1));
+    if (r < n) s0 = fma(qa[r], yb[r], s0);
+    Hf[a * K + b] = Hf[b * K + a] = (float)(s0 + s1);
   }
   for (int idx = tid; idx < K * K; idx += 256) Uf[idx] = (idx / K == idx % K) ? 1.f : 0.f;
   __syncthreads();
@@ -879,34 +897,32 @@ __device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
     }
   }
   __syncthreads();
-  // U = Uf(:, order) in FP64, then Gram-Schmidt twice on its columns
+  // U = Uf(:, order) in FP64; the FP32 rotations leave it orthonormal to a
+  // few K 2^-24, and two Newton-Schulz steps U <- U (3 I - U^T U) / 2 (the
+  // error squares each step) bring it to FP64 rounding without square roots
+  // or divisions (G in H, the new U through Fs)
   for (int idx = tid; idx < K * K; idx += 256) {
     const int a = idx / K, c = idx - (idx / K) * K;
     U[idx] = (double)Uf[a * K + order[c]];
   }
   __syncthreads();
-  for (int j = 0; j < K; ++j) {
-    for (int pass = 0; pass < 2; ++pass) {
-      if (tid < j) {
-        double s = 0.0;
-        for (int a = 0; a < K; ++a) s += U[a * K + tid] * U[a * K + j];
-        dots[tid] = s;
-      }
-      __syncthreads();
-      if (tid < K) {
-        double v = U[tid * K + j];
-        for (int i = 0; i < j; ++i) v -= dots[i] * U[tid * K + i];
-        U[tid * K + j] = v;
-      }
-      __syncthreads();
-    }
-    if (tid == 0) {
-      double s = 0.0;
-      for (int a = 0; a < K; ++a) s += U[a * K + j] * U[a * K + j];
-      dots[0] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  for (int it = 0; it < 2; ++it) {
+    for (int idx = tid; idx < K * K; idx += 256) {
+      const int b = idx / K, c = idx - (idx / K) * K;
+      if (b > c) continue;
+      double g = 0.0;
+      for (int a = 0; a < K; ++a) g = fma(U[a * K + b], U[a * K + c], g);
+      H[b * K + c] = H[c * K + b] = g;
     }
     __syncthreads();
-    if (tid < K) U[tid * K + j] *= dots[0];
+    for (int idx = tid; idx < K * K; idx += 256) {
+      const int a = idx / K, c = idx - (idx / K) * K;
+      double v = 0.0;
+      for (int b = 0; b < K; ++b) v = fma(U[a * K + b], H[b * K + c], v);
+      Fs[idx] = 1.5 * U[idx] - 0.5 * v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < K * K; idx += 256) U[idx] = Fs[idx];
     __syncthreads();
   }
   // F = Q U
