@@ -845,6 +845,25 @@ __device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
     for (int i = 0; i < K; ++i) hmax = fmaxf(hmax, fabsf(Hf[i * K + i]));
     const float floor_abs = 2e-7f * hmax;
     for (int sweep = 0; sweep < 30; ++sweep) {
+      // a sweep in which no pair reaches the rotation threshold only zeroes
+      // the off-diagonal entries: test every pair at once first and do that
+      // directly (the common case once Q approximates the eigenvectors)
+      bool big = false;
+      for (int idx = lane; idx < K * K; idx += 32) {
+        const int p = idx / K, q = idx - (idx / K) * K;
+        if (p >= q) continue;
+        const float apq = Hf[idx];
+        const float app = Hf[p * K + p], aqq = Hf[q * K + q];
+        big = big || (apq != 0.f && !(fabsf(apq) <= floor_abs ||
+                                      fabsf(apq) <= 1e-9f * sqrtf(fabsf(app) * fabsf(aqq))));
+      }
+      if (!__any_sync(0xffffffffu, big)) {
+        __syncwarp();
+        for (int idx = lane; idx < K * K; idx += 32)
+          if (idx / K != idx - (idx / K) * K) Hf[idx] = 0.f;
+        __syncwarp();
+        break;
+      }
       int rotated = 0;
       for (int p = 0; p < K - 1; ++p) {
         for (int q = p + 1; q < K; ++q) {

@@ -345,6 +345,108 @@ __global__ void __launch_bounds__(kColsThreads, (KB * sizeof(typename AccOf<TIn>
     if (kb0 + k < K) yp[k] = OutCvt<TOut>::run(acc[k]);
 }
 
+// ---------------------------------------------------------------------------
+// ttm_rows_multi: the last mode (C == 1) for FP32 accumulators when the rows
+// are many: each thread owns RV consecutive rows (RV x K accumulators, in k
+// pairs for the packed FP32x2 multiply-add), so that every F value read from
+// shared memory serves RV rows (one row per thread reads F once per
+// multiply-add pair); each row streams through the thread's own cp.async
+// slots, kRowsDepth steps of VEC elements in flight per row.  Same sums as
+// ttm_rows_pipe (l in increasing order, one FMA per term).
+// ---------------------------------------------------------------------------
+constexpr int kRowsDepth = 4;
+// rows per thread: four up to KB = 20, two above (register budget of two
+// 256-thread blocks per SM)
+__host__ __device__ constexpr int rows_multi(int KB) { return KB <= 20 ? 4 : 2; }
+
+template <typename TIn, typename TOut, int KB, int VEC, int RV>
+__global__ void __launch_bounds__(kColsThreads, 2)
+    ttm_rows_multi_kernel(const TIn* __restrict__ X, const float* __restrict__ F, TOut* __restrict__ Y,
+                          int64_t R, int L, int K) {
+  static_assert(sizeof(TIn) == 4 && VEC == 4 && KB % 2 == 0, "FP32 rows, 16-byte slots");
+  constexpr int SB = VEC * 4;
+  constexpr int kLChunk = 128;
+  __shared__ __align__(16) float Fs[kLChunk][KB];
+  // [kRowsDepth][RV][kColsThreads][SB] bytes of dynamic shared memory
+  extern __shared__ __align__(16) unsigned char ring_mem[];
+  const int tid = threadIdx.x;
+  const int kb0 = blockIdx.y * KB;
+  auto slot = [&](int st, int j) -> unsigned char* {
+    return ring_mem + (((size_t)st * RV + j) * kColsThreads + tid) * SB;
+  };
+  const int64_t rb = ((int64_t)blockIdx.x * kColsThreads + tid) * RV;
+  // rows rb .. rb + RV - 1 (consecutive, L elements each) and Y[r, kb0 ..]
+  unsigned act = 0;
+#pragma unroll
+  for (int j = 0; j < RV; ++j) {
+    const int64_t r = rb + j;
+    if (r < R && TK_DBG_IN(r * L, r * L + L - 1, R * L) &&
+        TK_DBG_IN(r * K + kb0, r * K + min(K, kb0 + KB) - 1, R * K))
+      act |= 1u << j;
+  }
+  const TIn* xb = X + (act ? rb : 0) * L;
+  const int nsteps = L / VEC;
+#pragma unroll
+  for (int st = 0; st < kRowsDepth; ++st) {
+#pragma unroll
+    for (int j = 0; j < RV; ++j)
+      if (((act >> j) & 1) && st < nsteps) cp_async_16(slot(st, j), xb + j * L + st * VEC);
+    cp_async_commit();
+  }
+  float2 acc[RV][KB / 2];
+#pragma unroll
+  for (int j = 0; j < RV; ++j)
+#pragma unroll
+    for (int kp = 0; kp < KB / 2; ++kp) acc[j][kp] = make_float2(0.f, 0.f);
+  for (int l0 = 0; l0 < L; l0 += kLChunk) {
+    const int lc = min(kLChunk, L - l0);
+    __syncthreads();
+    for (int i = tid; i < kLChunk * KB; i += kColsThreads) {
+      const int l = i / KB, k = i - (i / KB) * KB;
+      const int64_t e = (int64_t)(l0 + l) * K + kb0 + k;
+      Fs[l][k] = (l < lc && kb0 + k < K && TK_DBG_IN(e, e, (int64_t)L * K)) ? F[e] : 0.f;
+    }
+    __syncthreads();
+    for (int ll = 0; ll < lc; ll += VEC) {
+      const int step = (l0 + ll) / VEC;
+      cp_async_wait<kRowsDepth - 1>();
+      float x[RV][VEC];
+#pragma unroll
+      for (int j = 0; j < RV; ++j) {
+        const float4 q = *reinterpret_cast<const float4*>(slot(step % kRowsDepth, j));
+        x[j][0] = q.x;
+        x[j][1] = q.y;
+        x[j][2] = q.z;
+        x[j][3] = q.w;
+      }
+#pragma unroll
+      for (int j = 0; j < RV; ++j)
+        if (((act >> j) & 1) && step + kRowsDepth < nsteps)
+          cp_async_16(slot(step % kRowsDepth, j), xb + j * L + (step + kRowsDepth) * VEC);
+      cp_async_commit();
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const float2* f2 = reinterpret_cast<const float2*>(&Fs[ll + v][0]);
+#pragma unroll
+        for (int kp = 0; kp < KB / 2; ++kp) {
+          const float2 f = f2[kp];
+#pragma unroll
+          for (int j = 0; j < RV; ++j) acc[j][kp] = __ffma2_rn(f, make_float2(x[j][v], x[j][v]), acc[j][kp]);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+#pragma unroll
+  for (int j = 0; j < RV; ++j) {
+    if (!((act >> j) & 1)) continue;
+    TOut* yp = Y + (rb + j) * K + kb0;
+#pragma unroll
+    for (int k = 0; k < KB; ++k)
+      if (kb0 + k < K) yp[k] = OutCvt<TOut>::run((k & 1) ? acc[j][k / 2].y : acc[j][k / 2].x);
+  }
+}
+
 constexpr int kRowsThreads = 128;
 constexpr int kRowsLChunk = 32;
 
@@ -439,6 +541,23 @@ int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccO
         done = try_launch_rows_staged(LoadBF16{reinterpret_cast<const unsigned short*>(X)}, R, L,
                                       reinterpret_cast<const float*>(F), K, Y, s, &rc);
       if (done) return rc;
+    }
+  }
+  if constexpr (sizeof(TIn) == 4) {
+    // many long FP32 rows: RV rows per thread (enough blocks for two per SM;
+    // measured on C == 1 roots: 200^4 mode 3 2.97 -> 2.45 ms, 20 x 200^3
+    // 0.313 -> 0.291 ms; rows of 64 or fewer elements no faster)
+    if (C == 1 && L >= 128 && L % V == 0 && (uintptr_t)X % (V * sizeof(TIn)) == 0 &&
+        R >= (int64_t)rows_multi(KB) * kColsThreads * 2 * sm_count()) {
+      constexpr int RV = rows_multi(KB);
+      const int64_t gx = (R + (int64_t)RV * kColsThreads - 1) / ((int64_t)RV * kColsThreads);
+      constexpr size_t ring = (size_t)kRowsDepth * RV * kColsThreads * 16;
+      auto kern = ttm_rows_multi_kernel<TIn, TOut, KB, 4, RV>;
+      TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
+      kern<<<dim3((unsigned)gx, gy), kColsThreads, ring, s>>>(X, reinterpret_cast<const float*>(F), Y, R,
+                                                              (int)L, (int)K);
+      TK_LAUNCH_CHECK("ttm_rows_multi");
+      return TUCKER_OK;
     }
   }
   if (C == 1 && L % V == 0 && (uintptr_t)X % (V * sizeof(TIn)) == 0) {

@@ -114,6 +114,33 @@ def test_ttm_short_rows_match_oracle(tk, orc, shape, n, K, dtype, offset):
     assert np.all(err <= (shape[n] + 2) * U32 * bound + 1e-300), (err / (bound + 1e-300)).max()
 
 
+# C == 1 with many long FP32 rows (L >= 128; enough rows for two blocks per
+# SM at four rows per thread for K <= 20, two above): the multi-row kernel; R
+# ragged against the rows of a block, L over one F chunk of 128 or two, K over
+# the rank classes and above 32 (two k blocks); and rows just too short for it
+MULTI_ROW_CASES = [
+    ((311302, 128), 1, 20), ((311300, 200), 1, 5), ((160001, 136), 1, 24), ((160003, 128), 1, 33),
+    ((2, 160000, 132), 2, 16), ((311301, 124), 1, 20),
+]
+
+
+@pytest.mark.parametrize("shape,n,K", MULTI_ROW_CASES)
+def test_ttm_many_rows_match_oracle(tk, orc, shape, n, K):
+    X = workloads.random_tensor(shape, seed=sum(shape) + 3 * n, dtype=torch.float32)
+    F = workloads.random_factor(shape[n], K, seed=K + 5, dtype=torch.float32, orthonormal=False)
+    out_shape = list(shape)
+    out_shape[n] = K
+    Y = torch.full(out_shape, float("nan"), dtype=torch.float32, device="cuda")
+    tk.tucker_ttm(X.cuda(), n, F.cuda(), Y)
+    torch.cuda.synchronize()
+    Xd = X.double().numpy()
+    Fd = F.double().numpy()
+    ref = orc.ttm(Xd, n, Fd.T)
+    bound = orc.ttm(np.abs(Xd), n, np.abs(Fd).T)
+    err = np.abs(Y.double().cpu().numpy() - ref)
+    assert np.all(err <= (shape[n] + 2) * U32 * bound + 1e-300), (err / (bound + 1e-300)).max()
+
+
 TC_CASES = [
     # column case (mode not last; C % 8 == 0, C >= 64): ragged tiles, l chunks
     ((5, 200, 136), 1, 20), ((3, 37, 64), 1, 5), ((2, 64, 1000), 1, 16), ((130, 72), 0, 1),
