@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--workload", default="big_fp32")
     ap.add_argument("--tree", default="optimal",
                     choices=["optimal", "chain", "chain_k", "chain_h", "balanced"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the BF16-vs-FP32 comparison on the 64^5 workload")
@@ -900,26 +900,50 @@ def run_ours(args, ws_size, rank):
     traffic = traffic_from_profiles(f"ttm_root_{args.workload}")
     total_node_ms = {str(k): round(sum(v) / len(v), 5) for k, v in sorted(node_ms.items())}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step uploads
+    # its tensor from pinned host memory and reads its factors, core and fit
+    # back; the upload of step i + 1 goes into a second device buffer on a
+    # copy stream while step i computes (double buffering), so the link and
+    # the sweep overlap; the first upload and the last read-back are inside
+    # the timed region
     e2e_steps = max(1, args.e2e_steps)
     T_host = torch.empty(T.shape, dtype=T.dtype, pin_memory=True)
     T_host.copy_(T)
     F_host = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in d.F]
     G_host = torch.empty(d.G.shape, dtype=d.G.dtype, pin_memory=True)
     fit_host = torch.empty(2, dtype=torch.float64, pin_memory=True)
+    T_dev = [T, torch.empty_like(T)]
+    cs = torch.cuda.Stream()
+    landed = [torch.cuda.Event(), torch.cuda.Event()]
+    freed = [torch.cuda.Event(), torch.cuda.Event()]
     torch.cuda.synchronize()
     barrier(ws_size)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s)
-    for _ in range(e2e_steps):
-        T.copy_(T_host, non_blocking=True)
+    cs.wait_event(e0)
+    with torch.cuda.stream(cs):
+        T_dev[0].copy_(T_host, non_blocking=True)
+    landed[0].record(cs)
+    for i in range(e2e_steps):
+        b = i & 1
+        if i + 1 < e2e_steps:
+            if i >= 1:
+                cs.wait_event(freed[1 - b])  # step i - 1 is done with that buffer
+            with torch.cuda.stream(cs):
+                T_dev[1 - b].copy_(T_host, non_blocking=True)
+            landed[1 - b].record(cs)
+        s.wait_event(landed[b])
+        d.T = T_dev[b]
         step()
+        freed[b].record(s)
         for fh, fd in zip(F_host, d.F):
             fh.copy_(fd, non_blocking=True)
         G_host.copy_(d.G, non_blocking=True)
         fit_host.copy_(d.fit_out, non_blocking=True)
     e1.record(s)
     torch.cuda.synchronize()
+    d.T = T
+    del T_dev
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, ws_size)
     h2d = T.numel() * esz
     d2h = sum(f.numel() * f.element_size() for f in d.F) + d.G.numel() * d.G.element_size() + 16
@@ -957,7 +981,8 @@ def run_ours(args, ws_size, rank):
         "fit": fit,
         "vs_oracle": err,
         "e2e": {"value": round(ws_size * 1e3 / e2e_ms, 3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                "pipelined": "upload of step i + 1 on a copy stream overlaps step i (two device buffers)"},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
