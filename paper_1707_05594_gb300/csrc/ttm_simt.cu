@@ -447,6 +447,116 @@ __global__ void __launch_bounds__(kColsThreads, 2)
   }
 }
 
+// ---------------------------------------------------------------------------
+// ttm_rows_tile: the last mode (C == 1) for FP32 rows with L % 8 == 0.  A
+// block owns RB = 256 RV consecutive rows and streams them through S stages of
+// 8 columns: each stage copies the tile's RB x 8 floats with 16-byte cp.async
+// in row order (a warp's copy covers 16 whole 32-byte sectors, where a
+// thread-per-row stream touches 32 sectors for 16 bytes each), into rows
+// padded to 12 floats so that a quarter-warp's 16-byte reads of 8 consecutive
+// rows hit distinct banks; the stage's 8 rows of F arrive in the same
+// cp.async group (zero-filled past K).  Thread t owns rows t + 256 j of the
+// tile, k in pairs by packed FP32x2 FMAs.  Same sums as ttm_rows_pipe.
+// ---------------------------------------------------------------------------
+constexpr int kTileLC = 8;    // columns l per stage
+constexpr int kTileLD = 12;   // padded row stride of a stage (floats)
+__host__ __device__ constexpr int rows_tile_rv(int KB) { return KB <= 20 ? 2 : 1; }
+constexpr int kTileStages = 4;
+constexpr bool kRowsTileOn = true;
+
+__device__ __forceinline__ void cp_async_4_zfill(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+
+template <typename TOut, int KB, int RV>
+__global__ void __launch_bounds__(kColsThreads, 2)
+    ttm_rows_tile_kernel(const float* __restrict__ X, const float* __restrict__ F, TOut* __restrict__ Y,
+                         int64_t R, int L, int K) {
+  static_assert(KB % 2 == 0, "k pairs");
+  constexpr int RB = kColsThreads * RV;
+  constexpr int S = kTileStages;
+  // [S][RB][kTileLD] floats of row tiles, then [S][kTileLC][KB] floats of F
+  extern __shared__ __align__(16) float tile_mem[];
+  float* Xs = tile_mem;
+  float* Fs = tile_mem + (size_t)S * RB * kTileLD;
+  const int tid = threadIdx.x;
+  const int kb0 = blockIdx.y * KB;
+  const int64_t rb = (int64_t)blockIdx.x * RB;
+  const int nch = L / kTileLC;
+  // the block's rows rb .. rb + RB - 1 of X (L elements each), Y[r, kb0 ..]
+  const int64_t rlast = min(R, rb + RB) - 1;
+  const bool ok = TK_DBG_IN(rb * L, (rlast + 1) * L - 1, R * L) &&
+                  TK_DBG_IN(rb * K + kb0, rlast * K + min(K, kb0 + KB) - 1, R * K);
+  auto issue = [&](int c) {
+    if (c < nch && ok) {
+      float* xs = Xs + (size_t)(c % S) * RB * kTileLD;
+      const int l0 = c * kTileLC;
+#pragma unroll
+      for (int q = 0; q < 2 * RV; ++q) {
+        const int p = q * kColsThreads + tid;
+        const int row = p >> 1, half = p & 1;
+        if (rb + row < R) cp_async_16(xs + row * kTileLD + half * 4, X + (rb + row) * L + l0 + half * 4);
+      }
+      float* fs = Fs + (size_t)(c % S) * kTileLC * KB;
+      for (int i = tid; i < kTileLC * KB; i += kColsThreads) {
+        const int l = i / KB, k = i - (i / KB) * KB;
+        const bool in = kb0 + k < K && TK_DBG_IN((int64_t)(l0 + l) * K + kb0 + k, (int64_t)(l0 + l) * K + kb0 + k, (int64_t)L * K);
+        cp_async_4_zfill(fs + i, F + (in ? (int64_t)(l0 + l) * K + kb0 + k : 0), in ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int c = 0; c < S - 1; ++c) issue(c);
+  float2 acc[RV][KB / 2];
+#pragma unroll
+  for (int j = 0; j < RV; ++j)
+#pragma unroll
+    for (int kp = 0; kp < KB / 2; ++kp) acc[j][kp] = make_float2(0.f, 0.f);
+  for (int c = 0; c < nch; ++c) {
+    cp_async_wait<S - 2>();
+    __syncthreads();  // chunk c is in for every thread; chunk c - 1's slot is free
+    issue(c + S - 1);
+    const float* xs = Xs + (size_t)(c % S) * RB * kTileLD;
+    const float* fs = Fs + (size_t)(c % S) * kTileLC * KB;
+    // the stage's 8 columns in two halves of 4 (one 16-byte read per row)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float x[RV][4];
+#pragma unroll
+      for (int j = 0; j < RV; ++j) {
+        const float4 a = *reinterpret_cast<const float4*>(xs + (j * kColsThreads + tid) * kTileLD + 4 * h);
+        x[j][0] = a.x;
+        x[j][1] = a.y;
+        x[j][2] = a.z;
+        x[j][3] = a.w;
+      }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const float2* f2 = reinterpret_cast<const float2*>(fs + (4 * h + l) * KB);
+#pragma unroll
+        for (int kp = 0; kp < KB / 2; ++kp) {
+          const float2 f = f2[kp];
+#pragma unroll
+          for (int j = 0; j < RV; ++j) acc[j][kp] = __ffma2_rn(f, make_float2(x[j][l], x[j][l]), acc[j][kp]);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (!ok) return;
+#pragma unroll
+  for (int j = 0; j < RV; ++j) {
+    const int64_t r = rb + j * kColsThreads + tid;
+    if (r >= R) continue;
+    TOut* yp = Y + r * K + kb0;
+#pragma unroll
+    for (int k = 0; k < KB; ++k)
+      if (kb0 + k < K) yp[k] = OutCvt<TOut>::run((k & 1) ? acc[j][k / 2].y : acc[j][k / 2].x);
+  }
+}
+
 constexpr int kRowsThreads = 128;
 constexpr int kRowsLChunk = 32;
 
@@ -544,6 +654,27 @@ int launch_kb(const TIn* X, int64_t R, int64_t L, int64_t C, const typename AccO
     }
   }
   if constexpr (sizeof(TIn) == 4) {
+    // FP32 rows of a multiple of 8 elements: row tiles staged by stages of 8
+    // columns (enough blocks for one per SM), where measured faster than the
+    // multi-row kernel: rows of up to 64 elements (64^5 and 16 x 64^4 mode-4
+    // roots 2.36 -> 2.01 and 0.60 -> 0.52 ms) and inputs up to 2^28 elements
+    // (20 x 200^3 mode 3: 0.291 -> 0.276 ms); above that, rows of 200 ran 4-5 %
+    // slower than with four rows per thread
+    if (C == 1 && kRowsTileOn && L % kTileLC == 0 && (uintptr_t)X % 16 == 0 &&
+        (L <= 64 || R * L <= ((int64_t)1 << 28)) &&
+        R >= (int64_t)rows_tile_rv(KB) * kColsThreads * sm_count()) {
+      constexpr int RV = rows_tile_rv(KB);
+      const int64_t rbk = (int64_t)RV * kColsThreads;
+      const int64_t gx = (R + rbk - 1) / rbk;
+      constexpr size_t smem = ((size_t)kTileStages * rbk * kTileLD + (size_t)kTileStages * kTileLC * KB) * 4;
+      auto kern = ttm_rows_tile_kernel<TOut, KB, RV>;
+      TK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<dim3((unsigned)gx, gy), kColsThreads, smem, s>>>(reinterpret_cast<const float*>(X),
+                                                             reinterpret_cast<const float*>(F), Y, R,
+                                                             (int)L, (int)K);
+      TK_LAUNCH_CHECK("ttm_rows_tile");
+      return TUCKER_OK;
+    }
     // many long FP32 rows: RV rows per thread (enough blocks for two per SM;
     // measured on C == 1 roots: 200^4 mode 3 2.97 -> 2.45 ms, 20 x 200^3
     // 0.313 -> 0.291 ms; rows of 64 or fewer elements no faster)

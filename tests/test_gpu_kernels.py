@@ -114,13 +114,16 @@ def test_ttm_short_rows_match_oracle(tk, orc, shape, n, K, dtype, offset):
     assert np.all(err <= (shape[n] + 2) * U32 * bound + 1e-300), (err / (bound + 1e-300)).max()
 
 
-# C == 1 with many long FP32 rows (L >= 128; enough rows for two blocks per
-# SM at four rows per thread for K <= 20, two above): the multi-row kernel; R
-# ragged against the rows of a block, L over one F chunk of 128 or two, K over
-# the rank classes and above 32 (two k blocks); and rows just too short for it
+# C == 1 with many FP32 rows: the staged row-tile kernel where L % 8 == 0,
+# the multi-row kernel for long rows otherwise; R ragged against the rows of
+# a block, L over one F chunk of 128 or two, K over the rank classes and
+# above 32 (two k blocks)
 MULTI_ROW_CASES = [
     ((311302, 128), 1, 20), ((311300, 200), 1, 5), ((160001, 136), 1, 24), ((160003, 128), 1, 33),
     ((2, 160000, 132), 2, 16), ((311301, 124), 1, 20),
+    # staged row tiles (L % 8 == 0, at least a block of rows per SM): two
+    # stages of columns, K above 32 (two k blocks)
+    ((80001, 16), 1, 5), ((40000, 64), 1, 33), ((3, 30000, 200), 2, 20),
 ]
 
 
