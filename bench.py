@@ -916,6 +916,15 @@ def run_ours(args, ws_size, rank):
     cs = torch.cuda.Stream()
     landed = [torch.cuda.Event(), torch.cuda.Event()]
     freed = [torch.cuda.Event(), torch.cuda.Event()]
+    # the host-to-device rate of this machine for the same copy (the bound of
+    # e2e: it varies between hosts), timed alone before the e2e region
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(s)
+    T_dev[1].copy_(T_host, non_blocking=True)
+    c1.record(s)
+    torch.cuda.synchronize()
+    h2d_gbs = T.numel() * T.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9
     torch.cuda.synchronize()
     barrier(ws_size)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -982,7 +991,9 @@ def run_ours(args, ws_size, rank):
         "vs_oracle": err,
         "e2e": {"value": round(ws_size * 1e3 / e2e_ms, 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-                "pipelined": "upload of step i + 1 on a copy stream overlaps step i (two device buffers)"},
+                "pipelined": "upload of step i + 1 on a copy stream overlaps step i (two device buffers)",
+                "h2d_gbs": round(h2d_gbs, 1),
+                "link_bound_value": round(h2d_gbs * 1e9 / h2d * ws_size, 3)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
