@@ -393,8 +393,13 @@ size_t tucker_bf16_split_lo_offset(int64_t n);
  *              x_lo y_hi, one 32-column stage per accumulator, the stage sums
  *              added in FP32 registers and the block sums in FP64 -- as
  *              accurate as FP32 arithmetic; bit 0 also selects the CUDA cores).
+ *   bit 10 (1024): the warm-started eigensolver keeps each matrix's
+ *              orthonormalisations and Rayleigh-Ritz in one CTA (otherwise a
+ *              batch of at most 8 matrices with L >= 64, as in a sweep of
+ *              one tensor, runs them on a cluster of 4 CTAs per matrix, each
+ *              summing a quarter of the rows; the results agree to rounding).
  * Bits 5, 6 and 8 are read by tucker_plan (the pair changes the plan's
- * buffer layout) and by the calls.  TUCKER_ERR_INVALID_ARG outside 0..1023. */
+ * buffer layout) and by the calls.  TUCKER_ERR_INVALID_ARG outside 0..2047. */
 int tucker_set_kernel_policy(int policy);
 
 /* Debug build: the library compiled with -DTUCKER_DEBUG

@@ -24,6 +24,7 @@
 
 #include "batch_fused.h"
 #include "eig_bodies.cuh"
+#include "eig_cluster.cuh"
 
 namespace tk {
 namespace {
@@ -87,6 +88,18 @@ __global__ void __launch_bounds__(256) eig_finalize_kernel(const EigBatch B, int
     __syncthreads();
     eig_finalize_body<TOut>(P);
   }
+}
+
+// The warm path's orthonormalisation and Rayleigh-Ritz with a cluster of
+// kEigCS CTAs per matrix (descriptors by value: a few large matrices).
+__global__ void __launch_bounds__(256) eig_orth_cluster_kernel(const EigBatch B, int mode, double tol) {
+  const unsigned m = blockIdx.x / kEigCS;
+  eig_orth_cluster_body(get_desc(B, m), mode, tol, m, B.cold);
+}
+
+template <typename TOut>
+__global__ void __launch_bounds__(256) eig_finalize_cluster_kernel(const EigBatch B) {
+  eig_finalize_cluster_body<TOut>(get_desc(B, blockIdx.x / kEigCS));
 }
 
 int max_smem_optin() {
@@ -193,6 +206,28 @@ int launch_eig_cold_path(const EigDesc* dev, int count, int maxL, int maxK, char
 
 namespace {
 
+// Matrices of at least this many rows take the cluster form (a quarter of
+// the rows per CTA); smaller ones stay in one CTA.
+constexpr int kEigClusterMinL = 64;
+
+// nb clusters of kEigCS CTAs (one cluster per matrix), 256 threads each.
+template <typename... Args>
+cudaError_t launch_cluster(void (*kern)(Args...), int nb, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nb * kEigCS));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kEigCS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // The launch sequence for nb matrices described by EB (by value or device).
 int run_eig(const EigBatch& EB, int nb, int maxL, int maxK, int f_dtype, bool warm,
             cudaStream_t s, bool cold_only) {
@@ -237,18 +272,49 @@ int run_eig(const EigBatch& EB, int nb, int maxL, int maxK, int f_dtype, bool wa
       else
         eig_seed_kernel<float><<<gb, 256, 0, s>>>(EB);
       TK_LAUNCH_CHECK("eig_seed");
+      // a few large matrices (descriptors by value): a cluster of CTAs per
+      // matrix for the orthonormalisations and Rayleigh-Ritz, whose FP64 row
+      // sums one SM's FP64 pipe bounds
+      const size_t smoc = orth_cluster_smem(maxL, maxK), smfc = finalize_cluster_smem(maxL, maxK);
+      const bool clus = !EB.dev && maxL >= kEigClusterMinL && smoc <= (size_t)smax && smfc <= (size_t)smax &&
+                        (kernel_policy() & 1024) == 0;
+      auto orth = [&](int mode) -> int {
+        if (!clus) {
+          eig_orth_kernel<<<gb, 256, smo, s>>>(EB, mode, 0, tol);
+          TK_LAUNCH_CHECK("eig_orth");
+          return TUCKER_OK;
+        }
+        TK_CUDA_TRY(cudaFuncSetAttribute(eig_orth_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smoc));
+        TK_CUDA_TRY(launch_cluster(eig_orth_cluster_kernel, nb, smoc, s, EB, mode, tol));
+        TK_LAUNCH_CHECK("eig_orth_cluster");
+        return TUCKER_OK;
+      };
       launch_wmul<float>(EB, nb, maxL, 1, 0, s);
       TK_LAUNCH_CHECK("eig_wmul");
-      eig_orth_kernel<<<gb, 256, smo, s>>>(EB, 1, 0, tol);
-      TK_LAUNCH_CHECK("eig_orth");
-      launch_wmul<double>(EB, nb, maxL, 0, 0, s);
-      TK_LAUNCH_CHECK("eig_wmul");
-      eig_orth_kernel<<<gb, 256, smo, s>>>(EB, 2, 0, tol);
-      TK_LAUNCH_CHECK("eig_orth");
-      launch_wmul<double>(EB, nb, maxL, 0, 0, s);
-      TK_LAUNCH_CHECK("eig_wmul");
-      int rc = finalize(0);
+      int rc = orth(1);
       if (rc) return rc;
+      launch_wmul<double>(EB, nb, maxL, 0, 0, s);
+      TK_LAUNCH_CHECK("eig_wmul");
+      rc = orth(2);
+      if (rc) return rc;
+      launch_wmul<double>(EB, nb, maxL, 0, 0, s);
+      TK_LAUNCH_CHECK("eig_wmul");
+      if (clus) {
+        if (f_dtype == TUCKER_F64) {
+          TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_cluster_kernel<double>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smfc));
+          TK_CUDA_TRY(launch_cluster(eig_finalize_cluster_kernel<double>, nb, smfc, s, EB));
+        } else {
+          TK_CUDA_TRY(cudaFuncSetAttribute(eig_finalize_cluster_kernel<float>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smfc));
+          TK_CUDA_TRY(launch_cluster(eig_finalize_cluster_kernel<float>, nb, smfc, s, EB));
+        }
+        TK_LAUNCH_CHECK("eig_finalize_cluster");
+      } else {
+        rc = finalize(0);
+        if (rc) return rc;
+      }
       gate = 1;
     }
     eig_stage1_kernel<<<gb, kEigThreads, sm1, s>>>(EB, gate);

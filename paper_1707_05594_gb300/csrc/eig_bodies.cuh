@@ -797,6 +797,96 @@ __device__ __forceinline__ void eig_orth_body(const EigDesc& P, int mode, double
   }
 }
 
+// Cyclic Jacobi sweeps on the K x K FP32 matrix Hf (rotations accumulated
+// in Uf), by one warp: at most 30 sweeps; pairs below the rotation
+// threshold (floor_abs, or 1e-9 of the geometric mean of their diagonal
+// entries) are zeroed without rotating.
+__device__ __forceinline__ void jacobi_sweeps(float* Hf, float* Uf, int K, int lane, float floor_abs) {
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    // a sweep in which no pair reaches the rotation threshold only zeroes
+    // the off-diagonal entries: test every pair at once first and do that
+    // directly (the common case once Q approximates the eigenvectors)
+    bool big = false;
+    for (int idx = lane; idx < K * K; idx += 32) {
+      const int p = idx / K, q = idx - (idx / K) * K;
+      if (p >= q) continue;
+      const float apq = Hf[idx];
+      const float app = Hf[p * K + p], aqq = Hf[q * K + q];
+      big = big || (apq != 0.f && !(fabsf(apq) <= floor_abs ||
+                                    fabsf(apq) <= 1e-9f * sqrtf(fabsf(app) * fabsf(aqq))));
+    }
+    if (!__any_sync(0xffffffffu, big)) {
+      __syncwarp();
+      for (int idx = lane; idx < K * K; idx += 32)
+        if (idx / K != idx - (idx / K) * K) Hf[idx] = 0.f;
+      __syncwarp();
+      break;
+    }
+    int rotated = 0;
+    for (int p = 0; p < K - 1; ++p) {
+      for (int q = p + 1; q < K; ++q) {
+        const float apq = Hf[p * K + q];
+        const float app = Hf[p * K + p], aqq = Hf[q * K + q];
+        if (apq == 0.f) continue;
+        if (fabsf(apq) <= floor_abs || fabsf(apq) <= 1e-9f * sqrtf(fabsf(app) * fabsf(aqq))) {
+          __syncwarp();
+          if (lane == 0) Hf[p * K + q] = Hf[q * K + p] = 0.f;
+          __syncwarp();
+          continue;
+        }
+        rotated = 1;
+        const float th = (aqq - app) / (2.f * apq);
+        const float t = (th >= 0.f) ? 1.f / (th + sqrtf(1.f + th * th))
+                                    : -1.f / (-th + sqrtf(1.f + th * th));
+        const float c = rsqrtf(1.f + t * t), s = t * c;
+        __syncwarp();
+        for (int k = lane; k < K; k += 32) {
+          const float hkp = Hf[k * K + p], hkq = Hf[k * K + q];
+          Hf[k * K + p] = c * hkp - s * hkq;
+          Hf[k * K + q] = s * hkp + c * hkq;
+        }
+        __syncwarp();
+        for (int k = lane; k < K; k += 32) {
+          const float hpk = Hf[p * K + k], hqk = Hf[q * K + k];
+          Hf[p * K + k] = c * hpk - s * hqk;
+          Hf[q * K + k] = s * hpk + c * hqk;
+          const float ukp = Uf[k * K + p], ukq = Uf[k * K + q];
+          Uf[k * K + p] = c * ukp - s * ukq;
+          Uf[k * K + q] = s * ukp + c * ukq;
+        }
+        __syncwarp();
+        if (lane == 0) Hf[p * K + q] = Hf[q * K + p] = 0.f;
+        __syncwarp();
+      }
+    }
+    if (!rotated) break;
+  }}
+
+// Two Newton-Schulz steps U <- U (3 I - U^T U) / 2 on the K x K FP64 matrix
+// U (G and T are K x K scratch), all threads of the block.
+__device__ __forceinline__ void newton_schulz2(double* U, double* G, double* T, int K) {
+  const int tid = threadIdx.x;
+  for (int it = 0; it < 2; ++it) {
+    for (int idx = tid; idx < K * K; idx += 256) {
+      const int b = idx / K, c = idx - (idx / K) * K;
+      if (b > c) continue;
+      double g = 0.0;
+      for (int a = 0; a < K; ++a) g = fma(U[a * K + b], U[a * K + c], g);
+      G[b * K + c] = G[c * K + b] = g;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < K * K; idx += 256) {
+      const int a = idx / K, c = idx - (idx / K) * K;
+      double v = 0.0;
+      for (int b = 0; b < K; ++b) v = fma(U[a * K + b], G[b * K + c], v);
+      T[idx] = 1.5 * U[idx] - 0.5 * v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < K * K; idx += 256) U[idx] = T[idx];
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Rayleigh-Ritz: H = Q^T Y (Y = W Q) in FP64; the K x K eigenproblem of H by
 // cyclic Jacobi in FP32 (one warp; H is nearly diagonal here, since Q already
@@ -844,65 +934,7 @@ __device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
     float hmax = 0.f;
     for (int i = 0; i < K; ++i) hmax = fmaxf(hmax, fabsf(Hf[i * K + i]));
     const float floor_abs = 2e-7f * hmax;
-    for (int sweep = 0; sweep < 30; ++sweep) {
-      // a sweep in which no pair reaches the rotation threshold only zeroes
-      // the off-diagonal entries: test every pair at once first and do that
-      // directly (the common case once Q approximates the eigenvectors)
-      bool big = false;
-      for (int idx = lane; idx < K * K; idx += 32) {
-        const int p = idx / K, q = idx - (idx / K) * K;
-        if (p >= q) continue;
-        const float apq = Hf[idx];
-        const float app = Hf[p * K + p], aqq = Hf[q * K + q];
-        big = big || (apq != 0.f && !(fabsf(apq) <= floor_abs ||
-                                      fabsf(apq) <= 1e-9f * sqrtf(fabsf(app) * fabsf(aqq))));
-      }
-      if (!__any_sync(0xffffffffu, big)) {
-        __syncwarp();
-        for (int idx = lane; idx < K * K; idx += 32)
-          if (idx / K != idx - (idx / K) * K) Hf[idx] = 0.f;
-        __syncwarp();
-        break;
-      }
-      int rotated = 0;
-      for (int p = 0; p < K - 1; ++p) {
-        for (int q = p + 1; q < K; ++q) {
-          const float apq = Hf[p * K + q];
-          const float app = Hf[p * K + p], aqq = Hf[q * K + q];
-          if (apq == 0.f) continue;
-          if (fabsf(apq) <= floor_abs || fabsf(apq) <= 1e-9f * sqrtf(fabsf(app) * fabsf(aqq))) {
-            __syncwarp();
-            if (lane == 0) Hf[p * K + q] = Hf[q * K + p] = 0.f;
-            __syncwarp();
-            continue;
-          }
-          rotated = 1;
-          const float th = (aqq - app) / (2.f * apq);
-          const float t = (th >= 0.f) ? 1.f / (th + sqrtf(1.f + th * th))
-                                      : -1.f / (-th + sqrtf(1.f + th * th));
-          const float c = rsqrtf(1.f + t * t), s = t * c;
-          __syncwarp();
-          for (int k = lane; k < K; k += 32) {
-            const float hkp = Hf[k * K + p], hkq = Hf[k * K + q];
-            Hf[k * K + p] = c * hkp - s * hkq;
-            Hf[k * K + q] = s * hkp + c * hkq;
-          }
-          __syncwarp();
-          for (int k = lane; k < K; k += 32) {
-            const float hpk = Hf[p * K + k], hqk = Hf[q * K + k];
-            Hf[p * K + k] = c * hpk - s * hqk;
-            Hf[q * K + k] = s * hpk + c * hqk;
-            const float ukp = Uf[k * K + p], ukq = Uf[k * K + q];
-            Uf[k * K + p] = c * ukp - s * ukq;
-            Uf[k * K + q] = s * ukp + c * ukq;
-          }
-          __syncwarp();
-          if (lane == 0) Hf[p * K + q] = Hf[q * K + p] = 0.f;
-          __syncwarp();
-        }
-      }
-      if (!rotated) break;
-    }
+    jacobi_sweeps(Hf, Uf, K, lane, floor_abs);
     if (lane == 0) {
       for (int i = 0; i < K; ++i) order[i] = i;
       for (int i = 0; i < K; ++i) {
@@ -925,25 +957,7 @@ __device__ __forceinline__ void eig_finalize_body(const EigDesc& P) {
     U[idx] = (double)Uf[a * K + order[c]];
   }
   __syncthreads();
-  for (int it = 0; it < 2; ++it) {
-    for (int idx = tid; idx < K * K; idx += 256) {
-      const int b = idx / K, c = idx - (idx / K) * K;
-      if (b > c) continue;
-      double g = 0.0;
-      for (int a = 0; a < K; ++a) g = fma(U[a * K + b], U[a * K + c], g);
-      H[b * K + c] = H[c * K + b] = g;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < K * K; idx += 256) {
-      const int a = idx / K, c = idx - (idx / K) * K;
-      double v = 0.0;
-      for (int b = 0; b < K; ++b) v = fma(U[a * K + b], H[b * K + c], v);
-      Fs[idx] = 1.5 * U[idx] - 0.5 * v;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < K * K; idx += 256) U[idx] = Fs[idx];
-    __syncthreads();
-  }
+  newton_schulz2(U, H, Fs, K);
   // F = Q U
   for (int idx = tid; idx < n * K; idx += 256) {
     const int r = idx / K, c = idx - (idx / K) * K;

@@ -1438,8 +1438,8 @@ int kernel_policy() { return g_policy.load(std::memory_order_relaxed); }
 }  // namespace tk
 
 extern "C" int tucker_set_kernel_policy(int policy) {
-  if (policy < 0 || policy > 1023)
-    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 1023]");
+  if (policy < 0 || policy > 2047)
+    return tk::fail(TUCKER_ERR_INVALID_ARG, "tucker_set_kernel_policy: policy must be in [0, 2047]");
   tk::g_policy.store(policy, std::memory_order_relaxed);
   return TUCKER_OK;
 }
