@@ -396,8 +396,8 @@ size_t tucker_bf16_split_lo_offset(int64_t n);
  *   bit 10 (1024): the warm-started eigensolver keeps each matrix's
  *              orthonormalisations and Rayleigh-Ritz in one CTA (otherwise a
  *              batch of at most 8 matrices with L >= 64, as in a sweep of
- *              one tensor, runs them on a cluster of 4 CTAs per matrix, each
- *              summing a quarter of the rows; the results agree to rounding).
+ *              one tensor, runs them on a cluster of 8 CTAs per matrix, each
+ *              summing an eighth of the rows; the results agree to rounding).
  * Bits 5, 6 and 8 are read by tucker_plan (the pair changes the plan's
  * buffer layout) and by the calls.  TUCKER_ERR_INVALID_ARG outside 0..2047. */
 int tucker_set_kernel_policy(int policy);

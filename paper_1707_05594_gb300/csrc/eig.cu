@@ -206,7 +206,7 @@ int launch_eig_cold_path(const EigDesc* dev, int count, int maxL, int maxK, char
 
 namespace {
 
-// Matrices of at least this many rows take the cluster form (a quarter of
+// Matrices of at least this many rows take the cluster form (an eighth of
 // the rows per CTA); smaller ones stay in one CTA.
 constexpr int kEigClusterMinL = 64;
 

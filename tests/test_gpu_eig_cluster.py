@@ -1,5 +1,5 @@
 """The warm-started eigensolver of a sweep (Sec. 5's EVD, started from the
-input factors) on a cluster of CTAs per matrix -- each CTA sums a quarter of
+input factors) on a cluster of CTAs per matrix -- each CTA sums an eighth of
 the rows, the K x K work is the same in every CTA -- against the FP64 oracle's
 sweep, and against the single-CTA form (kernel policy bit 10) to rounding.
 Shapes: every mode L >= 64 (the cluster form's range), rows not divisible by
