@@ -159,6 +159,10 @@ WORKLOADS = {
                        noise="gauss", dtype=torch.float32, sweeps=10),
     "uneven6": dict(L=(64, 56, 48, 40, 32, 24), K=(16, 14, 12, 10, 8, 6), rho=1e-2, seed=5,
                     spectrum=None, noise="student_t3", dtype=torch.float32, sweeps=8),
+    # a 640 MB cut of the 200^4 recipe (three modes of 200, ranks 20) for
+    # profiler captures of the per-sweep kernels, which must stay small
+    "mid_fp32": dict(L=(200, 200, 200, 20), K=(20, 20, 20, 10), rho=1e-2, seed=6,
+                     spectrum="inv_k", noise="gauss", dtype=torch.float32, sweeps=5),
 }
 
 
